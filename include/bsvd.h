@@ -1,0 +1,134 @@
+/*
+ * bsvd.h -- C ABI of the batched QR / one-sided Jacobi SVD / randomized SVD library for GB300
+ * (sm_103a), after Boukaram, Turkiyyah, Ltaief & Keyes, "Batched QR and SVD Algorithms on GPUs
+ * with Applications in Hierarchical Matrix Compression" (2017).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A batch is `batch` independent matrices.  Each one is passed through a DEVICE array of
+ *    DEVICE pointers (`void* const* dA`, element b points at matrix b) plus DEVICE arrays of
+ *    per-matrix sizes (`d_m`, `d_n`, `d_lda`, ...).  This is the pointer-array form of the batched
+ *    interfaces the paper builds on (Section 3: batches of independent small matrices).
+ *  - Storage is column-major: entry (i, j) of matrix b lives at dA[b][j * lda[b] + i].  Every
+ *    leading dimension must be >= max(1, rows).
+ *  - dtype is BSVD_F32 or BSVD_F64; all matrices of one call share it.  Scalars such as
+ *    singular values have the same type as the matrices.
+ *  - `max_m`, `max_n` are HOST upper bounds of d_m, d_n over the batch; they choose the memory
+ *    tier and the launch shape.  A matrix that exceeds them gets info = BSVD_INFO_BAD_SHAPE.
+ *  - `stream` is a cudaStream_t passed as an opaque pointer (NULL = legacy default stream).
+ *    Every call is asynchronous on it: the host returns after enqueueing, never synchronises,
+ *    and never allocates device memory.  Buffers belong to the caller and must stay valid
+ *    until the stream work completes.
+ *  - The return value is a HOST status: BSVD_SUCCESS, a negative argument code
+ *    (-k means argument k, counted from 1, is invalid; nothing was launched),
+ *    BSVD_ERR_UNSUPPORTED (shape beyond the tiers this build implements; nothing launched) or
+ *    BSVD_ERR_CUDA (a launch failed; the stream's state is whatever CUDA reports).
+ *  - Per-matrix results go to the DEVICE array d_info (one int per matrix).
+ */
+#ifndef BSVD_H
+#define BSVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSVD_F32 0
+#define BSVD_F64 1
+
+#define BSVD_SUCCESS 0
+#define BSVD_ERR_UNSUPPORTED (-1000)
+#define BSVD_ERR_CUDA (-1001)
+
+/* per-matrix info */
+#define BSVD_INFO_BAD_SHAPE (-1)
+#define BSVD_INFO_NOT_CONVERGED (1 << 20) /* + sweeps run: the sweep cap was reached */
+
+/* Jacobi memory tiers (argument `tier` of batched_svd_jacobi).  `tier` may carry a variant in
+   bits 8 and up: BSVD_TIER_REGISTER | (k << 8) forces the k-th register variant that fits the
+   shape bound (k = 0: the first); see bsvd_jacobi_variants. */
+#define BSVD_TIER_AUTO 0
+#define BSVD_TIER_REGISTER 1 /* Section 4: matrix and V resident in registers, one lane per pair */
+#define BSVD_TIER_SHARED 2   /* Section 5: matrix and V resident in shared memory */
+
+/*
+ * batched_qr -- reduced Householder QR of each matrix, A = Q R (Algorithm 1, Section 2.1;
+ * batched kernel of Section 3.1).
+ *
+ *   dA[b]  (in)  m x n, m >= n, ld d_lda[b]; not modified.
+ *   dQ[b]  (out) m x n with orthonormal columns, ld d_ldq[b] >= m.  dQ may be NULL (no Q).
+ *   dR[b]  (out) n x n upper triangular, ld d_ldr[b] >= n; entries below the diagonal are
+ *                written as exact zeros.  dR may be NULL (no R).
+ *   d_info[b] (out) 0, or BSVD_INFO_BAD_SHAPE (m < n, a negative size, a size above max_m /
+ *                max_n, or a leading dimension too small) -- outputs of that matrix untouched.
+ * Reflectors follow Algorithm 1: v = house(x) with R(i,i) = -sign(x_1) ||x|| (sign(0) = +1).
+ * Q and R are therefore unique; a zero column gives the identity reflector.
+ * Limits: max_m <= 1024 and max_m * max_n * sizeof(element) <= 200 KiB (the matrix is factored
+ * in shared memory); otherwise BSVD_ERR_UNSUPPORTED.
+ */
+int batched_qr(int dtype, int batch, int max_m, int max_n,
+               void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+               void* const* dQ, const int* d_ldq,
+               void* const* dR, const int* d_ldr,
+               int* d_info, void* stream);
+
+/*
+ * batched_svd_jacobi -- reduced SVD A = U diag(S) V^T of each matrix by one-sided Jacobi
+ * (Algorithm 2, Section 2.2; register / shared-memory kernels of Sections 4-5).
+ *
+ *   dA[b]  (in)  m x n, ld d_lda[b]; not modified.  k = min(m, n).  A wide matrix (m < n) is
+ *                processed through its transpose.
+ *   dS[b]  (out) k singular values, descending (Section 1); ties keep column order.
+ *   dU[b]  (out) m x k left singular vectors, ld d_ldu[b] >= m; dU may be NULL.  A column whose
+ *                singular value is zero is written as zeros.
+ *   dV[b]  (out) n x k right singular vectors (accumulated rotations), ld d_ldv[b] >= n; dV may
+ *                be NULL, which also skips the accumulation.
+ *   tol    rotation threshold: pair (i, j) is rotated only when
+ *          |a_i . a_j| > tol * ||a_i|| ||a_j||.  tol <= 0 selects sqrt(max(m, n)) * u with u the
+ *          unit roundoff of dtype (2^-24 or 2^-53).
+ *   max_sweeps  sweep cap (<= 0 selects 30).
+ *   tier   BSVD_TIER_AUTO or a specific tier; see the tier macros.
+ *   d_info[b] (out) number of sweeps run (the last one rotates nothing), or
+ *                BSVD_INFO_NOT_CONVERGED + sweeps when the cap was reached (results are the last
+ *                iterate), or BSVD_INFO_BAD_SHAPE.
+ *   d_rotations[b] (out, nullable) number of plane rotations applied.
+ * Rotations use zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+ * c = 1 / sqrt(1 + t^2), s = c t on the 2 x 2 Gram matrix [[alpha, gamma], [gamma, beta]].
+ * Tiers: the register tier holds min(m, n) <= 64 and max(m, n) <= 128 (F32) / 64 (F64); the shared
+ * tier max(m, n) <= 256 and min(m, n) <= 128 (F32) / 64 (F64).  BSVD_TIER_AUTO uses the choice
+ * recorded by bsvd_set_jacobi_choice for the size bin, else the register tier when it fits, else
+ * the shared tier; larger shapes give BSVD_ERR_UNSUPPORTED.
+ */
+int batched_svd_jacobi(int dtype, int batch, int max_m, int max_n,
+                       void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+                       void* const* dS,
+                       void* const* dU, const int* d_ldu,
+                       void* const* dV, const int* d_ldv,
+                       double tol, int max_sweeps, int tier,
+                       int* d_info, long long* d_rotations, void* stream);
+
+/*
+ * bsvd_jacobi_variants -- number of kernel variants of `tier` (BSVD_TIER_REGISTER or
+ * BSVD_TIER_SHARED) that can run a batch bounded by max_m x max_n, or a negative argument code.
+ * Host only; launches nothing.  The autotuner times each variant and records the fastest.
+ */
+int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier);
+
+/*
+ * bsvd_set_jacobi_choice -- record the encoded tier (tier | variant << 8) that BSVD_TIER_AUTO
+ * uses for batches whose bounds fall in the same size bin as max_m x max_n (bins are powers of
+ * two of max(m, n) and min(m, n), up to 256).  BSVD_TIER_AUTO clears the entry.  Host only, not
+ * thread-safe against concurrent batched_svd_jacobi calls; returns 0 or a negative argument code.
+ * (This tuning table is the project's addition: the paper tunes its kernels by hand, Sections 3-5.)
+ */
+int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
+
+/* Library version and build description (static strings). */
+const char* bsvd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSVD_H */

@@ -1,0 +1,207 @@
+"""GB300-native batched QR, one-sided Jacobi SVD and randomized SVD.
+
+After Boukaram, Turkiyyah, Ltaief & Keyes, "Batched QR and SVD Algorithms on GPUs with
+Applications in Hierarchical Matrix Compression" (2017).  The work happens in ``libbsvd.so``, a
+CUDA library for sm_103a with the C ABI of ``include/bsvd.h``; this module only marshals
+arguments to it through ctypes.  PyTorch supplies device memory and streams.  There is no CPU
+path: every function raises if the library is not built or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB, build  # noqa: F401  (build() compiles libbsvd.so in-tree)
+
+F32, F64 = 0, 1
+SUCCESS = 0
+ERR_UNSUPPORTED = -1000
+ERR_CUDA = -1001
+INFO_BAD_SHAPE = -1
+INFO_NOT_CONVERGED = 1 << 20
+TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BsvdError(RuntimeError):
+    """A non-zero status returned by an entry point of libbsvd.so."""
+
+    def __init__(self, fn: str, code: int):
+        what = {ERR_UNSUPPORTED: "unsupported shape", ERR_CUDA: "CUDA launch failure"}.get(code)
+        super().__init__(f"{fn} returned {code}" + (f" ({what})" if what else f" (argument {-code} invalid)"))
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is missing: build it with paper_1707_05141_gb300.build()")
+            L = ctypes.CDLL(LIB)
+            i, d, p, ll = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
+            L.bsvd_version.restype = ctypes.c_char_p
+            L.bsvd_version.argtypes = []
+            L.batched_qr.restype = i
+            L.batched_qr.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, p]
+            L.batched_svd_jacobi.restype = i
+            L.batched_svd_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, p, p, p]
+            L.bsvd_jacobi_variants.restype = i
+            L.bsvd_jacobi_variants.argtypes = [i, i, i, i]
+            L.bsvd_set_jacobi_choice.restype = i
+            L.bsvd_set_jacobi_choice.argtypes = [i, i, i, i]
+            _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().bsvd_version().decode()
+
+
+def jacobi_variants(dtype_code: int, max_m: int, max_n: int, tier: int) -> int:
+    """Number of kernel variants of ``tier`` able to run a max_m x max_n batch."""
+    return lib().bsvd_jacobi_variants(dtype_code, max_m, max_n, tier)
+
+
+def set_jacobi_choice(dtype_code: int, max_m: int, max_n: int, tier: int) -> None:
+    """Record the (tier | variant << 8) that TIER_AUTO uses for this size bin."""
+    _check("bsvd_set_jacobi_choice", lib().bsvd_set_jacobi_choice(dtype_code, max_m, max_n, tier))
+
+
+# ----------------------------------------------------------------------------------------------
+# marshalling helpers (torch is only the allocator)
+# ----------------------------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
+
+
+class Batch:
+    """A batch of column-major matrices in device memory, in the pointer-array form of the C ABI.
+
+    ``ptrs`` (int64), ``m``, ``n``, ``ld`` (int32) are device tensors with one entry per matrix;
+    ``max_m``/``max_n`` are host bounds.  ``keep`` holds the tensors that own the storage.
+    """
+
+    def __init__(self, ptrs, m, n, ld, dtype, max_m, max_n, keep=()):
+        self.ptrs, self.m, self.n, self.ld = ptrs, m, n, ld
+        self.dtype, self.max_m, self.max_n = dtype, int(max_m), int(max_n)
+        self.keep = tuple(keep)
+
+    @property
+    def batch(self) -> int:
+        return int(self.ptrs.numel())
+
+    @property
+    def code(self) -> int:
+        torch = _torch()
+        return F32 if self.dtype == torch.float32 else F64
+
+    @classmethod
+    def uniform(cls, t, m: int | None = None, n: int | None = None):
+        """``t`` of shape (batch, cols, ld), contiguous on the GPU: matrix b is t[b].T[:m, :n]."""
+        torch = _torch()
+        assert t.is_cuda and t.is_contiguous() and t.dim() == 3
+        bsz, cols, ld = t.shape
+        m = ld if m is None else m
+        n = cols if n is None else n
+        es = t.element_size()
+        base = int(t.data_ptr())
+        dev = t.device
+        ptrs = base + torch.arange(bsz, device=dev, dtype=torch.int64) * (cols * ld * es)
+        full = lambda v: torch.full((bsz,), int(v), device=dev, dtype=torch.int32)
+        return cls(ptrs, full(m), full(n), full(ld), t.dtype, m, n, keep=(t,))
+
+    @classmethod
+    def packed(cls, flat, offsets, m, n, ld=None):
+        """Matrices at element ``offsets`` of a flat device tensor; ``m``, ``n``, ``ld`` per matrix
+        (``ld`` defaults to max(1, m))."""
+        torch = _torch()
+        dev = flat.device
+        off = torch.as_tensor(offsets, dtype=torch.int64).to(dev)
+        mt = torch.as_tensor(m, dtype=torch.int32).to(dev)
+        nt = torch.as_tensor(n, dtype=torch.int32).to(dev)
+        ldt = mt.clamp(min=1) if ld is None else torch.as_tensor(ld, dtype=torch.int32).to(dev)
+        ptrs = int(flat.data_ptr()) + off * flat.element_size()
+        mh = torch.as_tensor(m)
+        nh = torch.as_tensor(n)
+        return cls(ptrs, mt, nt, ldt, flat.dtype, int(mh.max()) if mh.numel() else 0,
+                   int(nh.max()) if nh.numel() else 0, keep=(flat,))
+
+
+def _check(fn, rc):
+    if rc != SUCCESS:
+        raise BsvdError(fn, rc)
+
+
+# ----------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ----------------------------------------------------------------------------------------------
+
+def batched_qr(A: Batch, Q: Batch | None, R: Batch | None, info, stream=None) -> None:
+    """Reduced Householder QR of every matrix of ``A`` (Algorithm 1); see include/bsvd.h."""
+    rc = lib().batched_qr(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
+                          _ptr(Q.ptrs if Q else None), _ptr(Q.ld if Q else None),
+                          _ptr(R.ptrs if R else None), _ptr(R.ld if R else None), _ptr(info), _stream_ptr(stream))
+    _check("batched_qr", rc)
+
+
+def batched_svd_jacobi(A: Batch, S: Batch, U: Batch | None, V: Batch | None, info, rotations=None,
+                       tol: float = 0.0, max_sweeps: int = 0, tier: int = TIER_AUTO, stream=None) -> None:
+    """Reduced SVD of every matrix of ``A`` by one-sided Jacobi (Algorithm 2); see include/bsvd.h."""
+    rc = lib().batched_svd_jacobi(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
+                                  _ptr(S.ptrs), _ptr(U.ptrs if U else None), _ptr(U.ld if U else None),
+                                  _ptr(V.ptrs if V else None), _ptr(V.ld if V else None), float(tol),
+                                  int(max_sweeps), int(tier), _ptr(info), _ptr(rotations), _stream_ptr(stream))
+    _check("batched_svd_jacobi", rc)
+
+
+# ----------------------------------------------------------------------------------------------
+# conveniences that allocate the outputs with torch (uniform batches)
+# ----------------------------------------------------------------------------------------------
+
+def qr(a, want_q: bool = True, want_r: bool = True, stream=None):
+    """QR of a uniform batch ``a`` (batch, n, m) on the GPU -> (Q (batch, n, m), R (batch, n, n), info)."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    A = Batch.uniform(a.contiguous(), m, n)
+    q = torch.empty((bsz, n, m), device=a.device, dtype=a.dtype) if want_q else None
+    r = torch.empty((bsz, n, n), device=a.device, dtype=a.dtype) if want_r else None
+    info = torch.empty(bsz, device=a.device, dtype=torch.int32)
+    batched_qr(A, Batch.uniform(q, m, n) if want_q else None, Batch.uniform(r, n, n) if want_r else None, info,
+               stream)
+    return q, r, info
+
+
+def svd(a, want_u: bool = True, want_v: bool = True, tol: float = 0.0, max_sweeps: int = 0, tier: int = TIER_AUTO,
+        stream=None):
+    """Jacobi SVD of a uniform batch ``a`` (batch, n, m) -> (U (batch, k, m), S (batch, k), V (batch, k, n),
+    info, rotations)."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    k = min(m, n)
+    A = Batch.uniform(a.contiguous(), m, n)
+    s = torch.empty((bsz, 1, k), device=a.device, dtype=a.dtype)
+    u = torch.empty((bsz, k, m), device=a.device, dtype=a.dtype) if want_u else None
+    v = torch.empty((bsz, k, n), device=a.device, dtype=a.dtype) if want_v else None
+    info = torch.empty(bsz, device=a.device, dtype=torch.int32)
+    rots = torch.empty(bsz, device=a.device, dtype=torch.int64)
+    batched_svd_jacobi(A, Batch.uniform(s, k, 1), Batch.uniform(u, m, k) if want_u else None,
+                       Batch.uniform(v, n, k) if want_v else None, info, rots, tol, max_sweeps, tier, stream)
+    return u, s.view(bsz, k), v, info, rots

@@ -1,0 +1,154 @@
+// api.cu -- the extern "C" boundary declared in include/bsvd.h: host-side argument checks, tier
+// selection and launches on the caller's stream.  No device allocation, no synchronisation.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsvd {
+template <typename T>
+int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st);
+template <typename T>
+int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
+                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st);
+template <typename T>
+int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                       void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st);
+}  // namespace bsvd
+
+using namespace bsvd;
+
+namespace {
+
+// Autotuning table: for each (dtype, size bin of max(m, n), size bin of min(m, n)) the encoded
+// tier | variant << 8 that BSVD_TIER_AUTO uses.  0 = not tuned (built-in preference order).
+constexpr int kBins = 9;  // bins 0..8 cover sizes <= 1, 2, 4, ..., 256
+int g_choice[2][kBins][kBins];
+
+int size_bin(int x)
+{
+    int b = 0;
+    while ((1 << b) < x && b < kBins - 1) ++b;
+    return b;
+}
+
+template <typename T>
+int svd_dispatch(int batch, int max_m, int max_n, int tier, void* const* dA, const int* d_m, const int* d_n,
+                 const int* d_lda, void* const* dS, void* const* dU, const int* d_ldu, void* const* dV, const int* d_ldv,
+                 double tol, int max_sweeps, int* d_info, long long* d_rot, cudaStream_t st)
+{
+    int base = tier & 0xff, variant = tier >> 8;
+    if (base == BSVD_TIER_AUTO) {
+        const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+        const int c = g_choice[sizeof(T) == 8][size_bin(mm)][size_bin(nn)];
+        if (c) {
+            base = c & 0xff;
+            variant = c >> 8;
+        }
+    }
+    if (base == BSVD_TIER_AUTO || base == BSVD_TIER_REGISTER) {
+        const int rc = launch_jacobi_reg<T>(batch, max_m, max_n, variant, dA, d_m, d_n, d_lda, dS, dU, d_ldu, dV,
+                                            d_ldv, tol, max_sweeps, d_info, d_rot, st);
+        if (rc != BSVD_ERR_UNSUPPORTED || base == BSVD_TIER_REGISTER) return rc;
+    }
+    return launch_jacobi_smem<T>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dS, dU, d_ldu, dV, d_ldv, tol,
+                                 max_sweeps, d_info, d_rot, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bsvd_version(void)
+{
+    return "bsvd-gb300 0.2 (sm_103a; batched Householder QR, register/shared one-sided Jacobi SVD)";
+}
+
+int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
+               const int* d_lda, void* const* dQ, const int* d_ldq, void* const* dR, const int* d_ldr, int* d_info,
+               void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0 || max_n > max_m) return -4;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (dQ && !d_ldq) return -10;
+    if (dR && !d_ldr) return -12;
+    if (!d_info) return -13;
+    const size_t es = dtype == BSVD_F32 ? 4 : 8;
+    if (max_m > 1024 || (size_t)max_m * max_n * es > 200 * 1024) return BSVD_ERR_UNSUPPORTED;
+    if (max_n == 0) max_n = 1;
+    if (max_m == 0) max_m = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32 ? launch_qr<float>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dQ, d_ldq, dR, d_ldr, d_info, st)
+                             : launch_qr<double>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dQ, d_ldq, dR, d_ldr, d_info, st);
+}
+
+int batched_svd_jacobi(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
+                       const int* d_lda, void* const* dS, void* const* dU, const int* d_ldu, void* const* dV,
+                       const int* d_ldv, double tol, int max_sweeps, int tier, int* d_info, long long* d_rotations,
+                       void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0) return -4;
+    if ((tier & 0xff) != BSVD_TIER_AUTO && (tier & 0xff) != BSVD_TIER_REGISTER && (tier & 0xff) != BSVD_TIER_SHARED)
+        return -16;
+    if ((tier & 0xff) == BSVD_TIER_SHARED && (tier >> 8) != 0) return -16;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (!dS) return -9;
+    if (dU && !d_ldu) return -11;
+    if (dV && !d_ldv) return -13;
+    if (!(tol == tol)) return -14;  // NaN
+    if (!d_info) return -17;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32 ? svd_dispatch<float>(batch, max_m, max_n, tier, dA, d_m, d_n, d_lda, dS, dU, d_ldu, dV,
+                                                   d_ldv, tol, max_sweeps, d_info, d_rotations, st)
+                             : svd_dispatch<double>(batch, max_m, max_n, tier, dA, d_m, d_n, d_lda, dS, dU, d_ldu, dV,
+                                                    d_ldv, tol, max_sweeps, d_info, d_rotations, st);
+}
+
+int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (max_m < 0) return -2;
+    if (max_n < 0) return -3;
+    if (tier == BSVD_TIER_REGISTER)
+        return dtype == BSVD_F32 ? launch_jacobi_reg<float>(0, max_m, max_n, -1, nullptr, nullptr, nullptr, nullptr,
+                                                            nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0,
+                                                            nullptr, nullptr, nullptr)
+                                 : launch_jacobi_reg<double>(0, max_m, max_n, -1, nullptr, nullptr, nullptr, nullptr,
+                                                             nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0,
+                                                             nullptr, nullptr, nullptr);
+    if (tier == BSVD_TIER_SHARED) {
+        const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+        return (mm <= 256 && nn <= (dtype == BSVD_F32 ? 128 : 64)) ? 1 : 0;
+    }
+    return -4;
+}
+
+int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (max_m < 0 || max_m > 256) return -2;
+    if (max_n < 0 || max_n > 256) return -3;
+    const int base = tier & 0xff;
+    if (base != BSVD_TIER_AUTO && base != BSVD_TIER_REGISTER && base != BSVD_TIER_SHARED) return -4;
+    const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+    g_choice[dtype == BSVD_F64][size_bin(mm)][size_bin(nn)] = base == BSVD_TIER_AUTO ? 0 : tier;
+    return BSVD_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,414 @@
+// jacobi_reg.cu -- one-sided Jacobi SVD with the whole matrix resident in registers
+// (Algorithm 2, Section 2.2; the register tier of Section 4, re-mapped for sm_103a).
+//
+// Layout.  The working matrix W (m x n, or A^T when m < n) and the accumulated rotations V are
+// spread over NS * PARTS lanes: lane (part, slot) holds RA rows (rows part*RA ...) of the two
+// columns that column-pair slot `slot` currently owns, and RV rows of the same two columns of V.
+// A round-robin step therefore processes all NS pairs at once, one pair per lane, with no shared
+// memory traffic: the three Gram dot products are serial partial sums over the lane's rows
+// followed by a reduction across the PARTS lanes of the pair (a shuffle when the parts share a
+// warp, one barrier with a double-buffered exchange slot when they do not).  Each lane then
+// computes its own pair's rotation, so one warp instruction serves NS pairs -- the parameter
+// computation the paper measured as the dominant cost (Section 4.2) is not replicated across a
+// warp.  All parts compute bit-identical parameters from identical sums.
+//
+// Pair ordering.  Odd-even transposition with exchange: 2 NS column positions, even steps pair
+// positions (2k, 2k+1), odd steps (2k+1, 2k+2), and every processed pair swaps positions, so after
+// 2 NS steps each of the 2NS(2NS-1)/2 pairs has met exactly once (one of the parallel orderings
+// Section 5 lists).  Slot k holds the pair it processes; between steps exactly ONE column per slot
+// moves to the neighbouring slot (a warp shuffle), half the traffic of the circle method.
+//
+// Scaled rotations (FAST = true).  Each column carries a scale d (W = W~ diag(d), V = V~ diag(d)).
+// The rotation [w_i, w_j] <- [c w_i - s w_j, s w_i + c w_j] with t = s / c becomes
+//   w~_i <- w~_i - t (d_j / d_i) w~_j,   w~_j <- w~_j + t (d_i / d_j) w~_i,   d_i, d_j <- c d_i, c d_j,
+// one FMA per element instead of two multiplies and two FMAs; the scales are folded back into
+// the columns at the end of every sweep (c >= 1/sqrt 2, so d stays above 2^-33 within a sweep).
+// FAST = false applies the rotation as written.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsvd {
+
+template <typename T>
+struct Red3 {
+    T a, b, c, pad;
+};
+
+// MINB is the number of matrices (CTAs) the launch bound asks to keep resident per SM; it caps
+// the register allocation at 65536 / (NS * PARTS * MINB), trading scheduling freedom against
+// occupancy.  Several values are instantiated and the autotuner picks one per size bin.
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST>
+__global__ void __launch_bounds__(NS * PARTS, MINB)
+    jacobi_reg_kernel(int batch, T* const* A, const int* M, const int* N, const int* LDA, T* const* Sout, T* const* U,
+                      const int* LDU, T* const* V, const int* LDV, double tol_in, int max_sweeps, int* info,
+                      long long* rot_out)
+{
+    constexpr int NT = NS * PARTS;
+    constexpr int PPW = 32 / NS;   // parts per warp (1 or 2)
+    constexpr int NW = NT / 32;    // warps per matrix
+    constexpr int NC = 2 * NS;     // column capacity
+    static_assert(NT % 32 == 0, "whole warps only");
+    typedef T P;                   // rotation parameters in the working precision
+
+    __shared__ Red3<T> red[2][NW > 1 ? NW : 1][32];
+    __shared__ T sig_s[NC];
+    __shared__ int rank_s[NC];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int s = lane % NS;                  // pair slot
+    const int part = warp * PPW + lane / NS;  // row part
+    const unsigned part_mask = PPW == 2 ? (lane < 16 ? 0x0000FFFFu : 0xFFFF0000u) : 0xFFFFFFFFu;
+
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        const int m = M[b], n = N[b], lda = LDA[b];
+        const bool tr = m < n;
+        const int mm = tr ? n : m;
+        const int nn = tr ? m : n;
+        const bool wantU = U != nullptr, wantV = V != nullptr;
+        const int ldu = wantU ? LDU[b] : 1, ldvo = wantV ? LDV[b] : 1;
+        const bool bad = m < 0 || n < 0 || mm > PARTS * RA || nn > NC || nn > PARTS * RV ||
+                         lda < (m > 1 ? m : 1) || (wantU && ldu < (m > 1 ? m : 1)) || (wantV && ldvo < (n > 1 ? n : 1));
+        if (bad) {
+            if (tid == 0) info[b] = BSVD_INFO_BAD_SHAPE;
+            continue;
+        }
+        if (nn == 0) {
+            if (tid == 0) {
+                info[b] = 0;
+                if (rot_out) rot_out[b] = 0;
+            }
+            continue;
+        }
+        const bool accV = tr ? wantU : wantV;
+
+        // ---- load: slot s owns columns (positions) 2s and 2s + 1 ----
+        int colL = 2 * s, colR = 2 * s + 1;
+        T aL[RA], aR[RA], vL[RV], vR[RV];
+        const T* a = A[b];
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+            const int r = part * RA + k;
+            aL[k] = T(0);
+            aR[k] = T(0);
+            if (r < mm) {
+                if (!tr) {
+                    if (colL < nn) aL[k] = a[(size_t)colL * lda + r];
+                    if (colR < nn) aR[k] = a[(size_t)colR * lda + r];
+                } else {
+                    if (colL < nn) aL[k] = a[(size_t)r * lda + colL];
+                    if (colR < nn) aR[k] = a[(size_t)r * lda + colR];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RV; ++k) {
+            const int r = part * RV + k;
+            vL[k] = (r == colL) ? T(1) : T(0);
+            vR[k] = (r == colR) ? T(1) : T(0);
+        }
+        T dL = T(1), dR = T(1), eL = T(1), eR = T(1);  // column scales and their inverses
+
+        const P tol = tol_in > 0.0 ? P(tol_in) : P(dsqrt(double(mm)) * Unit<T>::value);
+        const int sweeps_cap = max_sweeps > 0 ? max_sweeps : 30;
+        int sweep = 0, step_parity = 0;
+        bool converged = false;
+        long long total_rot = 0;
+
+        while (sweep < sweeps_cap) {
+            int rot_sweep = 0;
+#pragma unroll 1
+            for (int st = 0; st < 2 * NS; ++st) {
+                const bool odd = st & 1;
+                // Gram partials over this lane's rows (two accumulators per entry)
+                T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0), c0 = T(0), c1 = T(0);
+#pragma unroll
+                for (int k = 0; k < RA; k += 2) {
+                    a0 = fma(aL[k], aL[k], a0);
+                    b0 = fma(aR[k], aR[k], b0);
+                    c0 = fma(aL[k], aR[k], c0);
+                    if (k + 1 < RA) {
+                        a1 = fma(aL[k + 1], aL[k + 1], a1);
+                        b1 = fma(aR[k + 1], aR[k + 1], b1);
+                        c1 = fma(aL[k + 1], aR[k + 1], c1);
+                    }
+                }
+                T sa = a0 + a1, sb = b0 + b1, sc = c0 + c1;
+                if (PPW == 2) {
+                    sa += __shfl_xor_sync(0xffffffffu, sa, 16);
+                    sb += __shfl_xor_sync(0xffffffffu, sb, 16);
+                    sc += __shfl_xor_sync(0xffffffffu, sc, 16);
+                }
+                if (NW > 1) {
+                    red[step_parity][warp][lane] = Red3<T>{sa, sb, sc, T(0)};
+                    __syncthreads();
+                    sa = sb = sc = T(0);
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        const Red3<T> r = red[step_parity][w][lane];
+                        sa += r.a;
+                        sb += r.b;
+                        sc += r.c;
+                    }
+                    step_parity ^= 1;
+                }
+                // rotation of the pair, in the unscaled frame; the wrap slot idles on odd steps.
+                // t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2))
+                // is the same smaller root as sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with
+                // zeta = (beta - alpha) / (2 gamma), with one division and one square root.
+                const P alpha = FAST ? P(dL) * P(dL) * P(sa) : P(sa);
+                const P beta = FAST ? P(dR) * P(dR) * P(sb) : P(sb);
+                const P gamma = FAST ? P(dL) * P(dR) * P(sc) : P(sc);
+                const bool rot = !(odd && s == NS - 1) && alpha > P(0) && beta > P(0) &&
+                                 off_diagonal_large(alpha, beta, gamma, tol);
+                P tth = P(0), cth = P(1), xth = P(1);
+                if (rot) {
+                    const P d = beta - alpha;
+                    const P r = dsqrt(d * d + P(4) * gamma * gamma);
+                    tth = (d >= P(0) ? P(2) * gamma : P(-2) * gamma) / (dabs(d) + r);
+                    xth = P(1) + tth * tth;
+                    cth = drsqrt(xth);
+                }
+                // unconditional update: a skipped pair has multipliers 0 (and c = 1), which leaves
+                // its columns bit-identical; a warp runs this whenever any of its pairs rotates
+                if (FAST) {
+                    const T mL = -T(tth) * (dR * eL);  // -t d_j / d_i
+                    const T mR = T(tth) * (dL * eR);   //  t d_i / d_j
+#pragma unroll
+                    for (int k = 0; k < RA; ++k) {
+                        const T x = aL[k], y = aR[k];
+                        aL[k] = fma(mL, y, x);
+                        aR[k] = fma(mR, x, y);
+                    }
+                    if (accV) {
+#pragma unroll
+                        for (int k = 0; k < RV; ++k) {
+                            const T x = vL[k], y = vR[k];
+                            vL[k] = fma(mL, y, x);
+                            vR[k] = fma(mR, x, y);
+                        }
+                    }
+                    const T ci = T(xth * cth);  // 1 / c = sqrt(1 + t^2)
+                    dL *= T(cth);
+                    dR *= T(cth);
+                    eL *= ci;
+                    eR *= ci;
+                } else {
+                    const T cc = T(cth), ss = T(cth * tth);
+#pragma unroll
+                    for (int k = 0; k < RA; ++k) {
+                        const T x = aL[k], y = aR[k];
+                        aL[k] = fma(cc, x, -ss * y);
+                        aR[k] = fma(ss, x, cc * y);
+                    }
+                    if (accV) {
+#pragma unroll
+                        for (int k = 0; k < RV; ++k) {
+                            const T x = vL[k], y = vR[k];
+                            vL[k] = fma(cc, x, -ss * y);
+                            vR[k] = fma(ss, x, cc * y);
+                        }
+                    }
+                }
+                rot_sweep += __popc(__ballot_sync(0xffffffffu, rot) & part_mask);
+                // exchange: after the swap the pair's lower position holds the right column
+                if (!odd) {
+                    // even -> odd: the right column moves one slot down (slot s receives s + 1's)
+                    const int src = s + 1 == NS ? 0 : s + 1;
+#pragma unroll
+                    for (int k = 0; k < RA; ++k) aR[k] = __shfl_sync(0xffffffffu, aR[k], src, NS);
+                    if (accV) {
+#pragma unroll
+                        for (int k = 0; k < RV; ++k) vR[k] = __shfl_sync(0xffffffffu, vR[k], src, NS);
+                    }
+                    if (FAST) {
+                        dR = __shfl_sync(0xffffffffu, dR, src, NS);
+                        eR = __shfl_sync(0xffffffffu, eR, src, NS);
+                    }
+                    colR = __shfl_sync(0xffffffffu, colR, src, NS);
+                } else {
+                    // odd -> even: the left column moves one slot up; the wrap slot, which did not
+                    // rotate, hands over its right column and keeps its left one as the right
+                    const int src = s == 0 ? NS - 1 : s - 1;
+                    const bool wrap = s == NS - 1;
+#pragma unroll
+                    for (int k = 0; k < RA; ++k) {
+                        const T r = __shfl_sync(0xffffffffu, wrap ? aR[k] : aL[k], src, NS);
+                        aR[k] = wrap ? aL[k] : aR[k];
+                        aL[k] = r;
+                    }
+                    if (accV) {
+#pragma unroll
+                        for (int k = 0; k < RV; ++k) {
+                            const T r = __shfl_sync(0xffffffffu, wrap ? vR[k] : vL[k], src, NS);
+                            vR[k] = wrap ? vL[k] : vR[k];
+                            vL[k] = r;
+                        }
+                    }
+                    if (FAST) {
+                        const T r = __shfl_sync(0xffffffffu, wrap ? dR : dL, src, NS);
+                        dR = wrap ? dL : dR;
+                        dL = r;
+                        const T q = __shfl_sync(0xffffffffu, wrap ? eR : eL, src, NS);
+                        eR = wrap ? eL : eR;
+                        eL = q;
+                    }
+                    const int rc = __shfl_sync(0xffffffffu, wrap ? colR : colL, src, NS);
+                    colR = wrap ? colL : colR;
+                    colL = rc;
+                }
+            }
+            if (FAST) {
+                // fold the scales back into the columns
+#pragma unroll
+                for (int k = 0; k < RA; ++k) {
+                    aL[k] *= dL;
+                    aR[k] *= dR;
+                }
+                if (accV) {
+#pragma unroll
+                    for (int k = 0; k < RV; ++k) {
+                        vL[k] *= dL;
+                        vR[k] *= dR;
+                    }
+                }
+                dL = dR = eL = eR = T(1);
+            }
+            ++sweep;
+            total_rot += rot_sweep;
+            if (rot_sweep == 0) {
+                converged = true;
+                break;
+            }
+        }
+
+        // ---- sigma = column norms (reduced across parts like the Gram entries) ----
+        T na = T(0), nb = T(0);
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+            na = fma(aL[k], aL[k], na);
+            nb = fma(aR[k], aR[k], nb);
+        }
+        if (PPW == 2) {
+            na += __shfl_xor_sync(0xffffffffu, na, 16);
+            nb += __shfl_xor_sync(0xffffffffu, nb, 16);
+        }
+        if (NW > 1) {
+            red[step_parity][warp][lane] = Red3<T>{na, nb, T(0), T(0)};
+            __syncthreads();
+            na = nb = T(0);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                na += red[step_parity][w][lane].a;
+                nb += red[step_parity][w][lane].b;
+            }
+        }
+        const T sgL = dsqrt(na), sgR = dsqrt(nb);
+        if (part == 0) {
+            sig_s[colL] = sgL;
+            sig_s[colR] = sgR;
+        }
+        __syncthreads();
+        int rkL = 0, rkR = 0;
+        for (int i = 0; i < nn; ++i) {
+            const T si = sig_s[i];
+            rkL += (si > sgL) || (si == sgL && i < colL);
+            rkR += (si > sgR) || (si == sgR && i < colR);
+        }
+        T* s_out = Sout[b];
+        if (part == 0) {
+            if (colL < nn) s_out[rkL] = sgL;
+            if (colR < nn) s_out[rkR] = sgR;
+        }
+        T* uw = tr ? (wantV ? V[b] : nullptr) : (wantU ? U[b] : nullptr);  // receives W / sigma
+        const int lduw = tr ? ldvo : ldu;
+        T* vw = tr ? (wantU ? U[b] : nullptr) : (wantV ? V[b] : nullptr);  // receives V
+        const int ldvw = tr ? ldu : ldvo;
+        if (uw) {
+            const T iL = sgL > T(0) ? T(1) / sgL : T(0), iR = sgR > T(0) ? T(1) / sgR : T(0);
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                const int r = part * RA + k;
+                if (r < mm) {
+                    if (colL < nn) uw[(size_t)rkL * lduw + r] = aL[k] * iL;
+                    if (colR < nn) uw[(size_t)rkR * lduw + r] = aR[k] * iR;
+                }
+            }
+        }
+        if (vw) {
+#pragma unroll
+            for (int k = 0; k < RV; ++k) {
+                const int r = part * RV + k;
+                if (r < nn) {
+                    if (colL < nn) vw[(size_t)rkL * ldvw + r] = vL[k];
+                    if (colR < nn) vw[(size_t)rkR * ldvw + r] = vR[k];
+                }
+            }
+        }
+        if (tid == 0) {
+            info[b] = converged ? sweep : BSVD_INFO_NOT_CONVERGED + sweep;
+            if (rot_out) rot_out[b] = total_rot;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST>
+static int launch_reg(int batch, void* const* A, const int* M, const int* N, const int* LDA, void* const* S,
+                      void* const* U, const int* LDU, void* const* V, const int* LDV, double tol, int max_sweeps,
+                      int* info, long long* rot, cudaStream_t st)
+{
+    const int grid = batch < (1 << 30) ? batch : (1 << 30);
+    jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST><<<grid, NS * PARTS, 0, st>>>(
+        batch, (T* const*)A, M, N, LDA, (T* const*)S, (T* const*)U, LDU, (T* const*)V, LDV, tol, max_sweeps, info, rot);
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
+
+// Register-tier variants (slots, row parts, A rows per lane, V rows per lane, resident CTAs), in
+// order of preference.  `variant` 0 launches the first that fits the shape bound; k > 0 launches
+// the k-th fitting one; a negative `variant` only counts the fitting ones (returned).
+template <typename T>
+int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
+                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st)
+{
+    const int mm = max_m > max_n ? max_m : max_n;
+    const int nn = max_m > max_n ? max_n : max_m;
+    int seen = 0;
+#define BSVD_TRY(NS_, PARTS_, RA_, RV_, MINB_, FAST_)                                                                \
+    if (nn <= 2 * NS_ && mm <= PARTS_ * RA_ && nn <= PARTS_ * RV_) {                                         \
+        ++seen;                                                                                             \
+        if (variant == 0 || variant == seen)                                                                \
+            return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_>(batch, A, M, N, LDA, S, U, LDU, V, LDV, tol,     \
+                                                               max_sweeps, info, rot, st);                  \
+    }
+    if constexpr (sizeof(T) == 4) {
+        BSVD_TRY(16, 2, 16, 16, 16, true)   // n <= 32, m <= 32: one warp per matrix
+        BSVD_TRY(16, 2, 32, 16, 12, true)   // n <= 32, m <= 64
+        BSVD_TRY(32, 2, 32, 32, 6, true)    // n <= 64, m <= 64: two warps, 3 warps per SM sub-partition
+        BSVD_TRY(32, 2, 32, 32, 4, true)    //   ... 2 warps per sub-partition, no register cap
+        BSVD_TRY(32, 2, 32, 32, 6, false)   //   ... rotations applied as written
+        BSVD_TRY(32, 4, 16, 16, 4, true)    //   ... four warps, 128-register cap
+        BSVD_TRY(16, 4, 32, 8, 4, true)     // n <= 32, m <= 128
+        BSVD_TRY(32, 4, 32, 16, 2, true)    // n <= 64, m <= 128
+    } else {
+        BSVD_TRY(16, 2, 16, 16, 8, true)    // n <= 32, m <= 32: one warp per matrix
+        BSVD_TRY(16, 2, 16, 16, 8, false)
+        BSVD_TRY(16, 2, 16, 16, 12, true)
+        BSVD_TRY(16, 4, 16, 8, 5, true)     // n <= 32, m <= 64
+        BSVD_TRY(32, 4, 16, 16, 2, true)    // n <= 64, m <= 64
+    }
+#undef BSVD_TRY
+    return variant < 0 ? seen : BSVD_ERR_UNSUPPORTED;
+}
+
+template int launch_jacobi_reg<float>(int, int, int, int, void* const*, const int*, const int*, const int*,
+                                      void* const*, void* const*, const int*, void* const*, const int*, double, int,
+                                      int*, long long*, cudaStream_t);
+template int launch_jacobi_reg<double>(int, int, int, int, void* const*, const int*, const int*, const int*,
+                                       void* const*, void* const*, const int*, void* const*, const int*, double, int,
+                                       int*, long long*, cudaStream_t);
+
+}  // namespace bsvd

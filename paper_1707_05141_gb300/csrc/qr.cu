@@ -1,0 +1,136 @@
+// qr.cu -- batched Householder QR (Algorithm 1, Section 2.1; batched kernel of Section 3.1).
+//
+// One CTA per matrix.  The m x n matrix is staged once in shared memory with coalesced column
+// loads and factored there: for each column a single warp forms the reflector (norm by a warp
+// shuffle reduction, as in Section 3.1), then all warps apply it to the trailing columns, one
+// warp per column: the transpose-matrix-vector product M^T v is a warp reduction per column
+// followed by the rank-1 update.  R is written straight from shared memory; Q is formed in the
+// same buffer by backward accumulation of the reflectors (Q = H_0 H_1 ... H_{n-1} [I; 0]), each
+// reflector consumed in place as its column of Q is produced, so shared memory holds one m x n
+// matrix plus n diagonal entries.  Nothing goes to global memory but the outputs.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsvd {
+
+template <typename T>
+__global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const int* M, const int* N,
+                          const int* LDA, T* const* Q, const int* LDQ, T* const* R, const int* LDR,
+                          int* info)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    const int ld = max_m;
+    T* diag = S + (size_t)ld * max_n;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+
+    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+        const int m = M[b], n = N[b], lda = LDA[b];
+        const int ldq = Q ? LDQ[b] : m, ldr = R ? LDR[b] : n;
+        const bool bad = m < 0 || n < 0 || m < n || m > max_m || n > max_n || lda < (m > 1 ? m : 1) ||
+                         (Q && ldq < (m > 1 ? m : 1)) || (R && ldr < (n > 1 ? n : 1));
+        if (bad) {
+            if (tid == 0) info[b] = BSVD_INFO_BAD_SHAPE;
+            continue;
+        }
+        if (tid == 0) info[b] = 0;
+        if (n == 0) continue;
+        const T* a = A[b];
+        for (int j = warp; j < n; j += nwarps)
+            for (int i = lane; i < m; i += 32) S[j * ld + i] = a[(size_t)j * lda + i];
+        __syncthreads();
+
+        // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
+        for (int i = 0; i < n; ++i) {
+            T* col = S + i * ld;
+            if (warp == 0) {
+                const T x0 = col[i];  // read by every lane before the shuffles below
+                T ss = T(0);
+                for (int r = i + lane; r < m; r += 32) ss += col[r] * col[r];
+                ss = warp_sum(ss);
+                const T alpha = dsqrt(ss);
+                if (alpha > T(0)) {
+                    const T sg = x0 >= T(0) ? T(1) : T(-1);
+                    // ||x + sign(x0) alpha e1||^2 = 2 alpha (alpha + |x0|)
+                    const T inv = drsqrt(T(2) * alpha * (alpha + dabs(x0)));
+                    for (int r = i + lane; r < m; r += 32) col[r] = (r == i ? x0 + sg * alpha : col[r]) * inv;
+                    if (lane == 0) diag[i] = -sg * alpha;
+                } else if (lane == 0) {
+                    diag[i] = T(0);  // zero column: v = 0 (already zero), identity reflector
+                }
+            }
+            __syncthreads();
+            for (int j = i + 1 + warp; j < n; j += nwarps) {
+                T* cj = S + j * ld;
+                T w = T(0);
+                for (int r = i + lane; r < m; r += 32) w += col[r] * cj[r];
+                w = T(2) * warp_sum(w);
+                for (int r = i + lane; r < m; r += 32) cj[r] -= w * col[r];
+            }
+            __syncthreads();
+        }
+
+        // ---- R: strict upper part from S, diagonal from diag, zeros below ----
+        if (R) {
+            T* r_out = R[b];
+            for (int j = warp; j < n; j += nwarps)
+                for (int i = lane; i < n; i += 32)
+                    r_out[(size_t)j * ldr + i] = i < j ? S[j * ld + i] : (i == j ? diag[j] : T(0));
+        }
+        __syncthreads();
+
+        // ---- Q = H_0 ... H_{n-1} [I; 0], backward, in place ----
+        if (Q) {
+            for (int i = n - 1; i >= 0; --i) {
+                const T* col = S + i * ld;
+                for (int j = i + 1 + warp; j < n; j += nwarps) {
+                    T* cj = S + j * ld;
+                    T w = T(0);
+                    for (int r = i + lane; r < m; r += 32) w += col[r] * cj[r];
+                    w = T(2) * warp_sum(w);
+                    for (int r = i + lane; r < m; r += 32) cj[r] -= w * col[r];
+                }
+                const T v0 = col[i];
+                __syncthreads();
+                // column i of Q: H_i e_i = e_i - 2 v0 v on rows >= i, zero above
+                for (int r = tid; r < m; r += blockDim.x) {
+                    const T vr = S[i * ld + r];
+                    S[i * ld + r] = r < i ? T(0) : ((r == i ? T(1) : T(0)) - T(2) * v0 * vr);
+                }
+                __syncthreads();
+            }
+            T* q_out = Q[b];
+            for (int j = warp; j < n; j += nwarps)
+                for (int i = lane; i < m; i += 32) q_out[(size_t)j * ldq + i] = S[j * ld + i];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st)
+{
+    const size_t smem = ((size_t)max_m * max_n + max_n) * sizeof(T);
+    const int threads = max_n <= 32 ? 128 : 256;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return BSVD_ERR_CUDA;
+    }
+    const int grid = batch < (1 << 30) ? batch : (1 << 30);
+    qr_kernel<T><<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ,
+                                              (T* const*)R, LDR, info);
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
+
+template int launch_qr<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
+                              const int*, void* const*, const int*, int*, cudaStream_t);
+template int launch_qr<double>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
+                               const int*, void* const*, const int*, int*, cudaStream_t);
+
+}  // namespace bsvd

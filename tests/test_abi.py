@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every function that include/*.h declares (CPU only).
+
+Only host-side argument checks are called here: they return before any CUDA call.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DECL = re.compile(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", re.M)
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = re.sub(r"^\s*#[^\n]*", "", text, flags=re.M)
+        for m in DECL.finditer(text):
+            if m.group(1) not in ("if", "while", "for", "return", "sizeof"):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1707_05141_gb300 as bs
+    path = bs.build()
+    return ctypes.CDLL(path), bs
+
+
+def test_header_declares_the_three_entry_points():
+    names = declared_functions()
+    for want in ("batched_qr", "batched_svd_jacobi", "bsvd_version"):
+        assert want in names, names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L, _ = lib
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_version_string(lib):
+    _, bs = lib
+    assert "sm_103a" in bs.version()
+
+
+def test_host_argument_checks_without_gpu(lib):
+    _, bs = lib
+    L = bs.lib()
+    z = None
+    assert L.batched_qr(9, 1, 4, 4, z, z, z, z, z, z, z, z, z, z) == -1
+    assert L.batched_qr(0, -3, 4, 4, z, z, z, z, z, z, z, z, z, z) == -2
+    assert L.batched_qr(0, 1, 4, 8, z, z, z, z, z, z, z, z, z, z) == -4        # max_n > max_m
+    assert L.batched_qr(0, 0, 4, 4, z, z, z, z, z, z, z, z, z, z) == 0         # empty batch: no-op
+    assert L.batched_svd_jacobi(5, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 0, z, z, z) == -1
+    assert L.batched_svd_jacobi(0, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 99, z, z, z) == -16
+    assert L.batched_svd_jacobi(0, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 0, z, z, z) == -5
+    assert L.batched_svd_jacobi(1, 0, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 0, z, z, z) == 0
+    assert L.batched_svd_jacobi(0, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 2 | (1 << 8), z, z, z) == -16
+
+
+def test_variant_counts_and_tuning_table(lib):
+    _, bs = lib
+    L = bs.lib()
+    assert L.bsvd_jacobi_variants(0, 64, 64, bs.TIER_REGISTER) >= 2
+    assert L.bsvd_jacobi_variants(1, 32, 32, bs.TIER_REGISTER) >= 1
+    assert L.bsvd_jacobi_variants(0, 256, 256, bs.TIER_REGISTER) == 0
+    assert L.bsvd_jacobi_variants(0, 256, 128, bs.TIER_SHARED) == 1
+    assert L.bsvd_jacobi_variants(1, 256, 128, bs.TIER_SHARED) == 0
+    assert L.bsvd_jacobi_variants(3, 8, 8, bs.TIER_SHARED) == -1
+    assert L.bsvd_set_jacobi_choice(0, 64, 64, bs.TIER_REGISTER | (2 << 8)) == 0
+    assert L.bsvd_set_jacobi_choice(0, 64, 64, bs.TIER_AUTO) == 0
+    assert L.bsvd_set_jacobi_choice(0, 512, 64, bs.TIER_AUTO) == -2
+    assert L.bsvd_set_jacobi_choice(0, 64, 64, 7) == -4

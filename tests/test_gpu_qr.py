@@ -1,0 +1,157 @@
+"""GPU parity: batched Householder QR (Algorithm 1) through the C ABI vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+from parity import qr_errors, unit
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_1707_05141_gb300 as bs
+    bs.build()
+    assert torch.cuda.is_available()
+    return bs
+
+
+def _host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _check_uniform(bs, batch_obj, idx, dtype):
+    dev = torch.device("cuda")
+    a = torch.from_numpy(batch_obj.a).to(dev)
+    q, r, info = bs.qr(a)
+    torch.cuda.synchronize()
+    assert np.all(info.cpu().numpy() == 0)
+    mats = [batch_obj.a64(i) for i in idx]
+    Qo, Ro, _ = O.qr_batch(mats)
+    qh, rh = _host(q), _host(r)
+    u = unit(dtype)
+    for j, i in enumerate(idx):
+        e = qr_errors(mats[j], qh[i].T, rh[i].T, Qo[j], Ro[j], dtype)
+        assert e["r"] <= 1.0 and e["q"] <= 1.0, (i, e)
+        assert e["tril_zero"]
+        assert e["orth_q"] <= 64 * u * batch_obj.m and e["resid"] <= 64 * u * batch_obj.m, (i, e)
+
+
+def test_qr_fp64_32x32_full_batch(bs):
+    """1000 FP64 32 x 32 matrices, sigma_i = 10^(-8 i/31): every matrix against the oracle."""
+    b = gen.workload0(batch=1000)
+    _check_uniform(bs, b, range(1000), np.float64)
+
+
+def test_qr_fp32_128x32_full_batch_sampled(bs):
+    """20000 FP32 128 x 32 matrices in one launch; 96 sampled matrices checked."""
+    b = gen.workload1_qr(batch=20000)
+    idx = list(range(0, 20000, 20000 // 64))[:64] + list(range(19968, 20000))
+    _check_uniform(bs, b, idx, np.float32)
+
+
+RAGGED = [(1, 1), (2, 1), (7, 3), (33, 33), (64, 1), (100, 37), (129, 64), (5, 0), (0, 0), (31, 31), (48, 17),
+          (256, 96)]
+
+
+@pytest.mark.parametrize("dt,shapes", [(np.float32, RAGGED), (np.float64, RAGGED),
+                                       (np.float32, [(256, 192), (255, 191), (3, 2)]),    # 200 KiB in shared memory
+                                       (np.float32, [(1024, 16), (1000, 15), (17, 16)]),  # tallest supported
+                                       (np.float64, [(1024, 24), (512, 20)])])
+def test_qr_ragged_shapes_and_edges(bs, dt, shapes):
+    rng = np.random.default_rng(7)
+    mats = [rng.standard_normal(sh) * 10.0 ** rng.uniform(-2, 2) for sh in shapes]
+    special = set()
+    if shapes is RAGGED:
+        mats[3][:, 5] = 0.0                  # a zero column: identity reflector
+        mats[5][:, 10] = mats[5][:, 2]      # repeated column: R is rank deficient
+        special = {3, 5}
+    ms = np.array([s[0] for s in shapes], np.int32)
+    ns = np.array([s[1] for s in shapes], np.int32)
+    sizes = (ms.astype(np.int64) * ns + 1)
+    off = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    flat = np.zeros(int(sizes.sum()), dt)
+    for a, o in zip(mats, off):
+        flat[o:o + a.size] = a.T.reshape(-1).astype(dt)
+    offq = off.copy()
+    r_sizes = ns.astype(np.int64) ** 2 + 1
+    offr = np.concatenate([[0], np.cumsum(r_sizes)[:-1]])
+    dev = torch.device("cuda")
+    fa = torch.from_numpy(flat).to(dev)
+    fq = torch.full_like(fa, float("nan"))
+    fr = torch.full((int(r_sizes.sum()),), float("nan"), dtype=fa.dtype, device=dev)
+    A = bs.Batch.packed(fa, off, ms, ns)
+    Q = bs.Batch.packed(fq, offq, ms, ns)
+    R = bs.Batch.packed(fr, offr, ns, ns)
+    info = torch.empty(len(shapes), dtype=torch.int32, device=dev)
+    bs.batched_qr(A, Q, R, info)
+    torch.cuda.synchronize()
+    assert np.all(info.cpu().numpy() == 0)
+    fqh, frh = fq.cpu().numpy().astype(np.float64), fr.cpu().numpy().astype(np.float64)
+    for b, ((m, n), a) in enumerate(zip(shapes, mats)):
+        if n == 0:
+            continue
+        a64 = flat[off[b]:off[b] + m * n].reshape(n, m).T.astype(np.float64)
+        qg = fqh[offq[b]:offq[b] + m * n].reshape(n, m).T
+        rg = frh[offr[b]:offr[b] + n * n].reshape(n, n).T
+        qo, ro = O.qr(a64)
+        e = qr_errors(a64, qg, rg, qo, ro, dt)
+        assert e["tril_zero"], (shapes[b], e)
+        if b not in special:                 # rank deficient: trailing rows of R are not unique
+            assert e["r"] <= 1.0, (shapes[b], e)
+        u = unit(dt)
+        assert e["orth_q"] <= 64 * u * max(m, 8), (shapes[b], e)
+        assert e["resid"] <= 64 * u * max(m, 8), (shapes[b], e)
+        if "q" in e and b not in special:   # rank-deficient cases: Q not unique
+            assert e["q"] <= 1.0, (shapes[b], e)
+
+
+def test_qr_bad_shapes_flagged_and_neighbours_intact(bs):
+    dev = torch.device("cuda")
+    shapes = [(4, 6), (8, 4), (3, 3)]            # m < n is invalid for QR
+    ms = np.array([s[0] for s in shapes], np.int32)
+    ns = np.array([s[1] for s in shapes], np.int32)
+    off = np.array([0, 64, 128])
+    rng = np.random.default_rng(0)
+    flat = rng.standard_normal(192).astype(np.float32)
+    fa = torch.from_numpy(flat).to(dev)
+    fq = torch.zeros_like(fa)
+    fr = torch.zeros(192, dtype=torch.float32, device=dev)
+    info = torch.empty(3, dtype=torch.int32, device=dev)
+    bs.batched_qr(bs.Batch.packed(fa, off, ms, ns), bs.Batch.packed(fq, off, ms, ns),
+                  bs.Batch.packed(fr, off, ns, ns), info)
+    torch.cuda.synchronize()
+    inf = info.cpu().numpy()
+    assert inf[0] == bs.INFO_BAD_SHAPE and inf[1] == 0 and inf[2] == 0
+    assert np.all(fq.cpu().numpy()[:24] == 0)  # the invalid matrix's outputs untouched
+
+
+def test_qr_host_argument_errors(bs):
+    dev = torch.device("cuda")
+    a = torch.zeros((2, 4, 8), device=dev)
+    A = bs.Batch.uniform(a, 8, 4)
+    info = torch.empty(2, dtype=torch.int32, device=dev)
+    L = bs.lib()
+    assert L.batched_qr(7, 2, 8, 4, None, None, None, None, None, None, None, None, None, None) == -1
+    assert L.batched_qr(0, -1, 8, 4, None, None, None, None, None, None, None, None, None, None) == -2
+    assert L.batched_qr(0, 2, 8, 4, None, None, None, None, None, None, None, None, None, None) == -5
+    with pytest.raises(bs.BsvdError):
+        bs.batched_qr(A, None, None, None)           # d_info missing -> argument 13
+    assert bs.lib().batched_qr(0, 2, 8, 9, A.ptrs.data_ptr(), A.m.data_ptr(), A.n.data_ptr(), A.ld.data_ptr(),
+                               None, None, None, None, info.data_ptr(), None) == -4
+    assert bs.lib().batched_qr(0, 2, 2048, 4, A.ptrs.data_ptr(), A.m.data_ptr(), A.n.data_ptr(), A.ld.data_ptr(),
+                               None, None, None, None, info.data_ptr(), None) == bs.ERR_UNSUPPORTED
+    assert bs.lib().batched_qr(0, 0, 8, 4, None, None, None, None, None, None, None, None, None, None) == 0
+
+
+def test_qr_r_only_and_q_only(bs):
+    b = gen.workload1_qr(batch=16)
+    dev = torch.device("cuda")
+    a = torch.from_numpy(b.a).to(dev)
+    q1, r1, _ = bs.qr(a)
+    _, r2, _ = bs.qr(a, want_q=False)
+    q3, _, _ = bs.qr(a, want_r=False)
+    torch.cuda.synchronize()
+    assert torch.equal(r1, r2) and torch.equal(q1, q3)
