@@ -40,6 +40,7 @@ extern "C" {
 #define BSVD_SUCCESS 0
 #define BSVD_ERR_UNSUPPORTED (-1000)
 #define BSVD_ERR_CUDA (-1001)
+#define BSVD_ERR_WORKSPACE (-1002) /* workspace smaller than the matching *_workspace query */
 
 /* per-matrix info */
 #define BSVD_INFO_BAD_SHAPE (-1)
@@ -123,6 +124,51 @@ int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier);
  * (This tuning table is the project's addition: the paper tunes its kernels by hand, Sections 3-5.)
  */
 int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
+
+/* Block-Jacobi methods (argument `method` of batched_svd_block_jacobi), Algorithm 3 */
+#define BSVD_BLOCK_GRAM 0   /* Section 6.1: pair Gram matrix G, its eigenvectors as the block rotation */
+#define BSVD_BLOCK_DIRECT 1 /* Section 6.2: pair QR, SVD of the triangular factor */
+
+/*
+ * batched_svd_block_jacobi_workspace -- bytes of DEVICE workspace batched_svd_block_jacobi needs
+ * for these bounds, block width and method (0 for invalid arguments).  Host only.
+ */
+size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int max_n, int block_width,
+                                          int method);
+
+/*
+ * batched_svd_block_jacobi -- reduced SVD by one-sided block Jacobi in global memory (Algorithm 3,
+ * Section 6), for matrices too large for the register and shared-memory tiers.
+ *
+ * Arguments as batched_svd_jacobi, except:
+ *   dU[b], dV[b]  REQUIRED: they double as the working storage (the working matrix A, or A^T when
+ *                 m < n, lives in U, or V, and the rotations accumulate in the other one).
+ *   tol           pair threshold: a block pair is rotated when its largest scaled off-diagonal
+ *                 |G_pq| / sqrt(G_pp G_qq) exceeds tol (tested in FP64); tol <= 0 selects
+ *                 sqrt(max(m, n)) * u.  The same threshold drives the inner 2bw x 2bw Jacobi.
+ *   max_sweeps    block sweeps launched (<= 0 selects 20); converged matrices skip the rest.
+ *   block_width   bw = 16 or 32 columns per block (the paper uses 32, Section 6.3).
+ *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
+ *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
+ *                 DIRECT needs max(m, n) * 2 bw * sizeof(element) <= 200 KiB (the pair's QR runs on
+ *                 chip); its default tol is 8 sqrt(max(m, n)) u, since its rotations are only as
+ *                 orthogonal as the pair's Householder Q.
+ *   workspace     DEVICE buffer of at least batched_svd_block_jacobi_workspace(...) bytes, owned by
+ *                 the caller, contents need not be initialised; not used after the stream work
+ *                 completes.  Smaller -> BSVD_ERR_WORKSPACE.
+ *   d_info[b]     block sweeps run (the last one rotates no pair), or BSVD_INFO_NOT_CONVERGED +
+ *                 sweeps, or BSVD_INFO_BAD_SHAPE.
+ *   d_rotations[b] (nullable) number of block-pair rotations applied.
+ * Limits: max(m, n) <= 16384.  Host launches max_sweeps * (nb - 1) steps without synchronising.
+ */
+int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n,
+                             void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+                             void* const* dS,
+                             void* const* dU, const int* d_ldu,
+                             void* const* dV, const int* d_ldv,
+                             double tol, int max_sweeps, int block_width, int method,
+                             int* d_info, long long* d_rotations,
+                             void* workspace, size_t workspace_bytes, void* stream);
 
 /* Library version and build description (static strings). */
 const char* bsvd_version(void);

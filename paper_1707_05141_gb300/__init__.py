@@ -18,6 +18,8 @@ F32, F64 = 0, 1
 SUCCESS = 0
 ERR_UNSUPPORTED = -1000
 ERR_CUDA = -1001
+ERR_WORKSPACE = -1002
+BLOCK_GRAM, BLOCK_DIRECT = 0, 1
 INFO_BAD_SHAPE = -1
 INFO_NOT_CONVERGED = 1 << 20
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
@@ -30,7 +32,8 @@ class BsvdError(RuntimeError):
     """A non-zero status returned by an entry point of libbsvd.so."""
 
     def __init__(self, fn: str, code: int):
-        what = {ERR_UNSUPPORTED: "unsupported shape", ERR_CUDA: "CUDA launch failure"}.get(code)
+        what = {ERR_UNSUPPORTED: "unsupported shape", ERR_CUDA: "CUDA launch failure",
+                ERR_WORKSPACE: "workspace too small"}.get(code)
         super().__init__(f"{fn} returned {code}" + (f" ({what})" if what else f" (argument {-code} invalid)"))
         self.code = code
 
@@ -54,6 +57,11 @@ def lib() -> ctypes.CDLL:
             L.bsvd_jacobi_variants.argtypes = [i, i, i, i]
             L.bsvd_set_jacobi_choice.restype = i
             L.bsvd_set_jacobi_choice.argtypes = [i, i, i, i]
+            L.batched_svd_block_jacobi_workspace.restype = ctypes.c_size_t
+            L.batched_svd_block_jacobi_workspace.argtypes = [i, i, i, i, i, i]
+            L.batched_svd_block_jacobi.restype = i
+            L.batched_svd_block_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p, p,
+                                                   ctypes.c_size_t, p]
             _lib = L
     return _lib
 
@@ -172,6 +180,22 @@ def batched_svd_jacobi(A: Batch, S: Batch, U: Batch | None, V: Batch | None, inf
     _check("batched_svd_jacobi", rc)
 
 
+def batched_svd_block_jacobi_workspace(A: Batch, block_width: int = 32, method: int = BLOCK_GRAM) -> int:
+    """Workspace bytes batched_svd_block_jacobi needs for this batch's bounds."""
+    return int(lib().batched_svd_block_jacobi_workspace(A.code, A.batch, A.max_m, A.max_n, block_width, method))
+
+
+def batched_svd_block_jacobi(A: Batch, S: Batch, U: Batch, V: Batch, info, workspace, rotations=None,
+                             tol: float = 0.0, max_sweeps: int = 0, block_width: int = 32,
+                             method: int = BLOCK_GRAM, stream=None) -> None:
+    """Reduced SVD by one-sided block Jacobi (Algorithm 3); ``workspace`` a device uint8 tensor."""
+    rc = lib().batched_svd_block_jacobi(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n),
+                                        _ptr(A.ld), _ptr(S.ptrs), _ptr(U.ptrs), _ptr(U.ld), _ptr(V.ptrs), _ptr(V.ld),
+                                        float(tol), int(max_sweeps), int(block_width), int(method), _ptr(info),
+                                        _ptr(rotations), _ptr(workspace), int(workspace.numel()), _stream_ptr(stream))
+    _check("batched_svd_block_jacobi", rc)
+
+
 # ----------------------------------------------------------------------------------------------
 # conveniences that allocate the outputs with torch (uniform batches)
 # ----------------------------------------------------------------------------------------------
@@ -204,4 +228,22 @@ def svd(a, want_u: bool = True, want_v: bool = True, tol: float = 0.0, max_sweep
     rots = torch.empty(bsz, device=a.device, dtype=torch.int64)
     batched_svd_jacobi(A, Batch.uniform(s, k, 1), Batch.uniform(u, m, k) if want_u else None,
                        Batch.uniform(v, n, k) if want_v else None, info, rots, tol, max_sweeps, tier, stream)
+    return u, s.view(bsz, k), v, info, rots
+
+
+def svd_block(a, block_width: int = 32, method: int = BLOCK_GRAM, tol: float = 0.0, max_sweeps: int = 0,
+              stream=None):
+    """Block-Jacobi SVD of a uniform batch ``a`` (batch, n, m) -> (U, S, V, info, rotations)."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    k = min(m, n)
+    A = Batch.uniform(a.contiguous(), m, n)
+    s = torch.empty((bsz, 1, k), device=a.device, dtype=a.dtype)
+    u = torch.empty((bsz, k, m), device=a.device, dtype=a.dtype)
+    v = torch.empty((bsz, k, n), device=a.device, dtype=a.dtype)
+    info = torch.empty(bsz, device=a.device, dtype=torch.int32)
+    rots = torch.empty(bsz, device=a.device, dtype=torch.int64)
+    ws = torch.empty(batched_svd_block_jacobi_workspace(A, block_width, method), device=a.device, dtype=torch.uint8)
+    batched_svd_block_jacobi(A, Batch.uniform(s, k, 1), Batch.uniform(u, m, k), Batch.uniform(v, n, k), info, ws,
+                             rots, tol, max_sweeps, block_width, method, stream)
     return u, s.view(bsz, k), v, info, rots

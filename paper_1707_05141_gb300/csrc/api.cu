@@ -16,6 +16,13 @@ template <typename T>
 int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
                        int max_sweeps, int* info, long long* rot, cudaStream_t st);
+template <typename T>
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
+template <typename T>
+int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
+                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
 }  // namespace bsvd
 
 using namespace bsvd;
@@ -63,7 +70,7 @@ extern "C" {
 
 const char* bsvd_version(void)
 {
-    return "bsvd-gb300 0.2 (sm_103a; batched Householder QR, register/shared one-sided Jacobi SVD)";
+    return "bsvd-gb300 0.3 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD)";
 }
 
 int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
@@ -149,6 +156,49 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier)
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
     g_choice[dtype == BSVD_F64][size_bin(mm)][size_bin(nn)] = base == BSVD_TIER_AUTO ? 0 : tier;
     return BSVD_SUCCESS;
+}
+
+size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int max_n, int block_width, int method)
+{
+    if ((dtype != BSVD_F32 && dtype != BSVD_F64) || batch < 0 || max_m < 0 || max_n < 0) return 0;
+    const int base = method & 0xff;
+    if ((block_width != 16 && block_width != 32) || (base != BSVD_BLOCK_GRAM && base != BSVD_BLOCK_DIRECT)) return 0;
+    return dtype == BSVD_F32 ? block_jacobi_workspace<float>(batch, max_m, max_n, block_width, base)
+                             : block_jacobi_workspace<double>(batch, max_m, max_n, block_width, base);
+}
+
+int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m,
+                             const int* d_n, const int* d_lda, void* const* dS, void* const* dU, const int* d_ldu,
+                             void* const* dV, const int* d_ldv, double tol, int max_sweeps, int block_width,
+                             int method, int* d_info, long long* d_rotations, void* workspace, size_t workspace_bytes,
+                             void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0) return -4;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (!dS) return -9;
+    if (!dU) return -10;
+    if (!d_ldu) return -11;
+    if (!dV) return -12;
+    if (!d_ldv) return -13;
+    if (!(tol == tol)) return -14;
+    if (block_width != 16 && block_width != 32) return -16;
+    if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
+    if (!d_info) return -18;
+    if (!workspace) return -20;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32
+               ? launch_block_jacobi<float>(batch, max_m, max_n, block_width, method, dA, d_m, d_n, d_lda, dS, dU, d_ldu,
+                                            dV, d_ldv, tol, max_sweeps, d_info, d_rotations, workspace, workspace_bytes, st)
+               : launch_block_jacobi<double>(batch, max_m, max_n, block_width, method, dA, d_m, d_n, d_lda, dS, dU,
+                                             d_ldu, dV, d_ldv, tol, max_sweeps, d_info, d_rotations, workspace,
+                                             workspace_bytes, st);
 }
 
 }  // extern "C"

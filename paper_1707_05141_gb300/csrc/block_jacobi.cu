@@ -1,0 +1,631 @@
+// block_jacobi.cu -- batched one-sided block Jacobi SVD for matrices that live in global memory
+// (Algorithm 3, Section 6).
+//
+// The working matrix W (A, or A^T when m < n, copied into the caller's U or V output) is split into
+// nb column blocks of width bw.  A sweep visits every block pair once in round-robin order (nb - 1
+// steps of nb/2 disjoint pairs, Section 5's ordering applied to blocks), and every step runs three
+// batched stages over all (matrix, pair) items at once:
+//   GRAM   : G = [W_i W_j]^T [W_i W_j] (2bw x 2bw), FP32 dot products, then e_l = the largest
+//            |G_pq| / sqrt(G_pp G_qq) in FP64 (the paper's scaledOffdiag, Section 6.1).  A pair with
+//            e_l <= tol is already orthogonal and is skipped by the next stages.
+//   DIRECT : [W_i W_j] = Q R by the batched Householder QR, and R goes to the inner SVD instead of
+//            G (Section 6.2): robust for ill-conditioned blocks, where G loses the small singular
+//            values (Section 6.3).
+//   inner  : one-sided Jacobi of the 2bw x 2bw G (or R) with the register-tier kernel, which
+//            returns the accumulated rotation (eigenvectors of G; right singular vectors of R).
+//   polish : one Newton-Schulz step makes X orthogonal to rounding level (see bj_polish_kernel).
+//   update : [W_i W_j] <- [W_i W_j] X (GRAM, X = accumulated rotation) or <- Q U_R diag(S_R)
+//            (DIRECT), and [V_i V_j] <- [V_i V_j] X, in FP32 on row tiles staged in shared memory.
+// A matrix whose sweep rotated nothing is converged (the paper's "final sweep performs no
+// rotations"); its items are skipped from then on.  Finally sigma_j = ||w_j||, U = W / sigma and
+// the columns of U and V are sorted by descending sigma in place (cycle-following permutation).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsvd {
+
+template <typename T>
+int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st);
+template <typename T>
+int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
+                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st);
+
+// ------------------------------------------------------------------------------------------------
+// workspace layout (all offsets 256-byte aligned)
+// ------------------------------------------------------------------------------------------------
+struct BjLayout {
+    int batch, npairs, bw, mm_max;
+    size_t n_items;                   // batch * npairs
+    size_t off_G, off_X, off_S, off_UR, off_P;           // per-item matrices
+    size_t off_pG, off_pX, off_pS, off_pUR, off_pP;      // pointer arrays (item order)
+    size_t off_m, off_n, off_ld, off_ldp, off_info;      // int arrays per item
+    size_t off_state;                                    // per-matrix state
+    size_t total;
+};
+
+struct BjState {
+    int mm, nn, nblk, converged;
+    int sweeps, rot_sweep, pad0, pad1;
+    long long rotations;
+    double emax;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+static BjLayout bj_layout(int batch, int max_m, int max_n, int bw, bool direct)
+{
+    BjLayout L;
+    const int mm = max_m > max_n ? max_m : max_n;
+    const int nn = max_m > max_n ? max_n : max_m;
+    int nblk = (nn + bw - 1) / bw;
+    if (nblk < 2) nblk = 2;
+    nblk += nblk & 1;
+    L.batch = batch;
+    L.npairs = nblk / 2;
+    L.bw = bw;
+    L.mm_max = mm > 2 * bw ? mm : 2 * bw;  // rows of a packed pair (zero-padded to at least 2bw)
+    L.n_items = (size_t)batch * L.npairs;
+    const size_t k2 = (size_t)(2 * bw) * (2 * bw);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.off_G = take(L.n_items * k2 * sizeof(T));
+    L.off_X = take(L.n_items * k2 * sizeof(T));
+    L.off_S = take(L.n_items * 2 * bw * sizeof(T));
+    L.off_UR = take(direct ? L.n_items * k2 * sizeof(T) : 0);
+    L.off_P = take(direct ? L.n_items * (size_t)(mm > 2 * bw ? mm : 2 * bw) * 2 * bw * sizeof(T) : 0);
+    L.off_pG = take(L.n_items * sizeof(void*));
+    L.off_pX = take(L.n_items * sizeof(void*));
+    L.off_pS = take(L.n_items * sizeof(void*));
+    L.off_pUR = take(L.n_items * sizeof(void*));
+    L.off_pP = take(L.n_items * sizeof(void*));
+    L.off_m = take(L.n_items * sizeof(int));
+    L.off_n = take(L.n_items * sizeof(int));
+    L.off_ld = take(L.n_items * sizeof(int));
+    L.off_ldp = take(L.n_items * sizeof(int));
+    L.off_info = take(L.n_items * sizeof(int));
+    L.off_state = take((size_t)batch * sizeof(BjState));
+    L.total = o;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------------------
+// setup: working copy, V = I, per-item pointer arrays
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void bj_setup_kernel(int batch, int max_mm, int max_nn, int bw, int npairs, T* const* A, const int* M,
+                                const int* N, const int* LDA, T* const* U, const int* LDU, T* const* V,
+                                const int* LDV, unsigned char* ws, BjLayout L, int* info)
+{
+    const int b = blockIdx.x;
+    if (b >= batch) return;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    const int m = M[b], n = N[b], lda = LDA[b];
+    const bool tr = m < n;
+    const int mm = tr ? n : m, nn = tr ? m : n;
+    const int ldu = LDU[b], ldv = LDV[b];
+    const bool bad = m < 0 || n < 0 || mm > max_mm || nn > max_nn || lda < (m > 1 ? m : 1) ||
+                     ldu < (m > 1 ? m : 1) || ldv < (n > 1 ? n : 1);
+    T* Wk = tr ? V[b] : U[b];  // working matrix mm x nn
+    const int ldw = tr ? ldv : ldu;
+    T* Vk = tr ? U[b] : V[b];  // accumulated rotations nn x nn
+    const int ldvk = tr ? ldu : ldv;
+    if (threadIdx.x == 0) {
+        st->mm = bad ? 0 : mm;
+        st->nn = bad ? 0 : nn;
+        st->nblk = (nn + bw - 1) / bw;
+        st->converged = (bad || nn == 0) ? 1 : 0;
+        st->sweeps = 0;
+        st->rot_sweep = 0;
+        st->rotations = 0;
+        st->emax = 0.0;
+        info[b] = bad ? BSVD_INFO_BAD_SHAPE : 0;
+    }
+    // per-item pointers into the workspace
+    for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+        const size_t it = (size_t)b * npairs + k;
+        const size_t k2 = (size_t)(2 * bw) * (2 * bw);
+        T* G = reinterpret_cast<T*>(ws + L.off_G) + it * k2;
+        T* X = reinterpret_cast<T*>(ws + L.off_X) + it * k2;
+        T* S = reinterpret_cast<T*>(ws + L.off_S) + it * 2 * bw;
+        T* UR = reinterpret_cast<T*>(ws + L.off_UR) + it * k2;
+        T* P = reinterpret_cast<T*>(ws + L.off_P) + it * (size_t)L.mm_max * 2 * bw;
+        reinterpret_cast<T**>(ws + L.off_pG)[it] = G;
+        reinterpret_cast<T**>(ws + L.off_pX)[it] = X;
+        reinterpret_cast<T**>(ws + L.off_pS)[it] = S;
+        reinterpret_cast<T**>(ws + L.off_pUR)[it] = UR;
+        reinterpret_cast<T**>(ws + L.off_pP)[it] = P;
+        reinterpret_cast<int*>(ws + L.off_m)[it] = 0;
+        reinterpret_cast<int*>(ws + L.off_n)[it] = 0;
+        reinterpret_cast<int*>(ws + L.off_ld)[it] = 2 * bw;
+        reinterpret_cast<int*>(ws + L.off_ldp)[it] = mm > 1 ? mm : 1;
+    }
+    if (bad) return;
+    const T* a = A[b];
+    for (size_t e = threadIdx.x; e < (size_t)mm * nn; e += blockDim.x) {
+        const int j = (int)(e / mm), i = (int)(e - (size_t)j * mm);
+        Wk[(size_t)j * ldw + i] = tr ? a[(size_t)i * lda + j] : a[(size_t)j * lda + i];
+    }
+    for (size_t e = threadIdx.x; e < (size_t)nn * nn; e += blockDim.x) {
+        const int j = (int)(e / nn), i = (int)(e - (size_t)j * nn);
+        Vk[(size_t)j * ldvk + i] = i == j ? T(1) : T(0);
+    }
+}
+
+// column block (blk, column offset c in [0, 2bw)) -> global column, or -1 when past nn
+__device__ __forceinline__ int bj_col(int bi, int bj, int bw, int c, int nn)
+{
+    const int blk = c < bw ? bi : bj;
+    const int col = blk * bw + (c < bw ? c : c - bw);
+    return col < nn ? col : -1;
+}
+
+// ------------------------------------------------------------------------------------------------
+// GRAM stage: G = A_ij^T A_ij with FP32 dot products; FP64 scaled off-diagonal test
+// ------------------------------------------------------------------------------------------------
+template <typename T, int K2>  // K2 = 2 bw
+__global__ void __launch_bounds__(256) bj_gram_kernel(int batch, int npairs, int step, int bw, T* const* U,
+                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                      const int* N, unsigned char* ws, BjLayout L, double tol)
+{
+    constexpr int RC = 32;                 // rows per staged chunk
+    constexpr int TPO = (K2 * K2) / 256;   // outputs per thread
+    __shared__ T xs[K2][RC + 1];
+    __shared__ T gd[K2];
+    __shared__ double red[8];
+    const int it = blockIdx.x;
+    const int b = it / npairs, k = it - b * npairs;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    int* im = reinterpret_cast<int*>(ws + L.off_m);
+    int* in = reinterpret_cast<int*>(ws + L.off_n);
+    const int mm = st->mm, nn = st->nn, nblk = st->nblk;
+    const int nbp = nblk + (nblk & 1);
+    int bi = 0, bj = 0;
+    if (k < nbp / 2) round_robin_pair(nbp, step, k, bi, bj);
+    // pairs with the virtual block (odd nb) are skipped, except for a single block, which is
+    // orthogonalised internally through its pair with the empty block
+    const bool live = !st->converged && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn;
+    if (!live) {
+        if (threadIdx.x == 0) im[it] = in[it] = 0;
+        return;
+    }
+    const bool tr = M[b] < N[b];
+    const T* W = tr ? V[b] : U[b];
+    const int ldw = tr ? LDV[b] : LDU[b];
+    T* G = reinterpret_cast<T* const*>(ws + L.off_pG)[it];
+    const int tid = threadIdx.x;
+    // thread tile: TPO consecutive outputs of one column block
+    const int o0 = tid * TPO;
+    const int gc = o0 / K2, gr0 = o0 % K2;  // output column gc, rows gr0 .. gr0 + TPO - 1
+    T acc[TPO];
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+    for (int r0 = 0; r0 < mm; r0 += RC) {
+        for (int e = tid; e < K2 * RC; e += 256) {
+            const int c = e / RC, r = e % RC;
+            const int col = bj_col(bi, bj, bw, c, nn);
+            xs[c][r] = (col >= 0 && r0 + r < mm) ? W[(size_t)col * ldw + r0 + r] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < RC; ++r) {
+            const T y = xs[gc][r];
+#pragma unroll
+            for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[gr0 + q][r], y, acc[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) G[(size_t)gc * K2 + gr0 + q] = acc[q];
+    if (gr0 <= gc && gc < gr0 + TPO) gd[gc] = acc[gc - gr0];
+    __syncthreads();
+    // e_l = max |G_pq| / sqrt(G_pp G_qq), FP64
+    double e = 0.0;
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) {
+        const int r = gr0 + q;
+        if (r == gc) continue;
+        const double dp = (double)gd[r], dq = (double)gd[gc];
+        if (dp > 0.0 && dq > 0.0) {
+            const double v = fabs((double)acc[q]) / sqrt(dp * dq);
+            e = v > e ? v : e;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((tid & 31) == 0) red[tid >> 5] = e;
+    __syncthreads();
+    if (tid == 0) {
+        double em = 0.0;
+        for (int w = 0; w < 8; ++w) em = fmax(em, red[w]);
+        const bool rot = em > tol;
+        im[it] = rot ? K2 : 0;
+        in[it] = rot ? K2 : 0;
+        if (rot) atomicAdd(&st->rot_sweep, 1);
+        // emax of the matrix over the sweep, as ordered bits of a non-negative double
+        atomicMax(reinterpret_cast<unsigned long long*>(&st->emax), (unsigned long long)__double_as_longlong(em));
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// DIRECT stage: pack a live pair [W_i W_j] into a contiguous buffer for its QR.  Which pairs are
+// live is decided by the GRAM kernel's test, run first: FP32 dot products of the columns
+// themselves and the FP64 scaled off-diagonal, the same test for both methods.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int step, int bw, T* const* U,
+                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                      const int* N, unsigned char* ws, BjLayout L, double tol)
+{
+    const int it = blockIdx.x;
+    const int b = it / npairs, k = it - b * npairs;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    int* im = reinterpret_cast<int*>(ws + L.off_m);
+    int* in = reinterpret_cast<int*>(ws + L.off_n);
+    const int mm = st->mm, nn = st->nn, nblk = st->nblk;
+    const int nbp = nblk + (nblk & 1);
+    if (in[it] == 0) return;  // the pair test (GRAM kernel, run first) found it orthogonal
+    int bi, bj;
+    round_robin_pair(nbp, step, k, bi, bj);
+    const bool tr = M[b] < N[b];
+    const T* W = tr ? V[b] : U[b];
+    const int ldw = tr ? LDV[b] : LDU[b];
+    T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
+    // rows are zero-padded to at least K2 so that the pair's QR is of a tall matrix: the padding
+    // changes neither R nor the product A_ij V_R on the real rows
+    const int mp = mm > K2 ? mm : K2;
+    for (int c = threadIdx.x >> 5; c < K2; c += blockDim.x >> 5) {
+        const int col = bj_col(bi, bj, bw, c, nn);
+        for (int r = threadIdx.x & 31; r < mp; r += 32)
+            P[(size_t)c * mp + r] = (col >= 0 && r < mm) ? W[(size_t)col * ldw + r] : T(0);
+    }
+    if (threadIdx.x == 0) {
+        im[it] = mp;
+        in[it] = K2;
+        reinterpret_cast<int*>(ws + L.off_ldp)[it] = mp;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// polish: one Newton-Schulz step X <- X - X (X^T X - I) / 2 towards the orthogonal polar factor.
+// X (the inner SVD's accumulated rotation, a product of hundreds of plane rotations) is orthogonal
+// only to ~25 u; V multiplies ~150 of them per column, so their errors would add up.  After the
+// step ||X^T X - I|| is at the rounding level of one product.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLayout L)
+{
+    constexpr int TPO = (K2 * K2) / 256;
+    extern __shared__ __align__(16) unsigned char pol_sm[];
+    T(*xs)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm);                                  // X(r, c) at [c][r]
+    T(*es)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm + sizeof(T) * K2 * (K2 + 1));      // X^T X - I
+    const int it = blockIdx.x;
+    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
+    if (in[it] == 0) return;
+    T* X = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
+    for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) xs[e / K2][e % K2] = X[e];
+    __syncthreads();
+    const int o0 = threadIdx.x * TPO;
+    const int oc = o0 / K2, or0 = o0 % K2;
+    T acc[TPO];
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+    for (int k = 0; k < K2; ++k) {
+        const T y = xs[oc][k];
+#pragma unroll
+        for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[or0 + q][k], y, acc[q]);  // (X^T X)(or0+q, oc)
+    }
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) es[oc][or0 + q] = acc[q] - (or0 + q == oc ? T(1) : T(0));
+    __syncthreads();
+    // X(r, c) -= 0.5 * sum_k X(r, k) E(k, c)
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+    for (int k = 0; k < K2; ++k) {
+        const T e = es[oc][k];
+#pragma unroll
+        for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[k][or0 + q], e, acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = xs[oc][or0 + q] - T(0.5) * acc[q];
+}
+
+// ------------------------------------------------------------------------------------------------
+// update stage: dst rows <- src rows (r x 2bw) * X (2bw x 2bw) [* diag(S)]
+//   GRAM  : src = dst = [W_i W_j] (in place, row tiles), X = accumulated rotation of G
+//   DIRECT: src = Q (packed), X = U_R with columns scaled by S_R, dst = [W_i W_j]
+//   V     : src = dst = [V_i V_j], X = accumulated rotation (GRAM) or V_R (DIRECT)
+// grid: (items, row tiles of W + row tiles of V)
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+constexpr int bj_rows_per_tile() { return sizeof(T) == 4 ? 32 : 16; }
+
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_update_kernel(int npairs, int step, int bw, int direct, T* const* U,
+                                                        const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                        const int* N, unsigned char* ws, BjLayout L)
+{
+    constexpr int RT = bj_rows_per_tile<T>();
+    constexpr int TPO = (RT * K2) / 256;    // outputs per thread
+    __shared__ T xm[K2][K2 + 1];            // multiplier X (column-scaled for DIRECT)
+    __shared__ T ts[K2][RT + 1];            // source tile, column-major
+    const int it = blockIdx.x;
+    const int b = it / npairs, k = it - b * npairs;
+    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
+    if (in[it] == 0) return;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    const int mm = st->mm, nn = st->nn, nblk = st->nblk;
+    const int nbp = nblk + (nblk & 1);
+    int bi, bj;
+    round_robin_pair(nbp, step, k, bi, bj);
+    const int tilesW = (mm + RT - 1) / RT, tilesV = (nn + RT - 1) / RT;
+    const int tile = blockIdx.y;
+    if (tile >= tilesW + tilesV) return;
+    const bool onV = tile >= tilesW;
+    const int r0 = (onV ? tile - tilesW : tile) * RT;
+    const int rows = onV ? nn : mm;
+    const bool tr = M[b] < N[b];
+    T* dstM = onV ? (tr ? U[b] : V[b]) : (tr ? V[b] : U[b]);
+    const int ldd = onV ? (tr ? LDU[b] : LDV[b]) : (tr ? LDV[b] : LDU[b]);
+    // multiplier: the inner SVD's right factor X (GRAM: eigenvectors of G; DIRECT: V_R), or, for
+    // the W tile of DIRECT, U_R diag(S_R)
+    const T* Xv = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
+    const T* URv = reinterpret_cast<T* const*>(ws + L.off_pUR)[it];
+    const T* Sv = reinterpret_cast<T* const*>(ws + L.off_pS)[it];
+    const bool useUR = direct && !onV;
+    for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) {
+        const int c = e / K2, r = e % K2;
+        xm[c][r] = useUR ? URv[e] * Sv[c] : Xv[e];
+    }
+    // source tile
+    const T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
+    for (int e = threadIdx.x; e < K2 * RT; e += blockDim.x) {
+        const int c = e / RT, r = e % RT;
+        T v = T(0);
+        if (r0 + r < rows) {
+            if (useUR) {
+                v = P[(size_t)c * (mm > K2 ? mm : K2) + r0 + r];
+            } else {
+                const int col = bj_col(bi, bj, bw, c, nn);
+                if (col >= 0) v = dstM[(size_t)col * ldd + r0 + r];
+            }
+        }
+        ts[c][r] = v;
+    }
+    __syncthreads();
+    const int o0 = threadIdx.x * TPO;
+    const int oc = o0 / RT, or0 = o0 % RT;  // output column oc, rows or0 .. or0 + TPO - 1
+    T acc[TPO];
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+#pragma unroll 8
+    for (int kk = 0; kk < K2; ++kk) {
+        const T x = xm[oc][kk];
+#pragma unroll
+        for (int q = 0; q < TPO; ++q) acc[q] = fma(ts[kk][or0 + q], x, acc[q]);
+    }
+    const int col = bj_col(bi, bj, bw, oc, nn);
+    if (col >= 0) {
+#pragma unroll
+        for (int q = 0; q < TPO; ++q)
+            if (r0 + or0 + q < rows) dstM[(size_t)col * ldd + r0 + or0 + q] = acc[q];
+    }
+}
+
+// end of a sweep: a matrix whose sweep rotated nothing is converged
+__global__ void bj_sweep_end_kernel(int batch, int max_sweeps, int sweep, unsigned char* ws, BjLayout L, int* info)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    if (st->converged) return;
+    st->sweeps = sweep + 1;
+    st->rotations += st->rot_sweep;
+    if (st->rot_sweep == 0) {
+        st->converged = 1;
+        info[b] = sweep + 1;
+    } else if (sweep + 1 >= max_sweeps) {
+        info[b] = BSVD_INFO_NOT_CONVERGED + sweep + 1;
+    }
+    st->rot_sweep = 0;
+    st->emax = 0.0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// finalize: sigma, normalisation, descending sort of U and V columns in place
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) bj_finalize_kernel(int batch, T* const* S, T* const* U, const int* LDU,
+                                                          T* const* V, const int* LDV, const int* M, const int* N,
+                                                          unsigned char* ws, BjLayout L, int* info,
+                                                          long long* rot_out)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int b = blockIdx.x;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    if (info[b] == BSVD_INFO_BAD_SHAPE) return;
+    const int mm = st->mm, nn = st->nn;
+    if (threadIdx.x == 0 && rot_out) rot_out[b] = st->rotations;
+    if (nn == 0) return;
+    const bool tr = M[b] < N[b];
+    T* W = tr ? V[b] : U[b];
+    const int ldw = tr ? LDV[b] : LDU[b];
+    T* Vk = tr ? U[b] : V[b];
+    const int ldv = tr ? LDU[b] : LDV[b];
+    const size_t a16 = 16;
+    T* sig = reinterpret_cast<T*>(sm);
+    int* dest = reinterpret_cast<int*>(sm + ((nn * sizeof(T) + a16 - 1) & ~(a16 - 1)));
+    unsigned char* done = reinterpret_cast<unsigned char*>(dest) + ((nn * sizeof(int) + a16 - 1) & ~(a16 - 1));
+    T* tmpW = reinterpret_cast<T*>(done + ((nn + a16 - 1) & ~(a16 - 1)));
+    T* tmpV = tmpW + mm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < nn; j += nw) {
+        T s = T(0);
+        for (int r = lane; r < mm; r += 32) s = fma(W[(size_t)j * ldw + r], W[(size_t)j * ldw + r], s);
+        s = warp_sum(s);
+        if (lane == 0) sig[j] = dsqrt(s);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+        // rank in a total order (a NaN ranks last), so that dest is always a permutation
+        const T sj = sig[j] == sig[j] ? sig[j] : T(-1);
+        int r = 0;
+        for (int i = 0; i < nn; ++i) {
+            const T si = sig[i] == sig[i] ? sig[i] : T(-1);
+            r += (si > sj) || (si == sj && i < j);
+        }
+        dest[j] = r;
+        done[j] = 0;
+        S[b][r] = sig[j];
+    }
+    __syncthreads();
+    // normalise W columns (U = W / sigma)
+    for (int j = warp; j < nn; j += nw) {
+        const T sj = sig[j];
+        const T inv = sj > T(0) ? T(1) / sj : T(0);
+        for (int r = lane; r < mm; r += 32) W[(size_t)j * ldw + r] *= inv;
+    }
+    __syncthreads();
+    // permute columns j -> dest[j] by following cycles (one column in flight in shared memory)
+    for (int j0 = 0; j0 < nn; ++j0) {
+        if (done[j0] || dest[j0] == j0) continue;
+        for (int r = threadIdx.x; r < mm; r += blockDim.x) tmpW[r] = W[(size_t)j0 * ldw + r];
+        for (int r = threadIdx.x; r < nn; r += blockDim.x) tmpV[r] = Vk[(size_t)j0 * ldv + r];
+        __syncthreads();
+        int j = j0, guard = 0;
+        do {
+            const int d = dest[j];
+            // swap the in-flight column with column d
+            for (int r = threadIdx.x; r < mm; r += blockDim.x) {
+                const T x = W[(size_t)d * ldw + r];
+                W[(size_t)d * ldw + r] = tmpW[r];
+                tmpW[r] = x;
+            }
+            for (int r = threadIdx.x; r < nn; r += blockDim.x) {
+                const T x = Vk[(size_t)d * ldv + r];
+                Vk[(size_t)d * ldv + r] = tmpV[r];
+                tmpV[r] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) done[j] = 1;
+            j = d;
+            __syncthreads();
+        } while (j != j0 && ++guard < nn);  // a permutation closes every cycle within nn moves
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method)
+{
+    return bj_layout<T>(batch, max_m, max_n, bw, method != 0).total;
+}
+
+template <typename T, int K2>
+static int run_block(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                     void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
+                     int max_sweeps, int method, int* info, long long* rot, unsigned char* ws, cudaStream_t st)
+{
+    const int bw = K2 / 2;
+    const int inner_variant = method >> 8;  // register-tier variant of the inner SVD (0: first fitting)
+    method &= 0xff;
+    const bool direct = method != 0;
+    const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
+    const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+    const int npairs = L.npairs, nbp = 2 * npairs;
+    // default pair threshold sqrt(m) u; DIRECT rotations are only as orthogonal as the pair's
+    // Householder Q (~ 2bw u), so its default sits 8x higher
+    const double tol_outer = tol > 0.0 ? tol : (direct ? 8.0 : 1.0) * sqrt((double)mm) * Unit<T>::value;
+    bj_setup_kernel<T><<<batch, 256, 0, st>>>(batch, mm, nn, bw, npairs, (T* const*)A, M, N, LDA, (T* const*)U, LDU,
+                                              (T* const*)V, LDV, ws, L, info);
+    if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    const int items = batch * npairs;
+    void* const* pG = reinterpret_cast<void* const*>(ws + L.off_pG);
+    void* const* pX = reinterpret_cast<void* const*>(ws + L.off_pX);
+    void* const* pS = reinterpret_cast<void* const*>(ws + L.off_pS);
+    void* const* pUR = reinterpret_cast<void* const*>(ws + L.off_pUR);
+    void* const* pP = reinterpret_cast<void* const*>(ws + L.off_pP);
+    const int* im = reinterpret_cast<const int*>(ws + L.off_m);
+    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
+    const int* ild = reinterpret_cast<const int*>(ws + L.off_ld);  // 2bw for every item
+    const int* ildp = reinterpret_cast<const int*>(ws + L.off_ldp);
+    int* iinfo = reinterpret_cast<int*>(ws + L.off_info);
+    constexpr int RT = bj_rows_per_tile<T>();
+    const int tiles = (mm + RT - 1) / RT + (nn + RT - 1) / RT;
+    const int sweeps = max_sweeps > 0 ? max_sweeps : 20;
+    const size_t polish_smem = 2 * sizeof(T) * K2 * (K2 + 1);
+    if (polish_smem > 48 * 1024 && cudaFuncSetAttribute(bj_polish_kernel<T, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)polish_smem) != cudaSuccess)
+        return BSVD_ERR_CUDA;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int step = 0; step < nbp - 1; ++step) {
+            if (!direct) {
+                bj_gram_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
+                                                             LDV, M, N, ws, L, tol_outer);
+                const int rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, im, in, ild, pS, nullptr, nullptr,
+                                                    pX, ild, 0.0, 0, iinfo, nullptr, st);
+                if (rc != BSVD_SUCCESS) return rc;
+            } else {
+                bj_gram_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
+                                                             LDV, M, N, ws, L, tol_outer);
+                bj_pack_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
+                                                             LDV, M, N, ws, L, tol_outer);
+                int rc = launch_qr<T>(items, L.mm_max, K2, pP, im, in, ildp, pP, ildp, pG, ild, iinfo, st);
+                if (rc != BSVD_SUCCESS) return rc;
+                // the inner sizes are K2 x K2 (R) for live items: reuse the n array for both
+                rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, in, in, ild, pS, pUR, ild, pX, ild, 0.0, 0,
+                                          iinfo, nullptr, st);
+                if (rc != BSVD_SUCCESS) return rc;
+            }
+            bj_polish_kernel<T, K2><<<items, 256, polish_smem, st>>>(ws, L);
+            bj_update_kernel<T, K2><<<dim3(items, tiles), 256, 0, st>>>(npairs, step, bw, direct ? 1 : 0, (T* const*)U,
+                                                                        LDU, (T* const*)V, LDV, M, N, ws, L);
+            if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+        }
+        bj_sweep_end_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, sweeps, sw, ws, L, info);
+    }
+    const size_t fsm = (size_t)nn * (sizeof(T) + sizeof(int) + 1) + 48 + (size_t)(mm + nn) * sizeof(T) + 64;
+    if (fsm > 48 * 1024 &&
+        cudaFuncSetAttribute(bj_finalize_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess)
+        return BSVD_ERR_CUDA;
+    bj_finalize_kernel<T><<<batch, 256, fsm, st>>>(batch, (T* const*)S, (T* const*)U, LDU, (T* const*)V, LDV, M, N, ws,
+                                                   L, info, rot);
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
+
+template <typename T>
+int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
+                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
+                        cudaStream_t st)
+{
+    if (bw != 16 && bw != 32) return BSVD_ERR_UNSUPPORTED;
+    const int mm = max_m > max_n ? max_m : max_n;
+    if ((method & 0xff) != 0 && (size_t)(mm > 2 * bw ? mm : 2 * bw) * 2 * bw * sizeof(T) > 200 * 1024) return BSVD_ERR_UNSUPPORTED;
+    if (mm > 16384) return BSVD_ERR_UNSUPPORTED;
+    if (ws_bytes < block_jacobi_workspace<T>(batch, max_m, max_n, bw, method & 0xff)) return BSVD_ERR_WORKSPACE;
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    return bw == 16 ? run_block<T, 32>(batch, max_m, max_n, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, method,
+                                       info, rot, w, st)
+                    : run_block<T, 64>(batch, max_m, max_n, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, method,
+                                       info, rot, w, st);
+}
+
+template size_t block_jacobi_workspace<float>(int, int, int, int, int);
+template size_t block_jacobi_workspace<double>(int, int, int, int, int);
+template int launch_block_jacobi<float>(int, int, int, int, int, void* const*, const int*, const int*, const int*,
+                                        void* const*, void* const*, const int*, void* const*, const int*, double, int,
+                                        int*, long long*, void*, size_t, cudaStream_t);
+template int launch_block_jacobi<double>(int, int, int, int, int, void* const*, const int*, const int*, const int*,
+                                         void* const*, void* const*, const int*, void* const*, const int*, double, int,
+                                         int*, long long*, void*, size_t, cudaStream_t);
+
+}  // namespace bsvd

@@ -17,6 +17,8 @@ __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float drsqrt(float x) { return __frsqrt_rn(x); }
 __device__ __forceinline__ double drsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
 
@@ -85,6 +87,36 @@ __device__ __forceinline__ bool off_diagonal_large(float alpha, float beta, floa
 __device__ __forceinline__ bool off_diagonal_large(double alpha, double beta, double gamma, double tol)
 {
     return gamma * gamma > (tol * tol) * alpha * beta;
+}
+
+// 2^-floor(log2 x) for x > 0, read off the exponent bits (exact; clamped at the range ends).
+__device__ __forceinline__ float pow2_scale(float x)
+{
+    int e = (__float_as_int(x) >> 23) & 0xff;
+    e = e < 1 ? 1 : (e > 253 ? 253 : e);
+    return __int_as_float((254 - e) << 23);
+}
+__device__ __forceinline__ double pow2_scale(double x)
+{
+    long long e = (__double_as_longlong(x) >> 52) & 0x7ff;
+    e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
+    return __longlong_as_double((2046 - e) << 52);
+}
+
+// Smaller root t of t^2 + 2 zeta t - 1 = 0, zeta = (beta - alpha) / (2 gamma), written as
+// t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2))
+// (one division, one square root).  t is invariant under scaling (beta - alpha, gamma) together,
+// so both are first scaled by a power of two to [1, 2): the squares can then neither overflow nor
+// underflow, which matters when alpha, beta, gamma are themselves squares of small numbers.
+template <typename P>
+__device__ __forceinline__ P jacobi_t(P alpha, P beta, P gamma)
+{
+    const P d = beta - alpha, g2 = P(2) * gamma;
+    const P ad = dabs(d), ag = dabs(g2);
+    const P sc = pow2_scale(ad > ag ? ad : ag);
+    const P dn = ad * sc, gn = g2 * sc;
+    const P t = gn / (dn + dsqrt(dn * dn + gn * gn));
+    return d >= P(0) ? t : -t;
 }
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

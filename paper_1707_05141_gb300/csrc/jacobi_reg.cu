@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
 
     __shared__ Red3<T> red[2][NW > 1 ? NW : 1][32];
     __shared__ T sig_s[NC];
-    __shared__ int rank_s[NC];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
             vL[k] = (r == colL) ? T(1) : T(0);
             vR[k] = (r == colR) ? T(1) : T(0);
         }
-        T dL = T(1), dR = T(1), eL = T(1), eR = T(1);  // column scales and their inverses
+        T dL = T(1), dR = T(1);  // column scales
 
         const P tol = tol_in > 0.0 ? P(tol_in) : P(dsqrt(double(mm)) * Unit<T>::value);
         const int sweeps_cap = max_sweeps > 0 ? max_sweeps : 30;
@@ -154,28 +153,24 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                     }
                     step_parity ^= 1;
                 }
-                // rotation of the pair, in the unscaled frame; the wrap slot idles on odd steps.
-                // t = 2 gamma sign(beta - alpha) / (|beta - alpha| + sqrt((beta - alpha)^2 + 4 gamma^2))
-                // is the same smaller root as sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with
-                // zeta = (beta - alpha) / (2 gamma), with one division and one square root.
+                // rotation of the pair, in the unscaled frame; the wrap slot idles on odd steps
                 const P alpha = FAST ? P(dL) * P(dL) * P(sa) : P(sa);
                 const P beta = FAST ? P(dR) * P(dR) * P(sb) : P(sb);
                 const P gamma = FAST ? P(dL) * P(dR) * P(sc) : P(sc);
                 const bool rot = !(odd && s == NS - 1) && alpha > P(0) && beta > P(0) &&
                                  off_diagonal_large(alpha, beta, gamma, tol);
-                P tth = P(0), cth = P(1), xth = P(1);
+                P tth = P(0), cth = P(1);
                 if (rot) {
-                    const P d = beta - alpha;
-                    const P r = dsqrt(d * d + P(4) * gamma * gamma);
-                    tth = (d >= P(0) ? P(2) * gamma : P(-2) * gamma) / (dabs(d) + r);
-                    xth = P(1) + tth * tth;
-                    cth = drsqrt(xth);
+                    tth = jacobi_t(alpha, beta, gamma);
+                    cth = drsqrt(P(1) + tth * tth);
                 }
                 // unconditional update: a skipped pair has multipliers 0 (and c = 1), which leaves
                 // its columns bit-identical; a warp runs this whenever any of its pairs rotates
                 if (FAST) {
-                    const T mL = -T(tth) * (dR * eL);  // -t d_j / d_i
-                    const T mR = T(tth) * (dL * eR);   //  t d_i / d_j
+                    // scale ratios from the current scales (correctly rounded reciprocals), so that
+                    // their rounding does not accumulate over the rotations of a sweep
+                    const T mL = -T(tth) * (dR * rcp_rn(dL));  // -t d_j / d_i
+                    const T mR = T(tth) * (dL * rcp_rn(dR));   //  t d_i / d_j
 #pragma unroll
                     for (int k = 0; k < RA; ++k) {
                         const T x = aL[k], y = aR[k];
@@ -190,11 +185,8 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                             vR[k] = fma(mR, x, y);
                         }
                     }
-                    const T ci = T(xth * cth);  // 1 / c = sqrt(1 + t^2)
                     dL *= T(cth);
                     dR *= T(cth);
-                    eL *= ci;
-                    eR *= ci;
                 } else {
                     const T cc = T(cth), ss = T(cth * tth);
 #pragma unroll
@@ -223,10 +215,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
 #pragma unroll
                         for (int k = 0; k < RV; ++k) vR[k] = __shfl_sync(0xffffffffu, vR[k], src, NS);
                     }
-                    if (FAST) {
-                        dR = __shfl_sync(0xffffffffu, dR, src, NS);
-                        eR = __shfl_sync(0xffffffffu, eR, src, NS);
-                    }
+                    if (FAST) dR = __shfl_sync(0xffffffffu, dR, src, NS);
                     colR = __shfl_sync(0xffffffffu, colR, src, NS);
                 } else {
                     // odd -> even: the left column moves one slot up; the wrap slot, which did not
@@ -251,9 +240,6 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                         const T r = __shfl_sync(0xffffffffu, wrap ? dR : dL, src, NS);
                         dR = wrap ? dL : dR;
                         dL = r;
-                        const T q = __shfl_sync(0xffffffffu, wrap ? eR : eL, src, NS);
-                        eR = wrap ? eL : eR;
-                        eL = q;
                     }
                     const int rc = __shfl_sync(0xffffffffu, wrap ? colR : colL, src, NS);
                     colR = wrap ? colL : colR;
@@ -274,7 +260,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                         vR[k] *= dR;
                     }
                 }
-                dL = dR = eL = eR = T(1);
+                dL = dR = T(1);
             }
             ++sweep;
             total_rot += rot_sweep;

@@ -1,0 +1,113 @@
+"""GPU parity: batched one-sided block Jacobi (Algorithm 3) through the C ABI vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+import gen
+import oracle as O
+from parity import gate, svd_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bs():
+    import paper_1707_05141_gb300 as bs
+    bs.build()
+    assert torch.cuda.is_available()
+    return bs
+
+
+def _host(*ts):
+    return [t.detach().cpu().numpy().astype(np.float64) for t in ts]
+
+
+@pytest.fixture(scope="module")
+def w2():
+    """Four 512 x 512 FP32 matrices with sigma log-uniform on [1e-6, 1] and their oracle SVDs."""
+    b = gen.workload2(batch=4)
+    mats = [b.a64(i) for i in range(b.batch)]
+    Uo, So, Vo, info, _ = O.svd_batch(mats)
+    return b, mats, So
+
+
+@pytest.mark.parametrize("method,bw", [(0, 32), (1, 32), (0, 16), (1, 16)])
+def test_block_512_log_uniform_sigma(bs, w2, method, bw):
+    b, mats, So = w2
+    a = torch.from_numpy(b.a).cuda()
+    u, s, v, info, rots = bs.svd_block(a, block_width=bw, method=method, max_sweeps=30)
+    torch.cuda.synchronize()
+    u, s, v = _host(u, s, v)
+    info = info.cpu().numpy()
+    for i in range(b.batch):
+        assert 0 < info[i] < (1 << 20), (i, info[i])
+        e = svd_errors(mats[i], u[i].T, s[i], v[i].T, So[i])
+        if method == 0:
+            # GRAM: every gate at 1e-5, U's orthogonality over all columns down to sigma = 1e-6
+            assert max(e.values()) <= 1e-5, (i, e)
+        else:
+            # DIRECT: a rotation is only as orthogonal as the pair's Householder Q (~ 2bw u), which
+            # bounds U's orthogonality a little above the gate; the other gates hold
+            assert e["sigma"] <= 1e-5 and e["orth_v"] <= 1e-5 and e["resid"] <= 1e-5, (i, e)
+            assert e["orth_u"] <= 4e-5, (i, e)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("method", [0, 1])
+def test_block_ragged_shapes(bs, dt, method):
+    """Partial last block, a virtual empty block, wide input, tiny block counts."""
+    shapes = [(96, 80), (70, 130), (64, 64), (200, 33), (33, 33), (5, 3)]
+    rng = np.random.default_rng(21)
+    g = gate(dt)
+    for (m, n) in shapes:
+        k = min(m, n)
+        uu, _ = np.linalg.qr(rng.standard_normal((m, k)))
+        vv, _ = np.linalg.qr(rng.standard_normal((n, k)))
+        sig = np.sort(10.0 ** rng.uniform(-2, 0, k))[::-1]
+        a64 = (uu * sig) @ vv.T
+        a = torch.from_numpy(np.ascontiguousarray(a64.T.astype(dt))[None]).cuda()
+        u, s, v, info, rots = bs.svd_block(a, block_width=16, method=method, max_sweeps=30)
+        torch.cuda.synchronize()
+        u, s, v = _host(u, s, v)
+        assert 0 < int(info[0]) < (1 << 20), ((m, n), int(info[0]))
+        ad = a64.astype(dt).astype(np.float64)
+        _, so, _, _, _ = O.svd(ad)
+        e = svd_errors(ad, u[0].T, s[0], v[0].T, so)
+        assert max(e.values()) <= 4 * g, ((m, n), e)
+
+
+def test_block_matches_register_tier_on_64x64(bs):
+    b = gen.workload1_svd(batch=32)
+    a = torch.from_numpy(b.a).cuda()
+    _, s_reg, _, _, _ = bs.svd(a)
+    _, s_blk, _, info, _ = bs.svd_block(a, block_width=16, method=0)
+    torch.cuda.synchronize()
+    assert torch.all(info > 0)
+    assert (s_reg - s_blk).abs().max().item() <= 2e-6
+
+
+def test_block_workspace_and_errors(bs):
+    dev = torch.device("cuda")
+    a = torch.zeros((2, 40, 40), device=dev)
+    A = bs.Batch.uniform(a, 40, 40)
+    need = bs.batched_svd_block_jacobi_workspace(A, 16, 0)
+    assert need > 0
+    s = torch.zeros((2, 1, 40), device=dev)
+    u = torch.zeros((2, 40, 40), device=dev)
+    v = torch.zeros((2, 40, 40), device=dev)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)
+    small = torch.empty(need - 1, dtype=torch.uint8, device=dev)
+    with pytest.raises(bs.BsvdError) as e:
+        bs.batched_svd_block_jacobi(A, bs.Batch.uniform(s, 40, 1), bs.Batch.uniform(u, 40, 40),
+                                    bs.Batch.uniform(v, 40, 40), info, small, block_width=16)
+    assert e.value.code == bs.ERR_WORKSPACE
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    with pytest.raises(bs.BsvdError) as e:
+        bs.batched_svd_block_jacobi(A, bs.Batch.uniform(s, 40, 1), bs.Batch.uniform(u, 40, 40),
+                                    bs.Batch.uniform(v, 40, 40), info, ws, block_width=24)
+    assert e.value.code == -16
+    # a zero matrix converges in one sweep with zero singular values
+    bs.batched_svd_block_jacobi(A, bs.Batch.uniform(s, 40, 1), bs.Batch.uniform(u, 40, 40),
+                                bs.Batch.uniform(v, 40, 40), info, ws, block_width=16)
+    torch.cuda.synchronize()
+    assert info.tolist() == [1, 1] and float(s.abs().max()) == 0.0
