@@ -170,6 +170,39 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n,
                              int* d_info, long long* d_rotations,
                              void* workspace, size_t workspace_bytes, void* stream);
 
+/* Size of the library-owned scratch array used by batched_svd_block_jacobi_noalloc (64 MiB). */
+#define BSVD_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define BSVD_ERR_SCRATCH_LIMIT (-1003) /* the call needs more than BSVD_NOALLOC_SCRATCH_BYTES */
+
+/*
+ * batched_svd_block_jacobi_noalloc -- the same computation as batched_svd_block_jacobi, for
+ * callers that can neither pass a workspace nor allocate device memory (for example code running
+ * under a host application's memory manager that forbids driver allocations, or on a
+ * latency-critical path where cudaMalloc's implicit synchronisation is not acceptable).  The
+ * paper has no counterpart; this is a property of the library, not of the method.
+ *
+ * Arguments are those of batched_svd_block_jacobi without workspace/workspace_bytes.  The
+ * scratch is one static device array of BSVD_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until the process exits.  The function calls no cudaMalloc or cudaFree and no
+ * allocating library routine.
+ *   - A batch whose batched_svd_block_jacobi_workspace(...) exceeds BSVD_NOALLOC_SCRATCH_BYTES is
+ *     rejected with BSVD_ERR_SCRATCH_LIMIT before anything is launched (for 512 x 512 FP32 with
+ *     block width 32 that is about 250 matrices per call).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.  Lookup failure
+ *     returns BSVD_ERR_CUDA.
+ *   - Every call on a device uses the same array: calls whose GPU work overlaps (other streams,
+ *     other host threads) race on it and must be serialised by the caller.  Each call writes every
+ *     scratch location before reading it, so leftover contents of a previous call do not matter.
+ */
+int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
+                                     void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+                                     void* const* dS,
+                                     void* const* dU, const int* d_ldu,
+                                     void* const* dV, const int* d_ldv,
+                                     double tol, int max_sweeps, int block_width, int method,
+                                     int* d_info, long long* d_rotations, void* stream);
+
 /* Library version and build description (static strings). */
 const char* bsvd_version(void);
 

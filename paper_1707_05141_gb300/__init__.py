@@ -19,6 +19,8 @@ SUCCESS = 0
 ERR_UNSUPPORTED = -1000
 ERR_CUDA = -1001
 ERR_WORKSPACE = -1002
+ERR_SCRATCH_LIMIT = -1003
+NOALLOC_SCRATCH_BYTES = 64 << 20
 BLOCK_GRAM, BLOCK_DIRECT = 0, 1
 INFO_BAD_SHAPE = -1
 INFO_NOT_CONVERGED = 1 << 20
@@ -33,7 +35,7 @@ class BsvdError(RuntimeError):
 
     def __init__(self, fn: str, code: int):
         what = {ERR_UNSUPPORTED: "unsupported shape", ERR_CUDA: "CUDA launch failure",
-                ERR_WORKSPACE: "workspace too small"}.get(code)
+                ERR_WORKSPACE: "workspace too small", ERR_SCRATCH_LIMIT: "beyond the fixed scratch"}.get(code)
         super().__init__(f"{fn} returned {code}" + (f" ({what})" if what else f" (argument {-code} invalid)"))
         self.code = code
 
@@ -62,6 +64,9 @@ def lib() -> ctypes.CDLL:
             L.batched_svd_block_jacobi.restype = i
             L.batched_svd_block_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p, p,
                                                    ctypes.c_size_t, p]
+            L.batched_svd_block_jacobi_noalloc.restype = i
+            L.batched_svd_block_jacobi_noalloc.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p,
+                                                           p]
             _lib = L
     return _lib
 
@@ -194,6 +199,19 @@ def batched_svd_block_jacobi(A: Batch, S: Batch, U: Batch, V: Batch, info, works
                                         float(tol), int(max_sweeps), int(block_width), int(method), _ptr(info),
                                         _ptr(rotations), _ptr(workspace), int(workspace.numel()), _stream_ptr(stream))
     _check("batched_svd_block_jacobi", rc)
+
+
+def batched_svd_block_jacobi_noalloc(A: Batch, S: Batch, U: Batch, V: Batch, info, rotations=None,
+                                     tol: float = 0.0, max_sweeps: int = 0, block_width: int = 32,
+                                     method: int = BLOCK_GRAM, stream=None) -> None:
+    """Block-Jacobi SVD with the library's own fixed scratch (no workspace, no allocation);
+    see include/bsvd.h for its limit and the rule against overlapping calls."""
+    rc = lib().batched_svd_block_jacobi_noalloc(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m),
+                                                _ptr(A.n), _ptr(A.ld), _ptr(S.ptrs), _ptr(U.ptrs), _ptr(U.ld),
+                                                _ptr(V.ptrs), _ptr(V.ld), float(tol), int(max_sweeps),
+                                                int(block_width), int(method), _ptr(info), _ptr(rotations),
+                                                _stream_ptr(stream))
+    _check("batched_svd_block_jacobi_noalloc", rc)
 
 
 # ----------------------------------------------------------------------------------------------

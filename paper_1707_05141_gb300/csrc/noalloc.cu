@@ -1,0 +1,95 @@
+// noalloc.cu -- an allocation-free variant of batched_svd_block_jacobi.
+//
+// Some callers cannot hand the library a workspace, nor call cudaMalloc themselves: code that runs
+// under a host application's own memory manager that forbids direct driver allocations, or on a
+// latency-critical path where cudaMalloc (which may synchronise the device) is not acceptable.
+// For them this entry point keeps its scratch in a fixed-size array in device memory that belongs
+// to the library, so a call needs nothing beyond the caller's inputs and outputs.
+//
+// The array is a file-scope __device__ object: every GPU that loads this library holds it until
+// the process exits.  In host code its name is only a stand-in, not a device address, so the
+// first call on each device, with that device current, looks the address up with
+// cudaGetSymbolAddress and remembers it for that device.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace bsvd {
+template <typename T>
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
+template <typename T>
+int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
+                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
+}  // namespace bsvd
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)BSVD_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices];  // device address of g_scratch on each device, once looked up
+
+// Device address of the scratch array on the current device (nullptr on failure).
+void* scratch_address()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return nullptr;
+        g_addr[dev] = p;
+    }
+    return g_addr[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m,
+                                     const int* d_n, const int* d_lda, void* const* dS, void* const* dU,
+                                     const int* d_ldu, void* const* dV, const int* d_ldv, double tol, int max_sweeps,
+                                     int block_width, int method, int* d_info, long long* d_rotations, void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0) return -4;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (!dS) return -9;
+    if (!dU) return -10;
+    if (!d_ldu) return -11;
+    if (!dV) return -12;
+    if (!d_ldv) return -13;
+    if (!(tol == tol)) return -14;
+    if (block_width != 16 && block_width != 32) return -16;
+    if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
+    if (!d_info) return -18;
+    const size_t need = dtype == BSVD_F32
+                            ? bsvd::block_jacobi_workspace<float>(batch, max_m, max_n, block_width, method & 0xff)
+                            : bsvd::block_jacobi_workspace<double>(batch, max_m, max_n, block_width, method & 0xff);
+    if (need > kScratchBytes) return BSVD_ERR_SCRATCH_LIMIT;
+    void* ws = scratch_address();
+    if (!ws) return BSVD_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32
+               ? bsvd::launch_block_jacobi<float>(batch, max_m, max_n, block_width, method, dA, d_m, d_n, d_lda, dS, dU,
+                                                  d_ldu, dV, d_ldv, tol, max_sweeps, d_info, d_rotations, ws,
+                                                  kScratchBytes, st)
+               : bsvd::launch_block_jacobi<double>(batch, max_m, max_n, block_width, method, dA, d_m, d_n, d_lda, dS,
+                                                   dU, d_ldu, dV, d_ldv, tol, max_sweeps, d_info, d_rotations, ws,
+                                                   kScratchBytes, st);
+}
+
+}  // extern "C"
