@@ -45,6 +45,9 @@ extern "C" {
 /* per-matrix info */
 #define BSVD_INFO_BAD_SHAPE (-1)
 #define BSVD_INFO_NOT_CONVERGED (1 << 20) /* + sweeps run: the sweep cap was reached */
+#define BSVD_INFO_NO_SCRATCH (-2)         /* batched_rsvd: workspace too small for this matrix */
+#define BSVD_INFO_RANK_CAPPED (1 << 21)   /* batched_rsvd: the rank needed exceeds kmax */
+#define BSVD_INFO_FALLBACK (1 << 22)      /* batched_rsvd: sampling did not pass, full SVD used */
 
 /* Jacobi memory tiers (argument `tier` of batched_svd_jacobi).  `tier` may carry a variant in
    bits 8 and up: BSVD_TIER_REGISTER | (k << 8) forces the k-th register variant that fits the
@@ -169,6 +172,45 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n,
                              double tol, int max_sweeps, int block_width, int method,
                              int* d_info, long long* d_rotations,
                              void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * batched_rsvd_workspace -- bytes of DEVICE workspace for batched_rsvd.  h_m, h_n are optional
+ * HOST arrays of the batch's sizes (exact size); NULL bounds every matrix by max_m x max_n.
+ */
+size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const int* h_m, const int* h_n);
+
+/*
+ * batched_rsvd -- randomized truncated SVD of each matrix (Algorithm 4, Section 7) with one step
+ * of randomized subspace iteration, truncated to a relative Frobenius tolerance (Section 8.2).
+ * FP32 only (dtype BSVD_F32), m, n <= 256.
+ *
+ *   d_rank_hint[b] (nullable) first rank guess k0; the first round draws l = k0 + oversample
+ *                  Gaussian columns (Philox4x32-10, counter (row/4, column, b, 0), key = seed).
+ *                  NULL or 0 starts from l = oversample.  A guess with l >= min(m, n) (or > 128)
+ *                  sends the matrix straight to the full Jacobi SVD.
+ *   tol            eps: the result satisfies ||A - U S V^T||_F <= eps ||A||_F up to the posterior
+ *                  estimate's error.  After each round, 8 probe columns (stream 1) give
+ *                  est = ||(A - U_l S_l V_l^T) W||_F / sqrt(8); est <= eps/2 ||A||_F accepts the
+ *                  round, otherwise the next round draws `oversample` more columns.  Past
+ *                  max_rounds, or 128 columns, the matrix gets the full Jacobi SVD.
+ *   The rank k is the smallest with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 - 4 est^2 (the
+ *   estimate is trusted to a factor 2; 5% of eps is kept for the FP32 factorisation's residual).
+ *   A matrix sent straight to the full SVD has est = 0 and 0 rounds.
+ *   dU[b] (m x kmax, ld d_ldu[b]), dS[b] (kmax), dV[b] (n x kmax, ld d_ldv[b]): the first k columns
+ *                  and values are written; k > kmax writes kmax and flags BSVD_INFO_RANK_CAPPED.
+ *   d_rank[b]      k;  d_err_est[b] (nullable) est / ||A||_F;  d_samples[b] (nullable) the number
+ *                  of columns the result came from (l, or min(m, n) after a full SVD).
+ *   d_info[b]      rounds run | BSVD_INFO_FALLBACK | BSVD_INFO_RANK_CAPPED, or BSVD_INFO_BAD_SHAPE
+ *                  or BSVD_INFO_NO_SCRATCH (the matrix did not fit the workspace; nothing written).
+ *   workspace      at least batched_rsvd_workspace(...) bytes (else BSVD_ERR_WORKSPACE).
+ */
+int batched_rsvd(int dtype, int batch, int max_m, int max_n,
+                 void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+                 const int* d_rank_hint, double tol, int oversample, int max_rounds,
+                 unsigned long long seed,
+                 void* const* dU, const int* d_ldu, void* const* dS, void* const* dV, const int* d_ldv,
+                 const int* d_kmax, int* d_rank, float* d_err_est, int* d_samples, int* d_info,
+                 void* workspace, size_t workspace_bytes, void* stream);
 
 /* Size of the library-owned scratch array used by batched_svd_block_jacobi_noalloc (64 MiB). */
 #define BSVD_NOALLOC_SCRATCH_BYTES (64u << 20)

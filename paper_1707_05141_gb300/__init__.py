@@ -24,6 +24,9 @@ NOALLOC_SCRATCH_BYTES = 64 << 20
 BLOCK_GRAM, BLOCK_DIRECT = 0, 1
 INFO_BAD_SHAPE = -1
 INFO_NOT_CONVERGED = 1 << 20
+INFO_NO_SCRATCH = -2
+INFO_RANK_CAPPED = 1 << 21
+INFO_FALLBACK = 1 << 22
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -64,6 +67,11 @@ def lib() -> ctypes.CDLL:
             L.batched_svd_block_jacobi.restype = i
             L.batched_svd_block_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p, p,
                                                    ctypes.c_size_t, p]
+            L.batched_rsvd_workspace.restype = ctypes.c_size_t
+            L.batched_rsvd_workspace.argtypes = [i, i, i, i, p, p]
+            L.batched_rsvd.restype = i
+            L.batched_rsvd.argtypes = [i, i, i, i, p, p, p, p, p, d, i, i, ctypes.c_ulonglong, p, p, p, p, p, p, p,
+                                       p, p, p, p, ctypes.c_size_t, p]
             L.batched_svd_block_jacobi_noalloc.restype = i
             L.batched_svd_block_jacobi_noalloc.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p,
                                                            p]
@@ -199,6 +207,75 @@ def batched_svd_block_jacobi(A: Batch, S: Batch, U: Batch, V: Batch, info, works
                                         float(tol), int(max_sweeps), int(block_width), int(method), _ptr(info),
                                         _ptr(rotations), _ptr(workspace), int(workspace.numel()), _stream_ptr(stream))
     _check("batched_svd_block_jacobi", rc)
+
+
+def batched_rsvd_workspace(A: Batch, h_m=None, h_n=None) -> int:
+    """Workspace bytes batched_rsvd needs (host size arrays give the exact size)."""
+    import numpy as np
+    hm = None if h_m is None else np.ascontiguousarray(h_m, dtype=np.int32)
+    hn = None if h_n is None else np.ascontiguousarray(h_n, dtype=np.int32)
+    return int(lib().batched_rsvd_workspace(A.code, A.batch, A.max_m, A.max_n,
+                                            None if hm is None else hm.ctypes.data_as(ctypes.c_void_p),
+                                            None if hn is None else hn.ctypes.data_as(ctypes.c_void_p)))
+
+
+def batched_rsvd(A: Batch, U: Batch, S: Batch, V: Batch, kmax, rank, info, workspace, rank_hint=None,
+                 tol: float = 1e-5, oversample: int = 8, max_rounds: int = 4, seed: int = 0, err_est=None,
+                 samples=None, stream=None) -> None:
+    """Randomized truncated SVD (Algorithm 4 + one power step, adaptive); see include/bsvd.h."""
+    rc = lib().batched_rsvd(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
+                            _ptr(rank_hint), float(tol), int(oversample), int(max_rounds), int(seed), _ptr(U.ptrs),
+                            _ptr(U.ld), _ptr(S.ptrs), _ptr(V.ptrs), _ptr(V.ld), _ptr(kmax), _ptr(rank),
+                            _ptr(err_est), _ptr(samples), _ptr(info), _ptr(workspace), int(workspace.numel()),
+                            _stream_ptr(stream))
+    _check("batched_rsvd", rc)
+
+
+class RsvdResult:
+    """Outputs of ``rsvd``: flat device buffers plus per-matrix views on the host side."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def rsvd(flat, offsets, m, n, rank_hint=None, kmax=None, tol: float = 1e-5, oversample: int = 8,
+         max_rounds: int = 4, seed: int = 0, stream=None, workspace=None):
+    """Randomized SVD of matrices packed in ``flat`` (a device FP32 tensor) at element ``offsets``
+    with sizes ``m``, ``n`` (host sequences).  Allocates the outputs (kmax columns each, default
+    min(m, n)) and, unless given, the workspace."""
+    import numpy as np
+    torch = _torch()
+    dev = flat.device
+    m = np.asarray(m, dtype=np.int32)
+    n = np.asarray(n, dtype=np.int32)
+    bsz = len(m)
+    k = np.minimum(m, n)
+    km = k.copy() if kmax is None else np.asarray(kmax, dtype=np.int32)
+    su = (m.astype(np.int64) * km + 3) // 4 * 4
+    sv = (n.astype(np.int64) * km + 3) // 4 * 4
+    ss = (km.astype(np.int64) + 3) // 4 * 4
+    ou = np.concatenate([[0], np.cumsum(su)[:-1]])
+    ov = np.concatenate([[0], np.cumsum(sv)[:-1]])
+    os_ = np.concatenate([[0], np.cumsum(ss)[:-1]])
+    fu = torch.zeros(int(su.sum()) + 4, device=dev)
+    fv = torch.zeros(int(sv.sum()) + 4, device=dev)
+    fs = torch.zeros(int(ss.sum()) + 4, device=dev)
+    A = Batch.packed(flat, offsets, m, n)
+    U = Batch.packed(fu, ou, m, km)
+    V = Batch.packed(fv, ov, n, km)
+    S = Batch.packed(fs, os_, km, np.ones_like(km))
+    kmax_d = torch.as_tensor(km, dtype=torch.int32).to(dev)
+    hint_d = None if rank_hint is None else torch.as_tensor(np.asarray(rank_hint, np.int32)).to(dev)
+    rank = torch.zeros(bsz, dtype=torch.int32, device=dev)
+    info = torch.zeros(bsz, dtype=torch.int32, device=dev)
+    err = torch.zeros(bsz, dtype=torch.float32, device=dev)
+    samples = torch.zeros(bsz, dtype=torch.int32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(batched_rsvd_workspace(A, m, n), dtype=torch.uint8, device=dev)
+    batched_rsvd(A, U, S, V, kmax_d, rank, info, workspace, hint_d, tol, oversample, max_rounds, seed, err,
+                 samples, stream)
+    return RsvdResult(U=fu, V=fv, S=fs, off_u=ou, off_v=ov, off_s=os_, kmax=km, rank=rank, info=info, err_est=err,
+                      samples=samples, workspace=workspace, m=m, n=n)
 
 
 def batched_svd_block_jacobi_noalloc(A: Batch, S: Batch, U: Batch, V: Batch, info, rotations=None,

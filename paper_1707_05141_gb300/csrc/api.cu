@@ -23,6 +23,11 @@ int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, voi
                         const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
                         const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
                         cudaStream_t st);
+size_t rsvd_workspace(int batch, int max_m, int max_n, const int* h_m, const int* h_n);
+int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                const int* hint, const int* kmax, double eps, int p, int rounds, unsigned long long seed,
+                void* const* dU, const int* LDU, void* const* dS, void* const* dV, const int* LDV, int* rank_out,
+                float* err_est, int* samples, int* info, void* ws, size_t ws_bytes, cudaStream_t st);
 }  // namespace bsvd
 
 using namespace bsvd;
@@ -70,7 +75,7 @@ extern "C" {
 
 const char* bsvd_version(void)
 {
-    return "bsvd-gb300 0.3 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD)";
+    return "bsvd-gb300 0.4 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD, randomized SVD)";
 }
 
 int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
@@ -199,6 +204,46 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
                : launch_block_jacobi<double>(batch, max_m, max_n, block_width, method, dA, d_m, d_n, d_lda, dS, dU,
                                              d_ldu, dV, d_ldv, tol, max_sweeps, d_info, d_rotations, workspace,
                                              workspace_bytes, st);
+}
+
+size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const int* h_m, const int* h_n)
+{
+    if (dtype != BSVD_F32 || batch < 0 || max_m < 0 || max_n < 0 || max_m > 256 || max_n > 256) return 0;
+    return rsvd_workspace(batch, max_m, max_n, h_m, h_n);
+}
+
+int batched_rsvd(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
+                 const int* d_lda, const int* d_rank_hint, double tol, int oversample, int max_rounds,
+                 unsigned long long seed, void* const* dU, const int* d_ldu, void* const* dS, void* const* dV,
+                 const int* d_ldv, const int* d_kmax, int* d_rank, float* d_err_est, int* d_samples, int* d_info,
+                 void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (dtype != BSVD_F32) return BSVD_ERR_UNSUPPORTED;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0) return -4;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (max_m > 256 || max_n > 256) return BSVD_ERR_UNSUPPORTED;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (!(tol >= 0.0 && tol < 1.0)) return -10;
+    if (oversample < 1 || oversample > 64) return -11;
+    if (max_rounds < 1 || max_rounds > 64) return -12;
+    if (!dU) return -14;
+    if (!d_ldu) return -15;
+    if (!dS) return -16;
+    if (!dV) return -17;
+    if (!d_ldv) return -18;
+    if (!d_kmax) return -19;
+    if (!d_rank) return -20;
+    if (!d_info) return -23;
+    if (!workspace) return -24;
+    return launch_rsvd(batch, max_m, max_n, dA, d_m, d_n, d_lda, d_rank_hint, d_kmax, tol, oversample, max_rounds, seed,
+                       dU, d_ldu, dS, dV, d_ldv, d_rank, d_err_est, d_samples, d_info, workspace, workspace_bytes,
+                       (cudaStream_t)stream);
 }
 
 }  // extern "C"

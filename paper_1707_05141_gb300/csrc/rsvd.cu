@@ -1,0 +1,606 @@
+// rsvd.cu -- batched randomized truncated SVD (Algorithm 4, Section 7), FP32.
+//
+// Every block b (m x n, any shape up to 256 x 256) is processed by one batched pipeline, all
+// blocks at once, sizes per block:
+//   plan     ||A||_F (FP64 sums), l = min(hint + p, l_cap), a block whose l reaches min(m, n) is
+//            full rank: it skips the randomized steps and is factored directly at the end.
+//   sample   Y = A [Omega | Omega_probe]: Omega (n x l) and 8 probe columns are generated on the
+//            fly from Philox (no Omega in memory), one batched GEMM.
+//   range    [Q, ~] = qr(Y);  power step: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
+//            (q = 1 step of randomized subspace iteration, the robust variant Section 7 mentions).
+//   project  B^T = A^T Q (n x l), [Q_B, R_B] = qr(B^T)   (Section 7, phase 2).
+//   small    SVD of R_B by one-sided Jacobi (register tier for l <= 64, shared tier to 128):
+//            R_B = U' S V'^T, so R_B^T = V' S U'^T and U = Q V', V = Q_B U'.
+//   estimate posterior error of the rank-l approximation from the probes (Halko et al. 4.3):
+//            est^2 = mean_j ||A w_j - U S V^T w_j||^2.  If est > (eps / 2) ||A||_F the block
+//            gets 8 more samples in the next round (the adaptive range finder); past the
+//            sample cap it falls back to the full SVD.
+//   finish   the smallest k with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 - 4 est^2 (FP64 sums,
+//            Section 8.2's relative Frobenius truncation), first k columns of U, V and k values
+//            of S to the caller.
+// Full-rank blocks go through batched_svd_jacobi's tiers (register / shared) or, for min(m, n)
+// above 128, the block-Jacobi tier, with per-block sizes (other blocks get size 0).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace bsvd {
+
+template <typename T>
+int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st);
+template <typename T>
+int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
+                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st);
+template <typename T>
+int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                       void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st);
+template <typename T>
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
+template <typename T>
+int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
+                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
+
+constexpr int kProbes = 8;     // probe columns of the posterior estimate
+constexpr int kLCap = 128;     // sample cap: the small SVD stays in the register / shared tiers
+constexpr int kMaxDim = 256;
+
+enum { RS_RSVD = 0, RS_FULL = 1, RS_DONE = 2 };
+enum { RSF_FALLBACK = 1, RSF_FROM_FULL = 2, RSF_NO_SCRATCH = 4 };
+
+struct RsState {
+    int m, n, k;       // k = min(m, n)
+    int ell;           // current number of samples
+    int mode;          // RS_*
+    int rank, flags, rounds;
+    double norm2;      // ||A||_F^2
+    double est2;       // posterior estimate of ||A - U S V^T||_F^2 (rank ell)
+    long long off;     // scratch offset (floats)
+    long long size;    // scratch size (floats)
+};
+
+// per-block scratch (floats) for bounds m, n
+__host__ __device__ inline long long rs_scratch_floats(int m, int n)
+{
+    const long long k = m < n ? m : n;
+    const long long l = k < kLCap ? k : kLCap;
+    const long long a = 255;  // 256-float alignment of every piece
+    auto al = [&](long long x) { return (x + a) & ~a; };
+    return al((long long)m * (l + kProbes)) + al((long long)n * l) + al((long long)n * l) + 3 * al(l * l) + al(k) +
+           al((long long)m * k) + al((long long)n * k);
+}
+
+// pointer / size arrays handed to the batched QR, Jacobi and GEMM stages
+struct RsArrays {
+    float** pY;    // m x (l + probes), ld m          (Y, then Q in its first l columns)
+    float** pZ;    // n x l, ld n                     (Z, then Qz)
+    float** pBt;   // n x l, ld n                     (B^T, then Q_B)
+    float** pR;    // l x l, ld l                     (R of each QR; R_B for the small SVD)
+    float** pUp;   // l x l, ld l                     (U' of R_B)
+    float** pVp;   // l x l, ld l                     (V' of R_B)
+    float** pS;    // k                               (singular values)
+    float** pUw;   // m x k, ld m                     (U before truncation)
+    float** pVw;   // n x k, ld n                     (V before truncation)
+    int *m_act, *n_act, *l_act, *lp_act;  // sizes for active randomized blocks (0 otherwise)
+    int *l_reg, *l_smem;                  // l for the small SVD: register tier (l <= 64) / shared
+    int *ld_m, *ld_n, *ld_l;
+    int *m_reg, *n_reg;                   // full-rank blocks for the register tier (0 otherwise)
+    int *m_smem, *n_smem;                 // ... for the shared tier
+    int *m_blk, *n_blk;                   // ... for the block tier (min(m, n) > 128)
+    int* info;                            // scratch info of the inner stages
+    RsState* st;
+};
+
+// ------------------------------------------------------------------------------------------------
+// batched GEMM  C (M x N) = op(A) (M x K) * B (K x N), FP32, per-block sizes.
+// op(A) = A (column-major, lda) or A^T; B either from memory (column-major, ldb) or, when
+// OMEGA, the Gaussian sampling stream: columns c < nOmega from stream 0, the rest from the
+// probe stream 1 (column c - nOmega).
+// 64 x 64 output tile per CTA, 256 threads with a 4 x 4 register tile, K staged 16 at a time.
+// ------------------------------------------------------------------------------------------------
+template <bool TRANS_A, bool OMEGA>
+__global__ void __launch_bounds__(256) gemm_batched_kernel(float* const* A, const int* LDA, float* const* B,
+                                                           const int* LDB, float* const* C, const int* LDC,
+                                                           const int* M, const int* N, const int* K,
+                                                           const int* NOMEGA, unsigned long long seed)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ float As[BK][BM + 4];
+    __shared__ float Bs[BK][BN + 4];
+    const int b = blockIdx.x;
+    const int Mb = M[b], Nb = N[b], Kb = K[b];
+    const int tm = blockIdx.y / ((kMaxDim + kProbes + BN - 1) / BN), tn = blockIdx.y % ((kMaxDim + kProbes + BN - 1) / BN);
+    const int m0 = tm * BM, n0 = tn * BN;
+    if (Mb <= 0 || Nb <= 0 || m0 >= Mb || n0 >= Nb) return;
+    const float* a = A[b];
+    const int lda = LDA[b];
+    const float* bm = OMEGA ? nullptr : B[b];
+    const int ldb = OMEGA ? 0 : LDB[b];
+    const int nom = OMEGA ? NOMEGA[b] : 0;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < Kb; k0 += BK) {
+        // A tile: op(A)(m0 + i, k0 + kk)
+        for (int e = tid; e < BM * BK; e += 256) {
+            int i, kk;
+            if (!TRANS_A) {
+                i = e % BM;
+                kk = e / BM;  // consecutive threads walk down a column of A
+            } else {
+                kk = e % BK;
+                i = e / BK;   // consecutive threads walk down a column of A (= a row of A^T)
+            }
+            const int gi = m0 + i, gk = k0 + kk;
+            float v = 0.f;
+            if (gi < Mb && gk < Kb) v = TRANS_A ? a[(size_t)gi * lda + gk] : a[(size_t)gk * lda + gi];
+            As[kk][i] = v;
+        }
+        // B tile: B(k0 + kk, n0 + j)
+        if (!OMEGA) {
+            for (int e = tid; e < BK * BN; e += 256) {
+                const int kk = e % BK, j = e / BK;
+                const int gk = k0 + kk, gj = n0 + j;
+                Bs[kk][j] = (gk < Kb && gj < Nb) ? bm[(size_t)gj * ldb + gk] : 0.f;
+            }
+        } else {
+            // 4 rows per Philox call: BK / 4 = 4 groups x 64 columns = 256 calls, one per thread
+            const int g = tid & 3, j = tid >> 2;
+            const int gj = n0 + j;
+            const int gk0 = k0 + 4 * g;
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gj < Nb && gk0 < Kb) {
+                const bool probe = gj >= nom;
+                z = gauss4(seed, (uint32_t)b, probe ? 1u : 0u, (uint32_t)(gk0 >> 2), (uint32_t)(probe ? gj - nom : gj));
+            }
+            Bs[4 * g + 0][j] = gk0 + 0 < Kb ? z.x : 0.f;
+            Bs[4 * g + 1][j] = gk0 + 1 < Kb ? z.y : 0.f;
+            Bs[4 * g + 2][j] = gk0 + 2 < Kb ? z.z : 0.f;
+            Bs[4 * g + 3][j] = gk0 + 3 < Kb ? z.w : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 av = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float* c = C[b];
+    const int ldc = LDC[b];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gj = n0 + tx * 4 + j;
+        if (gj >= Nb) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int gi = m0 + ty * 4 + i;
+            if (gi < Mb) c[(size_t)gj * ldc + gi] = acc[i][j];
+        }
+    }
+}
+
+template <bool TRANS_A, bool OMEGA>
+static int gemm(int batch, float* const* A, const int* LDA, float* const* B, const int* LDB, float* const* C,
+                const int* LDC, const int* M, const int* N, const int* K, const int* NOM, unsigned long long seed,
+                cudaStream_t st)
+{
+    constexpr int tiles = ((kMaxDim + 63) / 64) * ((kMaxDim + kProbes + 63) / 64);
+    gemm_batched_kernel<TRANS_A, OMEGA><<<dim3(batch, tiles), 256, 0, st>>>(A, LDA, B, LDB, C, LDC, M, N, K, NOM,
+                                                                            seed);
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
+// plan: sizes, ||A||_F^2, first sample count, scratch sizes
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rs_plan_kernel(int batch, int max_m, int max_n, float* const* A, const int* M,
+                                                      const int* N, const int* LDA, const int* hint, int p,
+                                                      RsState* st, int* info)
+{
+    const int b = blockIdx.x;
+    const int m = M[b], n = N[b], lda = LDA[b];
+    const bool bad = m < 0 || n < 0 || m > max_m || n > max_n || lda < (m > 1 ? m : 1);
+    __shared__ double red[8];
+    double s = 0.0;
+    if (!bad) {
+        const float* a = A[b];
+        for (int j = 0; j < n; ++j)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const double x = a[(size_t)j * lda + i];
+                s += x * x;
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        RsState r;
+        r.m = bad ? 0 : m;
+        r.n = bad ? 0 : n;
+        r.k = bad ? 0 : (m < n ? m : n);
+        const int h = hint ? hint[b] : 0;
+        int l = (h > 0 ? h : 0) + p;
+        if (l < 1) l = 1;
+        r.ell = l;
+        r.mode = bad || r.k == 0 ? RS_DONE : ((l >= r.k || l > kLCap) ? RS_FULL : RS_RSVD);
+        r.rank = 0;
+        r.flags = 0;
+        r.rounds = 0;
+        r.norm2 = t;
+        r.est2 = 0.0;
+        r.off = 0;
+        r.size = bad ? 0 : rs_scratch_floats(m, n);
+        st[b] = r;
+        info[b] = bad ? BSVD_INFO_BAD_SHAPE : 0;
+    }
+}
+
+// exclusive scan of the scratch sizes (one CTA; batch up to millions in a strided loop); a block
+// whose pieces would end past the workspace's capacity is not processed (flag, no writes)
+__global__ void __launch_bounds__(1024) rs_scan_kernel(int batch, RsState* st, long long capacity, int* info)
+{
+    __shared__ long long part[1024];
+    const int per = (batch + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    long long s = 0;
+    for (int b = b0; b < b0 + per && b < batch; ++b) s += st[b].size;
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    long long base = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int b = b0; b < b0 + per && b < batch; ++b) {
+        st[b].off = base;
+        base += st[b].size;
+        if (base > capacity && st[b].mode != RS_DONE) {
+            st[b].mode = RS_DONE;
+            st[b].flags |= RSF_NO_SCRATCH;
+            info[b] = BSVD_INFO_NO_SCRATCH;
+        }
+    }
+}
+
+// pointers and per-stage sizes; `final` selects the full-rank pass instead of a sampling round
+__global__ void rs_arrays_kernel(int batch, float* scratch, RsArrays ar, int final)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const RsState s = ar.st[b];
+    const int m = s.m, n = s.n, k = s.k;
+    const int lcap = k < kLCap ? k : kLCap;
+    const long long a = 255;
+    auto al = [&](long long x) { return (x + a) & ~a; };
+    float* base = scratch + s.off;
+    long long o = 0;
+    ar.pY[b] = base + o;   o += al((long long)m * (lcap + kProbes));
+    ar.pZ[b] = base + o;   o += al((long long)n * lcap);
+    ar.pBt[b] = base + o;  o += al((long long)n * lcap);
+    ar.pR[b] = base + o;   o += al((long long)lcap * lcap);
+    ar.pUp[b] = base + o;  o += al((long long)lcap * lcap);
+    ar.pVp[b] = base + o;  o += al((long long)lcap * lcap);
+    ar.pS[b] = base + o;   o += al(k);
+    ar.pUw[b] = base + o;  o += al((long long)m * k);
+    ar.pVw[b] = base + o;
+    const bool act = !final && s.mode == RS_RSVD;
+    const int l = act ? s.ell : 0;
+    ar.m_act[b] = act ? m : 0;
+    ar.n_act[b] = act ? n : 0;
+    ar.l_act[b] = l;
+    ar.lp_act[b] = act ? l + kProbes : 0;
+    ar.l_reg[b] = l <= 64 ? l : 0;
+    ar.l_smem[b] = l > 64 ? l : 0;
+    ar.ld_m[b] = m > 1 ? m : 1;
+    ar.ld_n[b] = n > 1 ? n : 1;
+    ar.ld_l[b] = l > 1 ? l : 1;
+    const bool full = final && s.mode == RS_FULL;
+    const int mm = m > n ? m : n;
+    const bool reg = full && k <= 64 && mm <= 128;
+    const bool blk = full && k > kLCap;
+    const bool smem = full && !reg && !blk;
+    ar.m_reg[b] = reg ? m : 0;
+    ar.n_reg[b] = reg ? n : 0;
+    ar.m_smem[b] = smem ? m : 0;
+    ar.n_smem[b] = smem ? n : 0;
+    ar.m_blk[b] = blk ? m : 0;
+    ar.n_blk[b] = blk ? n : 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// posterior estimate and the next round's decision (one CTA per active block)
+//   E = A Wp - Uw diag(S) (Vw^T Wp)  with A Wp = the probe columns of Y (kept since sampling)
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rs_estimate_kernel(RsArrays ar, unsigned long long seed, double eps, int p)
+{
+    __shared__ float t[kLCap][kProbes];   // S (Vw^T Wp)
+    __shared__ double red[8];
+    const int b = blockIdx.x;
+    RsState* s = ar.st + b;
+    if (s->mode != RS_RSVD) return;
+    const int m = s->m, n = s->n, l = s->ell;
+    const float* Vw = ar.pVw[b];
+    const float* Uw = ar.pUw[b];
+    const float* S = ar.pS[b];
+    const float* Y = ar.pY[b];
+    // t(c, j) = S_c * sum_r Vw(r, c) Wp(r, j); one warp per (c, j) pair
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int cj = warp; cj < l * kProbes; cj += 8) {
+        const int c = cj / kProbes, j = cj % kProbes;
+        float acc = 0.f;
+        for (int r = lane; r < n; r += 32) acc = fmaf(Vw[(size_t)c * n + r], gauss1(seed, (uint32_t)b, 1u, r, j), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) t[c][j] = acc * S[c];
+    }
+    __syncthreads();
+    double e = 0.0;
+    for (int ij = threadIdx.x; ij < m * kProbes; ij += blockDim.x) {
+        const int i = ij % m, j = ij / m;
+        float v = Y[(size_t)(l + j) * m + i];
+        for (int c = 0; c < l; ++c) v = fmaf(-Uw[(size_t)c * m + i], t[c][j], v);
+        e += (double)v * (double)v;
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) red[warp] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        const double est2 = tot / kProbes;
+        s->est2 = est2;
+        s->rounds += 1;
+        if (est2 <= 0.25 * eps * eps * s->norm2) {
+            s->mode = RS_DONE;  // range accepted: finish from this round's factors (l columns)
+        } else {
+            const int next = s->ell + p;
+            if (next >= s->k || next > kLCap) {
+                s->mode = RS_FULL;
+                s->est2 = 0.0;
+                s->flags |= RSF_FALLBACK;
+            } else {
+                s->ell = next;
+            }
+        }
+    }
+}
+
+// blocks still sampling after the last round fall back to the full SVD
+__global__ void rs_fallback_kernel(int batch, RsState* st)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < batch && st[b].mode == RS_RSVD) {
+        st[b].mode = RS_FULL;
+        st[b].est2 = 0.0;
+        st[b].flags |= RSF_FALLBACK;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// finish: truncation rank and the copy of the first k columns to the caller
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rs_finish_kernel(RsArrays ar, float* const* dU, const int* LDU, float* const* dS,
+                                                        float* const* dV, const int* LDV, const int* kmax, double eps,
+                                                        int* rank_out, float* err_est, int* samples, int* info)
+{
+    __shared__ int kk;
+    const int b = blockIdx.x;
+    RsState* s = ar.st + b;
+    if (info[b] == BSVD_INFO_BAD_SHAPE) return;
+    const int m = s->m, n = s->n;
+    if (s->flags & RSF_NO_SCRATCH) return;
+    const bool from_full = s->mode == RS_FULL;
+    const int ncol = from_full ? s->k : s->ell;  // columns available: all k, or the l samples
+    const float* S = ar.pS[b];
+    if (threadIdx.x == 0) {
+        // smallest k with sum_{i >= k} S_i^2 <= (0.95 eps)^2 ||A||^2 - 4 est^2: the 8-probe estimate
+        // of the range error is trusted to a factor 2 (its relative spread is about sqrt(2/8)), and
+        // 5% of eps is left for the FP32 factorisation's own residual (~1e-6 ||A||)
+        double thr = 0.9025 * eps * eps * s->norm2 - 4.0 * s->est2;
+        if (thr < 0.0) thr = 0.0;
+        double tail = 0.0;
+        int k = ncol;
+        for (int i = ncol - 1; i >= 0; --i) {
+            const double t2 = tail + (double)S[i] * (double)S[i];
+            if (t2 > thr) break;
+            tail = t2;
+            k = i;
+        }
+        const int cap = kmax[b];
+        int fl = (s->flags & RSF_FALLBACK) ? BSVD_INFO_FALLBACK : 0;
+        if (k > cap) {
+            fl |= BSVD_INFO_RANK_CAPPED;
+            k = cap;
+        }
+        kk = k;
+        s->rank = k;
+        rank_out[b] = k;
+        if (err_est) err_est[b] = s->norm2 > 0.0 ? (float)sqrt(s->est2 / s->norm2) : 0.f;
+        if (samples) samples[b] = ncol;
+        info[b] = fl | s->rounds;
+    }
+    __syncthreads();
+    const int k = kk;
+    const float* Uw = ar.pUw[b];
+    const float* Vw = ar.pVw[b];
+    float* u = dU[b];
+    float* v = dV[b];
+    const int ldu = LDU[b], ldv = LDV[b];
+    for (int c = 0; c < k; ++c) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) u[(size_t)c * ldu + i] = Uw[(size_t)c * m + i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) v[(size_t)c * ldv + i] = Vw[(size_t)c * n + i];
+    }
+    for (int c = threadIdx.x; c < k; c += blockDim.x) dS[b][c] = S[c];
+}
+
+// ------------------------------------------------------------------------------------------------
+// host driver
+// ------------------------------------------------------------------------------------------------
+struct RsFixed {
+    size_t off_state, off_ptr, off_int, off_bjws, bj_bytes, off_scratch;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int kPtrArrays = 9, kIntArrays = 17;
+
+static RsFixed rs_fixed(int batch, int max_m, int max_n)
+{
+    RsFixed F;
+    size_t o = 0;
+    F.off_state = o;
+    o = al256(o + sizeof(RsState) * (size_t)batch);
+    F.off_ptr = o;
+    o = al256(o + sizeof(float*) * (size_t)batch * kPtrArrays);
+    F.off_int = o;
+    o = al256(o + sizeof(int) * (size_t)batch * kIntArrays);
+    F.off_bjws = o;
+    const int kmx = max_m < max_n ? max_m : max_n;
+    F.bj_bytes = kmx > kLCap ? block_jacobi_workspace<float>(batch, max_m, max_n, 32, 0) : 0;
+    o = al256(o + F.bj_bytes);
+    F.off_scratch = o;
+    return F;
+}
+
+size_t rsvd_workspace(int batch, int max_m, int max_n, const int* h_m, const int* h_n)
+{
+    const RsFixed F = rs_fixed(batch, max_m, max_n);
+    size_t fl = 0;
+    for (int b = 0; b < batch; ++b) {
+        const int m = h_m ? h_m[b] : max_m, n = h_n ? h_n[b] : max_n;
+        fl += (size_t)rs_scratch_floats(m < 0 ? 0 : m, n < 0 ? 0 : n);
+    }
+    return F.off_scratch + al256(fl * sizeof(float));
+}
+
+int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                const int* hint, const int* kmax, double eps, int p, int rounds, unsigned long long seed,
+                void* const* dU, const int* LDU, void* const* dS, void* const* dV, const int* LDV, int* rank_out,
+                float* err_est, int* samples, int* info, void* ws, size_t ws_bytes, cudaStream_t st)
+{
+    if (max_m > kMaxDim || max_n > kMaxDim) return BSVD_ERR_UNSUPPORTED;
+    const RsFixed F = rs_fixed(batch, max_m, max_n);
+    if (ws_bytes < F.off_scratch) return BSVD_ERR_WORKSPACE;
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    RsArrays ar;
+    ar.st = reinterpret_cast<RsState*>(w + F.off_state);
+    float** pp = reinterpret_cast<float**>(w + F.off_ptr);
+    float*** slots[kPtrArrays] = {&ar.pY, &ar.pZ, &ar.pBt, &ar.pR, &ar.pUp, &ar.pVp, &ar.pS, &ar.pUw, &ar.pVw};
+    for (int i = 0; i < kPtrArrays; ++i) *slots[i] = pp + (size_t)i * batch;
+    int* ip = reinterpret_cast<int*>(w + F.off_int);
+    int** islots[kIntArrays] = {&ar.m_act, &ar.n_act, &ar.l_act, &ar.lp_act, &ar.l_reg, &ar.l_smem,
+                                &ar.ld_m, &ar.ld_n, &ar.ld_l, &ar.m_reg, &ar.n_reg, &ar.m_smem,
+                                &ar.n_smem, &ar.m_blk, &ar.n_blk, &ar.info, nullptr};
+    for (int i = 0; i < kIntArrays; ++i)
+        if (islots[i]) *islots[i] = ip + (size_t)i * batch;
+    float* scratch = reinterpret_cast<float*>(w + F.off_scratch);
+    const long long capacity = (long long)((ws_bytes - F.off_scratch) / sizeof(float));
+
+    rs_plan_kernel<<<batch, 256, 0, st>>>(batch, max_m, max_n, (float* const*)A, M, N, LDA, hint, p, ar.st, info);
+    rs_scan_kernel<<<1, 1024, 0, st>>>(batch, ar.st, capacity, info);
+    if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    const int tb = (batch + 127) / 128;
+    float* const* fA = (float* const*)A;
+    const int mx = max_m, nx = max_n;
+    const int kx = mx < nx ? mx : nx;
+    const int lx = kx < kLCap ? kx : kLCap;
+    int rc = BSVD_SUCCESS;
+    for (int r = 0; r < rounds && rc == BSVD_SUCCESS && lx > 0; ++r) {
+        rs_arrays_kernel<<<tb, 128, 0, st>>>(batch, scratch, ar, 0);
+        // sample: Y = A [Omega | probes]
+        rc = gemm<false, true>(batch, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act, ar.n_act,
+                               ar.l_act, seed, st);
+        if (rc) break;
+        rc = launch_qr<float>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY,
+                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+        if (rc) break;
+        // power step: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
+        rc = gemm<true, false>(batch, fA, LDA, ar.pY, ar.ld_m, ar.pZ, ar.ld_n, ar.n_act, ar.l_act, ar.m_act, nullptr,
+                               seed, st);
+        if (rc) break;
+        rc = launch_qr<float>(batch, nx, lx, (void* const*)ar.pZ, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pZ,
+                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+        if (rc) break;
+        rc = gemm<false, false>(batch, fA, LDA, ar.pZ, ar.ld_n, ar.pY, ar.ld_m, ar.m_act, ar.l_act, ar.n_act, nullptr,
+                                seed, st);
+        if (rc) break;
+        rc = launch_qr<float>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY,
+                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+        if (rc) break;
+        // project: B^T = A^T Q, [Q_B, R_B] = qr(B^T)
+        rc = gemm<true, false>(batch, fA, LDA, ar.pY, ar.ld_m, ar.pBt, ar.ld_n, ar.n_act, ar.l_act, ar.m_act, nullptr,
+                               seed, st);
+        if (rc) break;
+        rc = launch_qr<float>(batch, nx, lx, (void* const*)ar.pBt, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pBt,
+                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+        if (rc) break;
+        // small SVD of R_B (l x l): register tier up to 64, shared tier above
+        const int lr = lx < 64 ? lx : 64;
+        rc = launch_jacobi_reg<float>(batch, lr, lr, 0, (void* const*)ar.pR, ar.l_reg, ar.l_reg, ar.ld_l,
+                                      (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
+                                      ar.ld_l, 0.0, 0, ar.info, nullptr, st);
+        if (rc) break;
+        if (lx > 64) {
+            rc = launch_jacobi_smem<float>(batch, lx, lx, (void* const*)ar.pR, ar.l_smem, ar.l_smem, ar.ld_l,
+                                           (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
+                                           ar.ld_l, 0.0, 0, ar.info, nullptr, st);
+            if (rc) break;
+        }
+        // U = Q V', V = Q_B U'
+        rc = gemm<false, false>(batch, ar.pY, ar.ld_m, ar.pVp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act, ar.l_act,
+                                nullptr, seed, st);
+        if (rc) break;
+        rc = gemm<false, false>(batch, ar.pBt, ar.ld_n, ar.pUp, ar.ld_l, ar.pVw, ar.ld_n, ar.n_act, ar.l_act, ar.l_act,
+                                nullptr, seed, st);
+        if (rc) break;
+        rs_estimate_kernel<<<batch, 256, 0, st>>>(ar, seed, eps, p);
+        if (cudaGetLastError() != cudaSuccess) rc = BSVD_ERR_CUDA;
+    }
+    if (rc) return rc;
+    // full-rank blocks, and blocks whose estimate never passed, by the direct Jacobi tiers
+    rs_fallback_kernel<<<tb, 128, 0, st>>>(batch, ar.st);
+    rs_arrays_kernel<<<tb, 128, 0, st>>>(batch, scratch, ar, 1);
+    if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    const int mm_x = mx > nx ? mx : nx;
+    if (kx > 0) {
+        // bounds cover every block routed to each tier (max(m, n), min(m, n) order is what counts)
+        rc = launch_jacobi_reg<float>(batch, mm_x < 128 ? mm_x : 128, kx < 64 ? kx : 64, 0, A, ar.m_reg, ar.n_reg, LDA,
+                                      (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n,
+                                      0.0, 0, ar.info, nullptr, st);
+        if (rc) return rc;
+        if (mm_x > 128 || kx > 64) {
+            rc = launch_jacobi_smem<float>(batch, mm_x, kx < kLCap ? kx : kLCap, A, ar.m_smem, ar.n_smem, LDA,
+                                           (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw,
+                                           ar.ld_n, 0.0, 0, ar.info, nullptr, st);
+            if (rc) return rc;
+        }
+        if (kx > kLCap) {
+            rc = launch_block_jacobi<float>(batch, mx, nx, 32, 0, A, ar.m_blk, ar.n_blk, LDA, (void* const*)ar.pS,
+                                            (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n, 0.0, 0,
+                                            ar.info, nullptr, w + F.off_bjws, F.bj_bytes, st);
+            if (rc) return rc;
+        }
+    }
+    rs_finish_kernel<<<batch, 256, 0, st>>>(ar, (float* const*)dU, LDU, (float* const*)dS, (float* const*)dV, LDV, kmax,
+                                            eps, rank_out, err_est, samples, info);
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
+
+}  // namespace bsvd
