@@ -227,3 +227,81 @@ def workload3(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: flo
                      for m, n, r0 in zip(ms, ns, r0s)], dtype=np.int32)
     return RaggedBatch(m=np.array(ms, np.int32), n=np.array(ns, np.int32), offset=off, flat=flat,
                        sigma=sig, extra={"r0": np.array(r0s), "rank_hint": hint})
+
+
+# ----------------------------------------------------------------------------------------------
+# workload 4: admissible blocks of an exponential covariance kernel over 3D points
+# ----------------------------------------------------------------------------------------------
+
+def _kd_tree(pts: np.ndarray, leaf: int):
+    """Median split along the widest side of each box; returns (perm, nodes) with nodes as
+    (start, end, lo, hi, children) in the permuted order."""
+    perm = np.arange(len(pts))
+    nodes = []
+
+    def build(start, end):
+        p = pts[perm[start:end]]
+        lo, hi = p.min(axis=0), p.max(axis=0)
+        idx = len(nodes)
+        nodes.append([start, end, lo, hi, None])
+        if end - start > leaf:
+            d = int(np.argmax(hi - lo))
+            order = np.argsort(p[:, d], kind="stable")
+            perm[start:end] = perm[start:end][order]
+            mid = (start + end) // 2
+            c0 = build(start, mid)
+            c1 = build(mid, end)
+            nodes[idx][4] = (c0, c1)
+        return idx
+
+    build(0, len(pts))
+    return perm, nodes
+
+
+def _admissible(a, b, eta):
+    da = float(np.linalg.norm(a[3] - a[2]))
+    db = float(np.linalg.norm(b[3] - b[2]))
+    gap = np.maximum(0.0, np.maximum(a[2] - b[3], b[2] - a[3]))
+    return min(da, db) <= eta * float(np.linalg.norm(gap))
+
+
+def workload4(n_points: int = 32768, seed_index: int = 0, leaf: int = 64, eta: float = 1.1, ell: float = 0.1,
+              lo: int = 64, hi: int = 256, max_blocks: int | None = None) -> RaggedBatch:
+    """Admissible blocks K(t, s) = exp(-|x - y| / ell) of the dual traversal of a k-d tree over
+    ``n_points`` uniform points in the unit cube, kept when lo <= |t|, |s| <= hi."""
+    u = uniforms(4, seed_index, TAG_MISC, 3 * n_points).reshape(n_points, 3)
+    perm, nodes = _kd_tree(u, leaf)
+    pts = u[perm]
+    pairs = []
+    stack = [(0, 0)]
+    while stack:
+        t, s = stack.pop()
+        a, b = nodes[t], nodes[s]
+        if _admissible(a, b, eta):
+            if lo <= a[1] - a[0] <= hi and lo <= b[1] - b[0] <= hi:
+                pairs.append((t, s))
+            continue
+        if a[4] is None or b[4] is None:
+            continue                       # a dense (inadmissible) leaf: not part of this workload
+        for c in a[4]:
+            for d in b[4]:
+                stack.append((c, d))
+    pairs.sort()
+    if max_blocks is not None:
+        pairs = pairs[:max_blocks]
+    ms = [nodes[t][1] - nodes[t][0] for t, _ in pairs]
+    ns = [nodes[s][1] - nodes[s][0] for _, s in pairs]
+    off, flat = _pack(ms, ns, np.float32)
+
+    def one(i):
+        t, s = pairs[i]
+        x = pts[nodes[t][0]:nodes[t][1]]
+        y = pts[nodes[s][0]:nodes[s][1]]
+        d = np.sqrt(((x[:, None, :] - y[None, :, :]) ** 2).sum(-1))
+        blk = np.exp(-d / ell)
+        flat[off[i]:off[i] + blk.size] = blk.T.reshape(-1).astype(np.float32)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        list(ex.map(one, range(len(pairs)), chunksize=256))
+    return RaggedBatch(m=np.array(ms, np.int32), n=np.array(ns, np.int32), offset=off, flat=flat,
+                       extra={"pairs": pairs, "n_points": n_points, "eta": eta})

@@ -212,6 +212,38 @@ int batched_rsvd(int dtype, int batch, int max_m, int max_n,
                  const int* d_kmax, int* d_rank, float* d_err_est, int* d_samples, int* d_info,
                  void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Learned rank predictor (no counterpart in the paper: the project's addition that chooses the
+ * first sample count of batched_rsvd; the adaptive range finder remains the fallback and the
+ * judge of every result).  FP32, device arrays, asynchronous on `stream`.
+ */
+#define BSVD_SKETCH_FEATURES 16
+#define BSVD_MLP_PARAMS 5313 /* W1 64x16, b1 64, W2 64x64, b2 64, w3 64, b3 1 (row-major) */
+
+/* bsvd_sketch_features -- 16 features per matrix (m, n <= 256) from column norms and 8 Gaussian
+ * probes (Philox stream 2 under `seed`): layout d_features[b * 16 + i]; see mlp.cu for the list. */
+int bsvd_sketch_features(int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
+                         const int* d_lda, unsigned long long seed, float* d_features, void* stream);
+
+/* bsvd_mlp_forward -- y = w3 . relu(W2 relu(W1 f + b1) + b2) + b3 for each feature row (y estimates
+ * log(rank + 1)).  d_out (nullable) receives y; d_rank_hint (nullable) receives
+ * clamp(ceil(exp(y) - 1 + margin), 1, min(m, n)) (min(m, n) only when d_m, d_n are given). */
+int bsvd_mlp_forward(int batch, const float* d_features, const float* d_params, float* d_out, int* d_rank_hint,
+                     float margin, const int* d_m, const int* d_n, void* stream);
+
+/* bsvd_mlp_grad -- gradient of L = 1/(2B) sum_b (y_b - target_b)^2 with respect to the parameters:
+ * d_grad (BSVD_MLP_PARAMS floats) and d_loss (one float) are overwritten. */
+int bsvd_mlp_grad(int batch, const float* d_features, const float* d_target, const float* d_params, float* d_grad,
+                  float* d_loss, void* stream);
+
+/* bsvd_mlp_adam -- one Adam step (Kingma & Ba 2015) on the parameters; m, v moment buffers of
+ * nparams floats (start at zero), step >= 1. */
+int bsvd_mlp_adam(int nparams, float* d_params, const float* d_grad, float* d_m, float* d_v, int step, float lr,
+                  float beta1, float beta2, float eps, void* stream);
+
+/* Number of parameters of the rank predictor (BSVD_MLP_PARAMS). */
+int bsvd_mlp_param_count(void);
+
 /* Size of the library-owned scratch array used by batched_svd_block_jacobi_noalloc (64 MiB). */
 #define BSVD_NOALLOC_SCRATCH_BYTES (64u << 20)
 #define BSVD_ERR_SCRATCH_LIMIT (-1003) /* the call needs more than BSVD_NOALLOC_SCRATCH_BYTES */

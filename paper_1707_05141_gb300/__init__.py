@@ -72,6 +72,17 @@ def lib() -> ctypes.CDLL:
             L.batched_rsvd.restype = i
             L.batched_rsvd.argtypes = [i, i, i, i, p, p, p, p, p, d, i, i, ctypes.c_ulonglong, p, p, p, p, p, p, p,
                                        p, p, p, p, ctypes.c_size_t, p]
+            L.bsvd_sketch_features.restype = i
+            L.bsvd_sketch_features.argtypes = [i, i, i, p, p, p, p, ctypes.c_ulonglong, p, p]
+            L.bsvd_mlp_forward.restype = i
+            L.bsvd_mlp_forward.argtypes = [i, p, p, p, p, ctypes.c_float, p, p, p]
+            L.bsvd_mlp_grad.restype = i
+            L.bsvd_mlp_grad.argtypes = [i, p, p, p, p, p, p]
+            L.bsvd_mlp_adam.restype = i
+            L.bsvd_mlp_adam.argtypes = [i, p, p, p, p, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, p]
+            L.bsvd_mlp_param_count.restype = i
+            L.bsvd_mlp_param_count.argtypes = []
             L.batched_svd_block_jacobi_noalloc.restype = i
             L.batched_svd_block_jacobi_noalloc.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, i, p, p,
                                                            p]
@@ -231,6 +242,36 @@ def batched_rsvd(A: Batch, U: Batch, S: Batch, V: Batch, kmax, rank, info, works
     _check("batched_rsvd", rc)
 
 
+SKETCH_FEATURES = 16
+MLP_PARAMS = 5313
+
+
+def bsvd_sketch_features(A: Batch, features, seed: int = 0, stream=None) -> None:
+    """16 sketch features per matrix into ``features`` (batch x 16 FP32 device tensor)."""
+    _check("bsvd_sketch_features", lib().bsvd_sketch_features(A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m),
+                                                               _ptr(A.n), _ptr(A.ld), int(seed), _ptr(features),
+                                                               _stream_ptr(stream)))
+
+
+def bsvd_mlp_forward(features, params, out=None, hint=None, margin: float = 2.0, m=None, n=None, stream=None):
+    batch = int(features.shape[0])
+    _check("bsvd_mlp_forward", lib().bsvd_mlp_forward(batch, _ptr(features), _ptr(params), _ptr(out), _ptr(hint),
+                                                       float(margin), _ptr(m), _ptr(n), _stream_ptr(stream)))
+
+
+def bsvd_mlp_grad(features, target, params, grad, loss, stream=None):
+    batch = int(features.shape[0])
+    _check("bsvd_mlp_grad", lib().bsvd_mlp_grad(batch, _ptr(features), _ptr(target), _ptr(params), _ptr(grad),
+                                                 _ptr(loss), _stream_ptr(stream)))
+
+
+def bsvd_mlp_adam(params, grad, mom, vel, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None):
+    _check("bsvd_mlp_adam", lib().bsvd_mlp_adam(int(params.numel()), _ptr(params), _ptr(grad), _ptr(mom), _ptr(vel),
+                                                 int(step), float(lr), float(beta1), float(beta2), float(eps),
+                                                 _stream_ptr(stream)))
+
+
 class RsvdResult:
     """Outputs of ``rsvd``: flat device buffers plus per-matrix views on the host side."""
 
@@ -265,7 +306,12 @@ def rsvd(flat, offsets, m, n, rank_hint=None, kmax=None, tol: float = 1e-5, over
     V = Batch.packed(fv, ov, n, km)
     S = Batch.packed(fs, os_, km, np.ones_like(km))
     kmax_d = torch.as_tensor(km, dtype=torch.int32).to(dev)
-    hint_d = None if rank_hint is None else torch.as_tensor(np.asarray(rank_hint, np.int32)).to(dev)
+    if rank_hint is None:
+        hint_d = None
+    elif isinstance(rank_hint, torch.Tensor):
+        hint_d = rank_hint.to(device=dev, dtype=torch.int32).contiguous()
+    else:
+        hint_d = torch.as_tensor(np.asarray(rank_hint, np.int32)).to(dev)
     rank = torch.zeros(bsz, dtype=torch.int32, device=dev)
     info = torch.zeros(bsz, dtype=torch.int32, device=dev)
     err = torch.zeros(bsz, dtype=torch.float32, device=dev)

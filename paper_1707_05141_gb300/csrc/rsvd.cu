@@ -342,12 +342,23 @@ __global__ void __launch_bounds__(256) rs_estimate_kernel(RsArrays ar, unsigned 
     const float* Uw = ar.pUw[b];
     const float* S = ar.pS[b];
     const float* Y = ar.pY[b];
+    // the probe columns Wp (n x 8), four rows per Philox call
+    __shared__ float wp[kMaxDim][kProbes];
+    for (int e = threadIdx.x; e < ((n + 3) / 4) * kProbes; e += blockDim.x) {
+        const int g = e / kProbes, j = e % kProbes;
+        const float4 z = gauss4(seed, (uint32_t)b, 1u, (uint32_t)g, (uint32_t)j);
+        wp[4 * g][j] = z.x;
+        if (4 * g + 1 < n) wp[4 * g + 1][j] = z.y;
+        if (4 * g + 2 < n) wp[4 * g + 2][j] = z.z;
+        if (4 * g + 3 < n) wp[4 * g + 3][j] = z.w;
+    }
+    __syncthreads();
     // t(c, j) = S_c * sum_r Vw(r, c) Wp(r, j); one warp per (c, j) pair
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int cj = warp; cj < l * kProbes; cj += 8) {
         const int c = cj / kProbes, j = cj % kProbes;
         float acc = 0.f;
-        for (int r = lane; r < n; r += 32) acc = fmaf(Vw[(size_t)c * n + r], gauss1(seed, (uint32_t)b, 1u, r, j), acc);
+        for (int r = lane; r < n; r += 32) acc = fmaf(Vw[(size_t)c * n + r], wp[r][j], acc);
         acc = warp_sum(acc);
         if (lane == 0) t[c][j] = acc * S[c];
     }
