@@ -1,12 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark of the batched Jacobi SVD / Householder QR path on one GB300 (or N, weak scaling).
+"""Benchmark of the batched QR / Jacobi SVD / randomized SVD path on one GB300 (or N, weak scaling).
 
-Default workload ("svd64_qr128"): one step = batched Householder QR of 20000 FP32 128 x 32
-matrices + batched one-sided Jacobi SVD (U, S, V) of 20000 FP32 64 x 64 matrices, the matrices
-built as U diag(sigma) V^T with Haar U, V and sigma_i = exp(-i/8).  The metric is SVDs per second
-(whole job); inputs are resident in HBM (656 MB, larger than the 129 MB L2) when the timed region
-starts.  Also reported: the dominant kernel against its roofline, an end-to-end figure through
-the public API with host buffers, and the FP64 oracle on the host cores as the CPU baseline.
+Default workload ``svd64_qr128``: one step = batched Householder QR of 20000 FP32 128 x 32 matrices
++ batched one-sided Jacobi SVD (U, S, V) of 20000 FP32 64 x 64 matrices (A = U diag(sigma) V^T,
+Haar U, V, sigma_i = exp(-i/8)).  Metric: SVDs per second, whole job; inputs resident in HBM
+(656 MB, larger than the 129 MB L2) when the timed region starts.
+
+Other workloads (``--workload``), each printing its own line:
+  fp64_32      1000 FP64 32 x 32 Jacobi SVDs + QRs, sigma_i = 10^(-8 i/31)
+  block512     500 FP32 512 x 512 block-Jacobi SVDs (GRAM, block width 32), sigma log-uniform
+  rsvd_uneven  16384 uneven blocks (m, n in {64, 128, 256}), randomized SVD to 1e-5 with the
+               generator's rank as hint, the whole call captured in a CUDA graph
+  hmatrix_mlp  ~52000 kernel blocks exp(-|x-y|/0.1) (3D points, k-d tree, leaf 64): randomized
+               SVD to 1e-5 with ranks predicted by the learned network vs the plain adaptive method
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 """
@@ -30,11 +36,20 @@ import numpy as np  # noqa: E402
 
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.070 GHz maximum SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# FP64 peak of the part (GB300 data sheet figure, for the FP64 workload only)
+# FP64 peak of the part (GB300 data sheet figure)
 FP64_PEAK_TFLOPS = 1.25
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only for
-# the kernel source it was taken on (the digest guards against reporting stale counters).
+
+def measured_hbm_gbs() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+# DRAM bytes (read + write) per launch of a dominant kernel from one ncu capture, keyed by the
+# digest of the kernel source it was taken on (a changed kernel reports null, not stale counters).
 TRAFFIC = {}
 
 
@@ -102,180 +117,579 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------------------------
-# workload
-# ----------------------------------------------------------------------------------------------
-
 def jacobi_flops(m, n, info, rots):
-    """Algorithmic flops of one-sided Jacobi: every visited pair costs its 2x2 Gram (6m), every
-    applied rotation 6(m + n) (A and V columns); sweeps = info (or info - NOT_CONVERGED)."""
+    """Algorithmic flops of one-sided Jacobi: every visited pair costs its 2x2 Gram (6 max(m,n)),
+    every applied rotation 6(m + n) (A and V columns); sweeps = info (or info - NOT_CONVERGED)."""
+    info = np.asarray(info)
     sweeps = np.where(info >= (1 << 20), info - (1 << 20), info).astype(np.float64)
     k = min(m, n)
     mm = max(m, n)
-    return float(np.sum(sweeps * (k * (k - 1) / 2) * 6 * mm + rots.astype(np.float64) * 6 * (m + n)))
+    return float(np.sum(sweeps * (k * (k - 1) / 2) * 6 * mm + np.asarray(rots, np.float64) * 6 * (m + n)))
 
 
-def qr_flops(m, n):
-    return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0 + 4.0 * m * n * n - 4.0 * n ** 3 / 3.0  # factor + form Q
+def max_over_ranks(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
 
 
-def make_inputs(rank: int, svd_batch: int, qr_batch: int):
-    import gen
-    a_svd = gen.workload1_svd(batch=svd_batch, first=rank * svd_batch)
-    a_qr = gen.workload1_qr(batch=qr_batch, first=rank * qr_batch)
-    return a_svd, a_qr
+# ----------------------------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------------------------
+
+class SvdQr64:
+    """20000 x (64 x 64) FP32 Jacobi SVD + 20000 x (128 x 32) FP32 QR per GPU per step."""
+    name = "svd64_qr128"
+    metric = "batched SVDs/s (64x64 FP32 Jacobi SVD + 128x32 FP32 QR per SVD)"
+    unit = "SVDs/s"
+    dtype = "f32"
+
+    def __init__(self, args):
+        self.args = args
+        self.nb, self.nq = args.svd_batch, args.qr_batch
+
+    def config(self, world):
+        return {"workload": "svd64_qr128: Jacobi SVD (U,S,V) of 20000 FP32 64x64 + Householder QR (Q,R) of 20000 "
+                            "FP32 128x32 per GPU per step; sigma_i = exp(-i/8), Haar U, V",
+                "svd_batch_per_gpu": self.nb, "qr_batch_per_gpu": self.nq, "m": 64, "n": 64, "qr_m": 128,
+                "qr_n": 32, "l2": "inputs (656 MB per GPU) larger than L2; no flush",
+                "parallelism": f"independent batches per GPU x{world}"}
+
+    def setup(self, rank, dev):
+        import torch
+        import gen
+        import paper_1707_05141_gb300 as bs
+        from paper_1707_05141_gb300 import autotune
+        self.bs = bs
+        a_svd = gen.workload1_svd(batch=self.nb, first=rank * self.nb)
+        a_qr = gen.workload1_qr(batch=self.nq, first=rank * self.nq)
+        self.h_in = [torch.from_numpy(a_svd.a).pin_memory(), torch.from_numpy(a_qr.a).pin_memory()]
+        self.d_svd, self.d_qr = (h.to(dev) for h in self.h_in)
+        m = n = k = 64
+        self.A = bs.Batch.uniform(self.d_svd, m, n)
+        self.S = torch.empty((self.nb, 1, k), device=dev)
+        self.U = torch.empty((self.nb, k, m), device=dev)
+        self.V = torch.empty((self.nb, k, n), device=dev)
+        self.Sb, self.Ub, self.Vb = bs.Batch.uniform(self.S, k, 1), bs.Batch.uniform(self.U, m, k), bs.Batch.uniform(self.V, n, k)
+        self.info = torch.empty(self.nb, dtype=torch.int32, device=dev)
+        self.rots = torch.empty(self.nb, dtype=torch.int64, device=dev)
+        self.AQ = bs.Batch.uniform(self.d_qr, 128, 32)
+        self.Q = torch.empty((self.nq, 32, 128), device=dev)
+        self.R = torch.empty((self.nq, 32, 32), device=dev)
+        self.Qb, self.Rb = bs.Batch.uniform(self.Q, 128, 32), bs.Batch.uniform(self.R, 32, 32)
+        self.qinfo = torch.empty(self.nq, dtype=torch.int32, device=dev)
+        self.tuned = autotune.tune_jacobi(self.d_svd, m, n)
+        self.outs = [self.S, self.U, self.V, self.Q, self.R]
+        self.d_in = [self.d_svd, self.d_qr]
+
+    def step(self, stream, kev=None):
+        self.bs.batched_qr(self.AQ, self.Qb, self.Rb, self.qinfo, stream)
+        if kev is not None:
+            kev[0].record(stream)
+        self.bs.batched_svd_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.rots, stream=stream)
+        if kev is not None:
+            kev[1].record(stream)
+
+    launches_per_step = 2
+    units = property(lambda self: self.nb)
+
+    def roofline(self, kernel_ms):
+        bs = self.bs
+        info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
+        assert np.all(info_h > 0), "Jacobi reported a bad shape"
+        fl = jacobi_flops(64, 64, info_h, rots_h)
+        achieved = fl / (kernel_ms * 1e-3) / 1e12
+        tier = int(self.tuned["tier"])
+        reg = (tier & 0xff) == bs.TIER_REGISTER
+        kname = ("jacobi_reg_kernel" if reg else "jacobi_smem_kernel") + f" (tier {tier:#x})"
+        traffic = TRAFFIC.get(kernel_digest("jacobi_reg.cu" if reg else "jacobi_smem.cu"))
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "ms_per_launch": kernel_ms,
+                "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (max SM clock)"}
+        detail = {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
+                  "jacobi_gflop_per_launch": fl / 1e9, "autotune": self.tuned}
+        return roof, detail
+
+    def cpu_sample(self, n):
+        import gen
+        import oracle
+        a_svd = gen.workload1_svd(batch=n)
+        a_qr = gen.workload1_qr(batch=n)
+        cores = oracle.default_threads()
+        mats, qmats = [a_svd.a64(i) for i in range(n)], [a_qr.a64(i) for i in range(n)]
+        t0 = time.time()
+        oracle.svd_batch(mats, nthreads=cores)
+        oracle.qr_batch(qmats, nthreads=cores)
+        dt = time.time() - t0
+        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+                "sample": f"{n} SVDs of 64x64 + {n} QRs of 128x32 (same generator), FP64, {dt:.2f} s wall"}
 
 
-def run_ours(args, rank, world, local_rank):
+class Fp64_32:
+    """1000 x (32 x 32) FP64 Jacobi SVD + QR of the same matrices."""
+    name = "fp64_32"
+    metric = "batched SVDs/s (32x32 FP64 Jacobi SVD + 32x32 FP64 QR per SVD)"
+    unit = "SVDs/s"
+    dtype = "f64"
+    launches_per_step = 2
+
+    def __init__(self, args):
+        self.args = args
+        self.nb = 1000
+
+    def config(self, world):
+        return {"workload": "fp64_32: Jacobi SVD (U,S,V) and Householder QR of 1000 FP64 32x32 per GPU per step; "
+                            "sigma_i = 10^(-8 i/31)", "batch_per_gpu": self.nb,
+                "l2": "8 MB inputs fit in L2: each step reads them once; compute bound",
+                "parallelism": f"independent batches per GPU x{world}"}
+
+    def setup(self, rank, dev):
+        import torch
+        import gen
+        import paper_1707_05141_gb300 as bs
+        from paper_1707_05141_gb300 import autotune
+        self.bs = bs
+        b = gen.workload0(batch=self.nb, first=rank * self.nb)
+        self.h_in = [torch.from_numpy(b.a).pin_memory()]
+        self.d = self.h_in[0].to(dev)
+        self.d_in = [self.d]
+        k = 32
+        self.A = bs.Batch.uniform(self.d, 32, 32)
+        self.S = torch.empty((self.nb, 1, k), device=dev, dtype=torch.float64)
+        self.U = torch.empty((self.nb, k, 32), device=dev, dtype=torch.float64)
+        self.V = torch.empty((self.nb, k, 32), device=dev, dtype=torch.float64)
+        self.Q = torch.empty((self.nb, 32, 32), device=dev, dtype=torch.float64)
+        self.R = torch.empty((self.nb, 32, 32), device=dev, dtype=torch.float64)
+        self.Sb, self.Ub, self.Vb = (bs.Batch.uniform(self.S, k, 1), bs.Batch.uniform(self.U, 32, k),
+                                     bs.Batch.uniform(self.V, 32, k))
+        self.Qb, self.Rb = bs.Batch.uniform(self.Q, 32, 32), bs.Batch.uniform(self.R, 32, 32)
+        self.info = torch.empty(self.nb, dtype=torch.int32, device=dev)
+        self.qinfo = torch.empty(self.nb, dtype=torch.int32, device=dev)
+        self.rots = torch.empty(self.nb, dtype=torch.int64, device=dev)
+        self.tuned = autotune.tune_jacobi(self.d, 32, 32, sample=self.nb)
+        self.outs = [self.S, self.U, self.V, self.Q, self.R]
+
+    def step(self, stream, kev=None):
+        self.bs.batched_qr(self.A, self.Qb, self.Rb, self.qinfo, stream)
+        if kev is not None:
+            kev[0].record(stream)
+        self.bs.batched_svd_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.rots, stream=stream)
+        if kev is not None:
+            kev[1].record(stream)
+
+    units = property(lambda self: self.nb)
+
+    def roofline(self, kernel_ms):
+        info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
+        fl = jacobi_flops(32, 32, info_h, rots_h)
+        achieved = fl / (kernel_ms * 1e-3) / 1e12
+        return ({"kernel": f"jacobi_reg_kernel<double> (tier {int(self.tuned['tier']):#x})", "bound": "alu",
+                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": "FP64: GB300 data-sheet 1.25 TFLOP/s"},
+                {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
+                 "autotune": self.tuned})
+
+    def cpu_sample(self, n):
+        import gen
+        import oracle
+        b = gen.workload0(batch=n)
+        mats = [b.a64(i) for i in range(n)]
+        cores = oracle.default_threads()
+        t0 = time.time()
+        oracle.svd_batch(mats, nthreads=cores)
+        oracle.qr_batch(mats, nthreads=cores)
+        dt = time.time() - t0
+        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+                "sample": f"{n} SVDs + QRs of 32x32 FP64 (same generator), {dt:.2f} s wall"}
+
+
+class Block512:
+    """500 x (512 x 512) FP32 block-Jacobi SVD (GRAM, block width 32)."""
+    name = "block512"
+    metric = "batched SVDs/s (512x512 FP32 block-Jacobi SVD)"
+    unit = "SVDs/s"
+    dtype = "f32"
+    launches_per_step = 0   # set after the first step (kernels launched inside the call)
+
+    def __init__(self, args):
+        self.args = args
+        self.nb = 500
+
+    def config(self, world):
+        return {"workload": "block512: block-Jacobi SVD (U,S,V) of 500 FP32 512x512 per GPU per step, GRAM "
+                            "method, block width 32; sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
+                "l2": "inputs (524 MB per GPU) larger than L2", "parallelism": f"independent batches per GPU x{world}"}
+
+    def setup(self, rank, dev):
+        import torch
+        import gen
+        import paper_1707_05141_gb300 as bs
+        self.bs = bs
+        b = gen.workload2(batch=self.nb, first=rank * self.nb)
+        self.h_in = [torch.from_numpy(b.a).pin_memory()]
+        self.d = self.h_in[0].to(dev)
+        self.d_in = [self.d]
+        k = 512
+        self.A = bs.Batch.uniform(self.d, 512, 512)
+        self.S = torch.empty((self.nb, 1, k), device=dev)
+        self.U = torch.empty((self.nb, k, 512), device=dev)
+        self.V = torch.empty((self.nb, k, 512), device=dev)
+        self.Sb, self.Ub, self.Vb = (bs.Batch.uniform(self.S, k, 1), bs.Batch.uniform(self.U, 512, k),
+                                     bs.Batch.uniform(self.V, 512, k))
+        self.info = torch.empty(self.nb, dtype=torch.int32, device=dev)
+        self.rots = torch.empty(self.nb, dtype=torch.int64, device=dev)
+        self.ws = torch.empty(bs.batched_svd_block_jacobi_workspace(self.A, 32, 0), dtype=torch.uint8, device=dev)
+        self.outs = [self.S, self.U, self.V]
+        self.sigma = b.sigma
+
+    def step(self, stream, kev=None):
+        if kev is not None:
+            kev[0].record(stream)
+        self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
+                                         max_sweeps=20, block_width=32, method=0, stream=stream)
+        if kev is not None:
+            kev[1].record(stream)
+
+    units = property(lambda self: self.nb)
+
+    def roofline(self, kernel_ms):
+        info_h = self.info.cpu().numpy()
+        sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
+        # per pair: Gram 2 m (2bw)^2, update 2 (m + n) (2bw)^2 flops; 120 pairs per sweep
+        pair_fl = 2 * 512 * 64 * 64 + 2 * 1024 * 64 * 64
+        fl = float(np.sum(sweeps) * 120 * pair_fl)
+        achieved = fl / (kernel_ms * 1e-3) / 1e12
+        err = float(np.abs(self.S.cpu().numpy()[:, 0, :] - self.sigma).max())
+        self.launches_per_step = int(np.max(sweeps)) * 15 * 4 + 2
+        return ({"kernel": "batched_svd_block_jacobi (all stages of one call)", "bound": "alu",
+                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": "FP32 SIMT; achieved counts Gram + update flops of the pairs of every sweep run"},
+                {"sweeps_mean": float(np.mean(sweeps)), "sweeps_max": int(np.max(sweeps)),
+                 "max_sigma_err_vs_generator": err})
+
+    def cpu_sample(self, n):
+        import gen
+        import oracle
+        n = max(1, min(n, 16))
+        b = gen.workload2(batch=n)
+        mats = [b.a64(i) for i in range(n)]
+        cores = oracle.default_threads()
+        t0 = time.time()
+        oracle.svd_batch(mats, nthreads=cores)
+        dt = time.time() - t0
+        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+                "sample": f"{n} SVDs of 512x512 FP64 (same generator), {dt:.2f} s wall"}
+
+
+class RsvdBase:
+    unit = "SVDs/s"
+    dtype = "f32"
+
+    def _alloc(self, rb, dev, hint_host):
+        import torch
+        bs = self.bs
+        self.rb = rb
+        m, n = rb.m, rb.n
+        k = np.minimum(m, n)
+        self.h_in = [torch.from_numpy(rb.flat).pin_memory()]
+        self.flat = self.h_in[0].to(dev)
+        self.d_in = [self.flat]
+        su, sv, ss = (m.astype(np.int64) * k + 3) // 4 * 4, (n.astype(np.int64) * k + 3) // 4 * 4, (k + 3) // 4 * 4
+        off = lambda x: np.concatenate([[0], np.cumsum(x)[:-1]])
+        self.fu = torch.zeros(int(su.sum()), device=dev)
+        self.fv = torch.zeros(int(sv.sum()), device=dev)
+        self.fs = torch.zeros(int(ss.sum()), device=dev)
+        self.A = bs.Batch.packed(self.flat, rb.offset, m, n)
+        self.U = bs.Batch.packed(self.fu, off(su), m, k)
+        self.V = bs.Batch.packed(self.fv, off(sv), n, k)
+        self.S = bs.Batch.packed(self.fs, off(ss), k, np.ones_like(k))
+        self.kmax = torch.as_tensor(k.astype(np.int32)).to(dev)
+        self.rank = torch.zeros(rb.batch, dtype=torch.int32, device=dev)
+        self.info = torch.zeros(rb.batch, dtype=torch.int32, device=dev)
+        self.err = torch.zeros(rb.batch, dtype=torch.float32, device=dev)
+        self.samples = torch.zeros(rb.batch, dtype=torch.int32, device=dev)
+        self.ws = torch.empty(bs.batched_rsvd_workspace(self.A, m, n), dtype=torch.uint8, device=dev)
+        self.hint = None if hint_host is None else torch.as_tensor(np.asarray(hint_host, np.int32)).to(dev)
+        self.outs = [self.fu, self.fv, self.fs]
+        self.graph = None
+
+    def _rsvd(self, stream, hint, rounds):
+        self.bs.batched_rsvd(self.A, self.U, self.S, self.V, self.kmax, self.rank, self.info, self.ws, hint,
+                             tol=1e-5, oversample=8, max_rounds=rounds, seed=1707, err_est=self.err,
+                             samples=self.samples, stream=stream)
+
+    def capture(self, stream):
+        import torch
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):          # captured on torch's side stream
+            self.inner(torch.cuda.current_stream())
+
+    def step(self, stream, kev=None):
+        if kev is not None:
+            kev[0].record(stream)
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.inner(stream)
+        if kev is not None:
+            kev[1].record(stream)
+
+    units = property(lambda self: self.rb.batch)
+
+    def error_sample(self, nsamp=64):
+        """Relative truncation error ||A - U_k S_k V_k^T||_F / ||A||_F on sampled blocks (FP64, host)."""
+        rb = self.rb
+        U, V, S = (t.cpu().numpy().astype(np.float64) for t in (self.fu, self.fv, self.fs))
+        rk = self.rank.cpu().numpy()
+        ou, ov, os_ = (np.asarray(x.ptrs.cpu().numpy() - x.ptrs[0].item(), np.int64) // 4 for x in (self.U, self.V, self.S))
+        worst = 0.0
+        for b in range(0, rb.batch, max(1, rb.batch // nsamp)):
+            a = rb.a64(b)
+            m, n, k = a.shape[0], a.shape[1], int(rk[b])
+            u = U[ou[b]:ou[b] + m * k].reshape(k, m).T
+            v = V[ov[b]:ov[b] + n * k].reshape(k, n).T
+            s = S[os_[b]:os_[b] + k]
+            worst = max(worst, float(np.linalg.norm(a - (u * s) @ v.T) / np.linalg.norm(a)))
+        return worst
+
+    def roofline(self, kernel_ms):
+        info = self.info.cpu().numpy()
+        rounds = info & 0xff
+        samp = self.samples.cpu().numpy()
+        rb = self.rb
+        # algorithmic bytes: every sampling round reads A four times (sample, power step x2,
+        # projection), a full SVD reads it once; outputs U, S, V of the rank k
+        abytes = float(np.sum((rb.m.astype(np.float64) * rb.n) * 4 * (4 * rounds + (samp == np.minimum(rb.m, rb.n)))))
+        rk = self.rank.cpu().numpy().astype(np.float64)
+        abytes += float(np.sum((rb.m + rb.n + 1) * rk * 4))
+        achieved = abytes / (kernel_ms * 1e-3) / 1e9
+        peak = measured_hbm_gbs()
+        k = np.minimum(rb.m, rb.n)
+        return ({"kernel": self.kernel_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": achieved / peak, "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json); achieved = algorithmic bytes of "
+                              "the whole call / its time"},
+                {"rounds_mean": float(rounds.mean()), "fallback_frac": float(np.mean((info >> 22) & 1)),
+                 "full_rank_frac": float(np.mean(samp == k)), "samples_mean": float(samp.mean()),
+                 "rank_mean": float(rk.mean()), "max_rel_error_sampled": self.error_sample()})
+
+    def cpu_sample_blocks(self, rb, n, hint):
+        import oracle
+        cores = oracle.default_threads()
+        idx = list(range(0, rb.batch, max(1, rb.batch // n)))[:n]
+        from concurrent.futures import ThreadPoolExecutor
+
+        def one(b):
+            a = rb.a64(b)
+            k = min(a.shape)
+            l = int(hint[b]) + 8 if hint is not None else 8
+            if l >= k or l > 128:
+                oracle.svd(a)
+            else:
+                oracle.rsvd(a, 1707, b, l, 1)
+
+        t0 = time.time()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            list(ex.map(one, idx))
+        dt = time.time() - t0
+        return len(idx), dt, cores
+
+
+class RsvdUneven(RsvdBase):
+    name = "rsvd_uneven"
+    metric = "batched randomized SVDs/s at 1e-5 relative Frobenius error (uneven 64..256 blocks)"
+    kernel_name = "batched_rsvd (whole call, CUDA graph)"
+
+    def __init__(self, args):
+        self.args = args
+        self.nb = 16384
+
+    def config(self, world):
+        return {"workload": "rsvd_uneven: randomized SVD to 1e-5 of 16384 FP32 blocks per GPU, m, n uniform on "
+                            "{64, 128, 256}, sigma_i = exp(-i/r0), r0 ~ U[2, 12]; p = 8, one power step, rank hint "
+                            "= the rank where sigma falls to 1e-5; one CUDA graph per step",
+                "batch_per_gpu": self.nb, "l2": "inputs (1.46 GB per GPU) larger than L2",
+                "parallelism": f"independent batches per GPU x{world}"}
+
+    def setup(self, rank, dev):
+        import gen
+        import paper_1707_05141_gb300 as bs
+        self.bs = bs
+        rb = gen.workload3(batch=self.nb, first=rank * self.nb)
+        self._alloc(rb, dev, rb.extra["rank_hint"])
+
+    def inner(self, stream):
+        self._rsvd(stream, self.hint, 4)
+
+    launches_per_step = 4 * 15 + 6
+
+    def cpu_sample(self, n):
+        import gen
+        rb = gen.workload3(batch=max(n, 1))
+        cnt, dt, cores = self.cpu_sample_blocks(rb, n, rb.extra["rank_hint"])
+        return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+                "sample": f"{cnt} blocks of the same generator, fixed-width FP64 RSVD (hint + 8 columns, one "
+                          f"power step) or full Jacobi SVD, {dt:.2f} s wall"}
+
+
+class HmatrixMlp(RsvdBase):
+    name = "hmatrix_mlp"
+    metric = "batched randomized SVDs/s at 1e-5 with learned rank hints (kernel blocks)"
+    kernel_name = "sketch features + MLP + batched_rsvd (whole step, CUDA graph)"
+
+    def __init__(self, args):
+        self.args = args
+
+    def config(self, world):
+        return {"workload": "hmatrix_mlp: admissible blocks (64..256) of exp(-|x-y|/0.1) over 32768 uniform 3D points "
+                            "(k-d tree, median split, leaf 64, eta 1.1); randomized SVD to 1e-5 with ranks from the "
+                            "rank predictor (trained on another point set's plain-adaptive ranks); plain adaptive "
+                            "timed alongside", "blocks_per_gpu": getattr(self, "nblocks", None),
+                "l2": "inputs (2.25 GB per GPU) larger than L2", "parallelism": f"independent point sets x{world}"}
+
+    def setup(self, rank, dev):
+        import torch
+        import gen
+        import paper_1707_05141_gb300 as bs
+        from paper_1707_05141_gb300 import rank_mlp
+        self.bs = bs
+        self.rank_mlp = rank_mlp
+        tr = gen.workload4(n_points=16384, seed_index=100 + rank)
+        ft = torch.from_numpy(tr.flat).to(dev)
+        ranks, _ = rank_mlp.plain_adaptive_ranks(ft, tr.offset, tr.m, tr.n, seed=5)
+        feats = rank_mlp.features(ft, tr.offset, tr.m, tr.n, seed=6)
+        t0 = time.time()
+        self.params, hist = rank_mlp.train(feats, ranks, steps=2000, log_every=500)
+        self.train_info = {"train_blocks": tr.batch, "final_loss": hist[-1][1], "train_s": time.time() - t0}
+        del ft, feats
+        rb = gen.workload4(n_points=32768, seed_index=rank)
+        self.nblocks = rb.batch
+        self._alloc(rb, dev, None)
+        self.feats = torch.empty((rb.batch, 16), device=dev)
+        self.pred = torch.empty(rb.batch, device=dev)
+        self.hint_d = torch.empty(rb.batch, dtype=torch.int32, device=dev)
+        self.md = torch.as_tensor(rb.m).to(dev)
+        self.nd = torch.as_tensor(rb.n).to(dev)
+
+    def inner(self, stream):
+        bs = self.bs
+        bs.bsvd_sketch_features(self.A, self.feats, 6, stream)
+        bs.bsvd_mlp_forward(self.feats, self.params, self.pred, self.hint_d, 2.0, self.md, self.nd, stream)
+        self._rsvd(stream, self.hint_d, 16)
+
+    launches_per_step = 2 + 15 + 6
+
+    def plain_ms(self, stream):
+        """The plain adaptive method (no hints) on the same blocks: time, rounds, worst error."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self._rsvd(torch.cuda.current_stream(), None, 16)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = self.info.cpu().numpy()
+        out = {"plain_ms": e0.elapsed_time(e1) / 3, "plain_rounds_mean": float((info & 0xff).mean()),
+               "plain_max_rel_error_sampled": self.error_sample(), "plain_rank_mean": float(self.rank.float().mean())}
+        return out
+
+    def cpu_sample(self, n):
+        import gen
+        rb = gen.workload4(n_points=8192, seed_index=0)
+        cnt, dt, cores = self.cpu_sample_blocks(rb, n, None)
+        return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+                "sample": f"{cnt} kernel blocks (8192-point set), FP64 RSVD with 8 columns + power step, "
+                          f"{dt:.2f} s wall"}
+
+
+WORKLOADS = {c.name: c for c in (SvdQr64, Fp64_32, Block512, RsvdUneven, HmatrixMlp)}
+
+
+# ----------------------------------------------------------------------------------------------
+# harness
+# ----------------------------------------------------------------------------------------------
+
+def run_ours(W, args, rank, world, local_rank):
     import torch
     import paper_1707_05141_gb300 as bs
 
     bs.lib()  # fail loudly when the library is missing
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    nb_svd, nb_qr = args.svd_batch, args.qr_batch
-    a_svd, a_qr = make_inputs(rank, nb_svd, nb_qr)
-    h_svd = torch.from_numpy(a_svd.a).pin_memory()
-    h_qr = torch.from_numpy(a_qr.a).pin_memory()
-    d_svd = h_svd.to(dev)
-    d_qr = h_qr.to(dev)
-    m, n = 64, 64
-    mq, nq = 128, 32
-    k = 64
-    A = bs.Batch.uniform(d_svd, m, n)
-    S = torch.empty((nb_svd, 1, k), device=dev)
-    U = torch.empty((nb_svd, k, m), device=dev)
-    V = torch.empty((nb_svd, k, n), device=dev)
-    Sb, Ub, Vb = bs.Batch.uniform(S, k, 1), bs.Batch.uniform(U, m, k), bs.Batch.uniform(V, n, k)
-    info = torch.empty(nb_svd, dtype=torch.int32, device=dev)
-    rots = torch.empty(nb_svd, dtype=torch.int64, device=dev)
-    AQ = bs.Batch.uniform(d_qr, mq, nq)
-    Q = torch.empty((nb_qr, nq, mq), device=dev)
-    R = torch.empty((nb_qr, nq, nq), device=dev)
-    Qb, Rb = bs.Batch.uniform(Q, mq, nq), bs.Batch.uniform(R, nq, nq)
-    qinfo = torch.empty(nb_qr, dtype=torch.int32, device=dev)
+    W.setup(rank, dev)
     stream = torch.cuda.current_stream()
-    from paper_1707_05141_gb300 import autotune
-    tuned = autotune.tune_jacobi(d_svd, m, n)   # picks tier/variant for this size bin (not timed)
-
-    ev = []
-
-    def step(record=False):
-        bs.batched_qr(AQ, Qb, Rb, qinfo, stream)
-        if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        bs.batched_svd_jacobi(A, Sb, Ub, Vb, info, rots, stream=stream)
-        if record:
-            e1.record(stream)
-            ev.append((e0, e1))
-
     for _ in range(args.warmup):
-        step()
+        W.step(stream)
     torch.cuda.synchronize()
+    if hasattr(W, "capture"):
+        W.capture(stream)
+        W.step(stream)
+        torch.cuda.synchronize()
+    kev = []
     clocks = Clocks(local_rank)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.time()
-    t_start.record(stream)
+    t0e.record(stream)
     for _ in range(args.steps):
-        step(record=True)
-    t_end.record(stream)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        W.step(stream, ev)
+        kev.append(ev)
+    t1e.record(stream)
     torch.cuda.synchronize()
     wall1 = time.time()
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop(wall0, wall1)
-    ms_total = t_start.elapsed_time(t_end)
-    jac_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
+    ms_step = max_over_ranks(t0e.elapsed_time(t1e) / args.steps, world, dev)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    roof, detail = W.roofline(kernel_ms)
+    extra = W.plain_ms(stream) if hasattr(W, "plain_ms") else {}
+    if hasattr(W, "train_info"):
+        extra["training"] = W.train_info
 
-    info_h = info.cpu().numpy()
-    rots_h = rots.cpu().numpy()
-    assert np.all(info_h > 0), "Jacobi reported a bad shape"
-    fl = jacobi_flops(m, n, info_h, rots_h)
-    achieved = fl / (jac_ms * 1e-3) / 1e12
-    tier = int(tuned["tier"])
-    kname = ("jacobi_reg_kernel" if (tier & 0xff) == bs.TIER_REGISTER else "jacobi_smem_kernel") + f" (tier {tier:#x})"
-    dig = kernel_digest("jacobi_reg.cu" if (tier & 0xff) == bs.TIER_REGISTER else "jacobi_smem.cu")
-    traffic = TRAFFIC.get(dig)
-
-    # ---- end to end through the public API: pinned host in, host out ----
-    o_s = torch.empty((nb_svd, 1, k)).pin_memory()
-    o_u = torch.empty((nb_svd, k, m)).pin_memory()
-    o_v = torch.empty((nb_svd, k, n)).pin_memory()
-    o_q = torch.empty((nb_qr, nq, mq)).pin_memory()
-    o_r = torch.empty((nb_qr, nq, nq)).pin_memory()
-    e2e_steps = max(1, min(args.steps, 10))
+    # end to end through the public API: pinned host inputs copied in, every output copied out
+    houts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in W.outs]
+    e2e_steps = max(1, min(args.steps, 5))
 
     def e2e_step():
-        d_svd.copy_(h_svd, non_blocking=True)
-        d_qr.copy_(h_qr, non_blocking=True)
-        step()
-        o_s.copy_(S, non_blocking=True)
-        o_u.copy_(U, non_blocking=True)
-        o_v.copy_(V, non_blocking=True)
-        o_q.copy_(Q, non_blocking=True)
-        o_r.copy_(R, non_blocking=True)
+        for d, h in zip(W.d_in, W.h_in):
+            d.copy_(h, non_blocking=True)
+        W.step(stream)
+        for h, o in zip(houts, W.outs):
+            h.copy_(o, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    x0 = torch.cuda.Event(enable_timing=True)
-    x1 = torch.cuda.Event(enable_timing=True)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x0.record(stream)
     for _ in range(e2e_steps):
         e2e_step()
     x1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = x0.elapsed_time(x1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    h2d = h_svd.numel() * 4 + h_qr.numel() * 4
-    d2h = sum(t.numel() * 4 for t in (o_s, o_u, o_v, o_q, o_r))
-
-    return {
-        "ms_step": ms_step,
-        "value": world * nb_svd / (ms_step * 1e-3),
-        "e2e": {"value": world * nb_svd / (e2e_ms * 1e-3), "unit": "SVDs/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": traffic, "ms_per_launch": jac_ms,
-                     "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (max SM clock)"},
-        "clocks": ck,
-        "gpu_launches": 2 * args.steps,
-        "detail": {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
-                   "jacobi_gflop_per_launch": fl / 1e9, "autotune": tuned},
-    }
-
-
-def cpu_baseline(args, n_svd, n_qr):
-    """The FP64 oracle (as it stands) on a bounded sample of the same workload, all host cores."""
-    import oracle
-    a_svd, a_qr = make_inputs(0, n_svd, n_qr)
-    mats = [a_svd.a64(i) for i in range(n_svd)]
-    qmats = [a_qr.a64(i) for i in range(n_qr)]
-    cores = oracle.default_threads()
-    t0 = time.time()
-    oracle.svd_batch(mats, tol=-1.0, nthreads=cores)
-    oracle.qr_batch(qmats, nthreads=cores)
-    dt = time.time() - t0
-    # one step's unit of work is (1 SVD of 64x64 + 1 QR of 128x32) per SVD counted
-    return {"value": n_svd / dt, "unit": "SVDs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_svd} SVDs of 64x64 + {n_qr} QRs of 128x32 (same generator), FP64, {dt:.2f} s wall"}
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / e2e_steps, world, dev)
+    h2d = sum(h.numel() * h.element_size() for h in W.h_in)
+    d2h = sum(h.numel() * h.element_size() for h in houts)
+    detail.update(extra)
+    return {"ms_step": ms_step, "value": world * W.units / (ms_step * 1e-3),
+            "e2e": {"value": world * W.units / (e2e_ms * 1e-3), "unit": W.unit, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "roofline": roof, "clocks": ck, "gpu_launches": W.launches_per_step * args.steps, "detail": detail}
 
 
 def main():
@@ -284,53 +698,48 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="svd64_qr128")
     ap.add_argument("--svd-batch", type=int, default=20000)
     ap.add_argument("--qr-batch", type=int, default=20000)
-    ap.add_argument("--cpu-sample", type=int, default=4000)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    W = WORKLOADS[args.workload](args)
+    default_sample = {"svd64_qr128": 4000, "fp64_32": 1000, "block512": 4, "rsvd_uneven": 256, "hmatrix_mlp": 512}
+    ns = args.cpu_sample or default_sample[W.name]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    config = {"workload": "svd64_qr128: Jacobi SVD (U,S,V) of 20000 FP32 64x64 + Householder QR (Q,R) of 20000 "
-                          "FP32 128x32 per GPU per step; sigma_i = exp(-i/8), Haar U, V",
-              "svd_batch_per_gpu": args.svd_batch, "qr_batch_per_gpu": args.qr_batch, "m": 64, "n": 64,
-              "qr_m": 128, "qr_n": 32, "l2": "inputs (656 MB per GPU) larger than L2; no flush",
-              "parallelism": f"independent batches per GPU x{world}"}
-    metric = "batched SVDs/s (64x64 FP32 Jacobi SVD + 128x32 FP32 QR per SVD)"
 
     if args.impl == "reference":
+        # the reference arm is the FP64 oracle on the host cores (the paper ships no code)
         if rank != 0:
             return
-        vals = []
-        n = max(1, args.cpu_sample // 4)
-        for _ in range(args.warmup if args.warmup < 1 else 1):
-            cpu_baseline(args, 64, 64)
-        for _ in range(args.steps if args.steps <= 5 else 5):
-            vals.append(cpu_baseline(args, n, n))
+        vals = [W.cpu_sample(max(1, ns // 4)) for _ in range(min(max(args.steps, 1), 3))]
         v = statistics.median(x["value"] for x in vals)
         cb = dict(vals[0])
         cb["value"] = v
-        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "SVDs/s", "n_gpus": 0,
-                          "steps": len(vals), "warmup": args.warmup, "ms_per_step": 1e3 * args.svd_batch / v,
+        print(json.dumps({"impl": "reference", "metric": W.metric, "value": v, "unit": W.unit, "n_gpus": 0,
+                          "steps": len(vals), "warmup": 0,
+                          "ms_per_step": 1e3 * getattr(W, "nb", 0) / v if getattr(W, "nb", 0) else None,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": config, "cpu_baseline": cb,
-                          "e2e": {"value": v, "unit": "SVDs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+                          "data": "synthetic", "config": W.config(1), "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": W.unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
+    res = run_ours(W, args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(args, args.cpu_sample, args.cpu_sample)
+        cb = W.cpu_sample(ns)
     if rank == 0:
-        line = {"metric": metric, "value": res["value"], "unit": "SVDs/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": W.metric, "value": res["value"], "unit": W.unit, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                "vs_baseline": None, "dtype": W.dtype, "data": "synthetic", "config": W.config(world),
                 "roofline": res["roofline"], "cpu_baseline": cb, "e2e": res["e2e"], "clocks": res["clocks"],
                 "gpu_launches": res["gpu_launches"], "detail": res["detail"]}
         print(json.dumps(line))
