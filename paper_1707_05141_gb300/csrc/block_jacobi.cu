@@ -21,17 +21,12 @@
 // the columns of U and V are sorted by descending sigma in place (cycle-following permutation).
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "common.cuh"
+#include "launch.cuh"
 
 namespace bsvd {
-
-template <typename T>
-int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
-              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st);
-template <typename T>
-int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
-                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
-                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------------------
 // workspace layout (all offsets 256-byte aligned)
@@ -43,8 +38,19 @@ struct BjLayout {
     size_t off_pG, off_pX, off_pS, off_pUR, off_pP;      // pointer arrays (item order)
     size_t off_m, off_n, off_ld, off_ldp, off_info;      // int arrays per item
     size_t off_state;                                    // per-matrix state
+    size_t off_mlist, off_plist;                         // live matrices, rotating pair items
+    size_t off_ctr;                                      // BjCounters
     size_t total;
 };
+
+// claim counters of the persistent stage kernels and the lengths of the two live lists
+struct BjCounters {
+    unsigned long long claim[8];  // gram, pack, polish, update, QR, inner SVD
+    int pcount;                   // rotating pairs of the current step (plist)
+    int mcount;                   // matrices not yet converged (mlist)
+    int pad[2];
+};
+constexpr size_t kStepCounterBytes = offsetof(BjCounters, mcount);  // claims + pcount: zeroed every step
 
 struct BjState {
     int mm, nn, nblk, converged;
@@ -92,6 +98,9 @@ static BjLayout bj_layout(int batch, int max_m, int max_n, int bw, bool direct)
     L.off_ldp = take(L.n_items * sizeof(int));
     L.off_info = take(L.n_items * sizeof(int));
     L.off_state = take((size_t)batch * sizeof(BjState));
+    L.off_mlist = take((size_t)batch * sizeof(int));
+    L.off_plist = take(L.n_items * sizeof(int));
+    L.off_ctr = take(sizeof(BjCounters));
     L.total = o;
     return L;
 }
@@ -127,6 +136,10 @@ __global__ void bj_setup_kernel(int batch, int max_mm, int max_nn, int bw, int n
         st->rotations = 0;
         st->emax = 0.0;
         info[b] = bad ? BSVD_INFO_BAD_SHAPE : 0;
+        if (!st->converged) {
+            BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+            reinterpret_cast<int*>(ws + L.off_mlist)[atomicAdd(&C->mcount, 1)] = b;
+        }
     }
     // per-item pointers into the workspace
     for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
@@ -171,16 +184,15 @@ __device__ __forceinline__ int bj_col(int bi, int bj, int bw, int c, int nn)
 // GRAM stage: G = A_ij^T A_ij with FP32 dot products; FP64 scaled off-diagonal test
 // ------------------------------------------------------------------------------------------------
 template <typename T, int K2>  // K2 = 2 bw
-__global__ void __launch_bounds__(256) bj_gram_kernel(int batch, int npairs, int step, int bw, T* const* U,
-                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
-                                                      const int* N, unsigned char* ws, BjLayout L, double tol)
+__device__ __forceinline__ void bj_gram_item(int it, int batch, int npairs, int step, int bw, T* const* U,
+                                             const int* LDU, T* const* V, const int* LDV, const int* M,
+                                             const int* N, unsigned char* ws, const BjLayout& L, double tol)
 {
     constexpr int RC = 32;                 // rows per staged chunk
     constexpr int TPO = (K2 * K2) / 256;   // outputs per thread
     __shared__ T xs[K2][RC + 1];
     __shared__ T gd[K2];
     __shared__ double red[8];
-    const int it = blockIdx.x;
     const int b = it / npairs, k = it - b * npairs;
     BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
     int* im = reinterpret_cast<int*>(ws + L.off_m);
@@ -247,9 +259,28 @@ __global__ void __launch_bounds__(256) bj_gram_kernel(int batch, int npairs, int
         const bool rot = em > tol;
         im[it] = rot ? K2 : 0;
         in[it] = rot ? K2 : 0;
-        if (rot) atomicAdd(&st->rot_sweep, 1);
+        if (rot) {
+            atomicAdd(&st->rot_sweep, 1);
+            BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+            reinterpret_cast<int*>(ws + L.off_plist)[atomicAdd(&C->pcount, 1)] = it;
+        }
         // emax of the matrix over the sweep, as ordered bits of a non-negative double
         atomicMax(reinterpret_cast<unsigned long long*>(&st->emax), (unsigned long long)__double_as_longlong(em));
+    }
+}
+
+// persistent over the pairs of the live matrices (mlist); appends the rotating pairs to plist
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_gram_kernel(int batch, int npairs, int step, int bw, T* const* U,
+                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                      const int* N, unsigned char* ws, BjLayout L, double tol)
+{
+    BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    const int* mlist = reinterpret_cast<const int*>(ws + L.off_mlist);
+    const long long items = (long long)C->mcount * npairs;
+    for (long long j = next_work(&C->claim[0]); j < items; j = next_work(&C->claim[0])) {
+        const int b = mlist[j / npairs], k = (int)(j % npairs);
+        bj_gram_item<T, K2>(b * npairs + k, batch, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L, tol);
     }
 }
 
@@ -259,11 +290,10 @@ __global__ void __launch_bounds__(256) bj_gram_kernel(int batch, int npairs, int
 // themselves and the FP64 scaled off-diagonal, the same test for both methods.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int K2>
-__global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int step, int bw, T* const* U,
-                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
-                                                      const int* N, unsigned char* ws, BjLayout L, double tol)
+__device__ __forceinline__ void bj_pack_item(int it, int batch, int npairs, int step, int bw, T* const* U,
+                                             const int* LDU, T* const* V, const int* LDV, const int* M,
+                                             const int* N, unsigned char* ws, const BjLayout& L)
 {
-    const int it = blockIdx.x;
     const int b = it / npairs, k = it - b * npairs;
     BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
     int* im = reinterpret_cast<int*>(ws + L.off_m);
@@ -292,6 +322,18 @@ __global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int
     }
 }
 
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int step, int bw, T* const* U,
+                                                      const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                      const int* N, unsigned char* ws, BjLayout L)
+{
+    BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
+    const long long items = C->pcount;
+    for (long long j = next_work(&C->claim[1]); j < items; j = next_work(&C->claim[1]))
+        bj_pack_item<T, K2>(plist[j], batch, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L);
+}
+
 // ------------------------------------------------------------------------------------------------
 // polish: one Newton-Schulz step X <- X - X (X^T X - I) / 2 towards the orthogonal polar factor.
 // X (the inner SVD's accumulated rotation, a product of hundreds of plane rotations) is orthogonal
@@ -299,13 +341,11 @@ __global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int
 // step ||X^T X - I|| is at the rounding level of one product.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int K2>
-__global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLayout L)
+__device__ __forceinline__ void bj_polish_item(int it, unsigned char* ws, const BjLayout& L, unsigned char* pol_sm)
 {
     constexpr int TPO = (K2 * K2) / 256;
-    extern __shared__ __align__(16) unsigned char pol_sm[];
     T(*xs)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm);                                  // X(r, c) at [c][r]
     T(*es)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm + sizeof(T) * K2 * (K2 + 1));      // X^T X - I
-    const int it = blockIdx.x;
     const int* in = reinterpret_cast<const int*>(ws + L.off_n);
     if (in[it] == 0) return;
     T* X = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
@@ -336,6 +376,17 @@ __global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLay
     for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = xs[oc][or0 + q] - T(0.5) * acc[q];
 }
 
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLayout L)
+{
+    extern __shared__ __align__(16) unsigned char pol_sm[];
+    BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
+    const long long items = C->pcount;
+    for (long long j = next_work(&C->claim[2]); j < items; j = next_work(&C->claim[2]))
+        bj_polish_item<T, K2>(plist[j], ws, L, pol_sm);
+}
+
 // ------------------------------------------------------------------------------------------------
 // update stage: dst rows <- src rows (r x 2bw) * X (2bw x 2bw) [* diag(S)]
 //   GRAM  : src = dst = [W_i W_j] (in place, row tiles), X = accumulated rotation of G
@@ -347,15 +398,14 @@ template <typename T>
 constexpr int bj_rows_per_tile() { return sizeof(T) == 4 ? 32 : 16; }
 
 template <typename T, int K2>
-__global__ void __launch_bounds__(256) bj_update_kernel(int npairs, int step, int bw, int direct, T* const* U,
-                                                        const int* LDU, T* const* V, const int* LDV, const int* M,
-                                                        const int* N, unsigned char* ws, BjLayout L)
+__device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int step, int bw, int direct, T* const* U,
+                                               const int* LDU, T* const* V, const int* LDV, const int* M,
+                                               const int* N, unsigned char* ws, const BjLayout& L)
 {
     constexpr int RT = bj_rows_per_tile<T>();
     constexpr int TPO = (RT * K2) / 256;    // outputs per thread
     __shared__ T xm[K2][K2 + 1];            // multiplier X (column-scaled for DIRECT)
     __shared__ T ts[K2][RT + 1];            // source tile, column-major
-    const int it = blockIdx.x;
     const int b = it / npairs, k = it - b * npairs;
     const int* in = reinterpret_cast<const int*>(ws + L.off_n);
     if (in[it] == 0) return;
@@ -365,7 +415,6 @@ __global__ void __launch_bounds__(256) bj_update_kernel(int npairs, int step, in
     int bi, bj;
     round_robin_pair(nbp, step, k, bi, bj);
     const int tilesW = (mm + RT - 1) / RT, tilesV = (nn + RT - 1) / RT;
-    const int tile = blockIdx.y;
     if (tile >= tilesW + tilesV) return;
     const bool onV = tile >= tilesW;
     const int r0 = (onV ? tile - tilesW : tile) * RT;
@@ -418,6 +467,21 @@ __global__ void __launch_bounds__(256) bj_update_kernel(int npairs, int step, in
     }
 }
 
+// work items are (rotating pair, row tile) flattened; `tiles` is the bound on tiles per pair
+template <typename T, int K2>
+__global__ void __launch_bounds__(256) bj_update_kernel(int tiles, int npairs, int step, int bw, int direct,
+                                                        T* const* U, const int* LDU, T* const* V, const int* LDV,
+                                                        const int* M, const int* N, unsigned char* ws, BjLayout L)
+{
+    BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
+    const long long total = (long long)C->pcount * tiles;
+    for (long long w = next_work(&C->claim[3]); w < total; w = next_work(&C->claim[3])) {
+        const long long j = w / tiles;
+        bj_update_item<T, K2>(plist[j], (int)(w - j * tiles), npairs, step, bw, direct, U, LDU, V, LDV, M, N, ws, L);
+    }
+}
+
 // end of a sweep: a matrix whose sweep rotated nothing is converged
 __global__ void bj_sweep_end_kernel(int batch, int max_sweeps, int sweep, unsigned char* ws, BjLayout L, int* info)
 {
@@ -435,6 +499,10 @@ __global__ void bj_sweep_end_kernel(int batch, int max_sweeps, int sweep, unsign
     }
     st->rot_sweep = 0;
     st->emax = 0.0;
+    if (!st->converged) {  // still live: on the next sweep's list
+        BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+        reinterpret_cast<int*>(ws + L.off_mlist)[atomicAdd(&C->mcount, 1)] = b;
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -544,6 +612,8 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     // default pair threshold sqrt(m) u; DIRECT rotations are only as orthogonal as the pair's
     // Householder Q (~ 2bw u), so its default sits 8x higher
     const double tol_outer = tol > 0.0 ? tol : (direct ? 8.0 : 1.0) * sqrt((double)mm) * Unit<T>::value;
+    BjCounters* ctr = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    if (cudaMemsetAsync(ctr, 0, sizeof(BjCounters), st) != cudaSuccess) return BSVD_ERR_CUDA;
     bj_setup_kernel<T><<<batch, 256, 0, st>>>(batch, mm, nn, bw, npairs, (T* const*)A, M, N, LDA, (T* const*)U, LDU,
                                               (T* const*)V, LDV, ws, L, info);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
@@ -565,31 +635,39 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     if (polish_smem > 48 * 1024 && cudaFuncSetAttribute(bj_polish_kernel<T, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)polish_smem) != cudaSuccess)
         return BSVD_ERR_CUDA;
+    // persistent grids over the live lists: converged matrices and orthogonal pairs cost nothing
+    const ItemList pairs{reinterpret_cast<const int*>(ws + L.off_plist), &ctr->pcount, nullptr};
+    const int g_gram = persistent_grid(bj_gram_kernel<T, K2>, 256, 0, items);
+    const int g_pack = persistent_grid(bj_pack_kernel<T, K2>, 256, 0, items);
+    const int g_polish = persistent_grid(bj_polish_kernel<T, K2>, 256, polish_smem, items);
+    const int g_update = persistent_grid(bj_update_kernel<T, K2>, 256, 0, (long long)items * tiles);
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int step = 0; step < nbp - 1; ++step) {
+            if (cudaMemsetAsync(ctr, 0, kStepCounterBytes, st) != cudaSuccess) return BSVD_ERR_CUDA;
+            bj_gram_kernel<T, K2><<<g_gram, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
+                                                          LDV, M, N, ws, L, tol_outer);
             if (!direct) {
-                bj_gram_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
-                                                             LDV, M, N, ws, L, tol_outer);
                 const int rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, im, in, ild, pS, nullptr, nullptr,
-                                                    pX, ild, 0.0, 0, iinfo, nullptr, st);
+                                                    pX, ild, 0.0, 0, iinfo, nullptr, st,
+                                                    ItemList{pairs.idx, pairs.count, &ctr->claim[5]});
                 if (rc != BSVD_SUCCESS) return rc;
             } else {
-                bj_gram_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
-                                                             LDV, M, N, ws, L, tol_outer);
-                bj_pack_kernel<T, K2><<<items, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
-                                                             LDV, M, N, ws, L, tol_outer);
-                int rc = launch_qr<T>(items, L.mm_max, K2, pP, im, in, ildp, pP, ildp, pG, ild, iinfo, st);
+                bj_pack_kernel<T, K2><<<g_pack, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU,
+                                                              (T* const*)V, LDV, M, N, ws, L);
+                int rc = launch_qr<T>(items, L.mm_max, K2, pP, im, in, ildp, pP, ildp, pG, ild, iinfo, st,
+                                      ItemList{pairs.idx, pairs.count, &ctr->claim[4]});
                 if (rc != BSVD_SUCCESS) return rc;
                 // the inner sizes are K2 x K2 (R) for live items: reuse the n array for both
                 rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, in, in, ild, pS, pUR, ild, pX, ild, 0.0, 0,
-                                          iinfo, nullptr, st);
+                                          iinfo, nullptr, st, ItemList{pairs.idx, pairs.count, &ctr->claim[5]});
                 if (rc != BSVD_SUCCESS) return rc;
             }
-            bj_polish_kernel<T, K2><<<items, 256, polish_smem, st>>>(ws, L);
-            bj_update_kernel<T, K2><<<dim3(items, tiles), 256, 0, st>>>(npairs, step, bw, direct ? 1 : 0, (T* const*)U,
-                                                                        LDU, (T* const*)V, LDV, M, N, ws, L);
+            bj_polish_kernel<T, K2><<<g_polish, 256, polish_smem, st>>>(ws, L);
+            bj_update_kernel<T, K2><<<g_update, 256, 0, st>>>(tiles, npairs, step, bw, direct ? 1 : 0, (T* const*)U,
+                                                              LDU, (T* const*)V, LDV, M, N, ws, L);
             if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
         }
+        if (cudaMemsetAsync(&ctr->mcount, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
         bj_sweep_end_kernel<<<(batch + 127) / 128, 128, 0, st>>>(batch, sweeps, sw, ws, L, info);
     }
     const size_t fsm = (size_t)nn * (sizeof(T) + sizeof(int) + 1) + 48 + (size_t)(mm + nn) * sizeof(T) + 64;

@@ -119,6 +119,81 @@ __device__ __forceinline__ P jacobi_t(P alpha, P beta, P gamma)
     return d >= P(0) ? t : -t;
 }
 
+// Grid for a persistent launch: as many CTAs as can be resident at once (SM count x occupancy),
+// never more than the work items.
+template <typename K>
+inline int persistent_grid(K kernel, int threads, size_t smem, long long work)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+    if (sms < 1) sms = 1;
+    if (per < 1) per = 1;
+    const long long g = (long long)sms * per;
+    const long long n = work < g ? work : g;
+    return (int)(n > 0 ? n : 1);
+}
+
+// Dynamic work queue for persistent kernels: the CTA claims its next position with one atomic on
+// a counter zeroed (by a memset in stream order) before the launch.  Called by all threads; the
+// first barrier also separates the previous item's shared-memory use from the next one's.
+__device__ __forceinline__ long long next_work(unsigned long long* counter)
+{
+    __shared__ long long s_item;
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    return s_item;
+}
+
+// The items a batched kernel visits.  Without a list (idx == null) the grid has one CTA per item
+// and the hardware scheduler balances items of uneven cost.  With a list -- item indices in device
+// memory whose length is known only on the device, e.g. the matrices still active in a later
+// round of a captured CUDA graph -- the grid is persistent and its CTAs claim list positions from
+// `claim`, so an item left out of the list costs nothing.
+struct ItemList {
+    const int* idx;             // item indices (device), or null: every item of the batch
+    const int* count;           // number of entries of idx (device)
+    unsigned long long* claim;  // claim counter (device); the launcher zeroes it
+};
+
+inline ItemList all_items() { return ItemList{nullptr, nullptr, nullptr}; }
+
+__device__ __forceinline__ int list_item(const ItemList& wl)
+{
+    const long long i = next_work(wl.claim);
+    return i < (long long)*wl.count ? wl.idx[i] : -1;
+}
+
+// first item of this CTA, or -1; every thread of the CTA must call it
+__device__ __forceinline__ int item_first(const ItemList& wl, int batch)
+{
+    if (wl.idx == nullptr) return (int)blockIdx.x < batch ? (int)blockIdx.x : -1;
+    return list_item(wl);
+}
+
+// next item after b, or -1; every thread of the CTA must call it
+__device__ __forceinline__ int item_next(const ItemList& wl, int batch, int b)
+{
+    if (wl.idx == nullptr) {
+        __syncthreads();  // the shared memory of item b is reused by the next one
+        const long long nb = (long long)b + gridDim.x;
+        return nb < batch ? (int)nb : -1;
+    }
+    return list_item(wl);
+}
+
+// Grid of a launch over `batch` items (or over a list of at most `batch` entries, whose claim
+// counter is zeroed here in stream order); 0 on a CUDA error.
+template <typename K>
+inline int item_grid(K kernel, int threads, size_t smem, const ItemList& wl, int batch, cudaStream_t st)
+{
+    if (wl.idx == nullptr) return batch < 1 ? 1 : (batch < (1 << 30) ? batch : (1 << 30));
+    if (cudaMemsetAsync(wl.claim, 0, sizeof(unsigned long long), st) != cudaSuccess) return 0;
+    return persistent_grid(kernel, threads, smem, batch);
+}
+
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace bsvd

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "launch.cuh"
 
 namespace bsvd {
 
@@ -42,7 +43,7 @@ template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST>
 __global__ void __launch_bounds__(NS * PARTS, MINB)
     jacobi_reg_kernel(int batch, T* const* A, const int* M, const int* N, const int* LDA, T* const* Sout, T* const* U,
                       const int* LDU, T* const* V, const int* LDV, double tol_in, int max_sweeps, int* info,
-                      long long* rot_out)
+                      long long* rot_out, ItemList wl)
 {
     constexpr int NT = NS * PARTS;
     constexpr int PPW = 32 / NS;   // parts per warp (1 or 2)
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
     const int part = warp * PPW + lane / NS;  // row part
     const unsigned part_mask = PPW == 2 ? (lane < 16 ? 0x0000FFFFu : 0xFFFF0000u) : 0xFFFFFFFFu;
 
-    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+    for (int b = item_first(wl, batch); b >= 0; b = item_next(wl, batch, b)) {
         const int m = M[b], n = N[b], lda = LDA[b];
         const bool tr = m < n;
         const int mm = tr ? n : m;
@@ -344,11 +345,13 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
 template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST>
 static int launch_reg(int batch, void* const* A, const int* M, const int* N, const int* LDA, void* const* S,
                       void* const* U, const int* LDU, void* const* V, const int* LDV, double tol, int max_sweeps,
-                      int* info, long long* rot, cudaStream_t st)
+                      int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
-    const int grid = batch < (1 << 30) ? batch : (1 << 30);
+    const int grid = item_grid(jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST>, NS * PARTS, 0, wl, batch, st);
+    if (grid == 0) return BSVD_ERR_CUDA;
     jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST><<<grid, NS * PARTS, 0, st>>>(
-        batch, (T* const*)A, M, N, LDA, (T* const*)S, (T* const*)U, LDU, (T* const*)V, LDV, tol, max_sweeps, info, rot);
+        batch, (T* const*)A, M, N, LDA, (T* const*)S, (T* const*)U, LDU, (T* const*)V, LDV, tol, max_sweeps, info, rot,
+        wl);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
@@ -358,7 +361,7 @@ static int launch_reg(int batch, void* const* A, const int* M, const int* N, con
 template <typename T>
 int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
                       const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
-                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st)
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
     const int mm = max_m > max_n ? max_m : max_n;
     const int nn = max_m > max_n ? max_n : max_m;
@@ -368,7 +371,7 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
         ++seen;                                                                                             \
         if (variant == 0 || variant == seen)                                                                \
             return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_>(batch, A, M, N, LDA, S, U, LDU, V, LDV, tol,     \
-                                                               max_sweeps, info, rot, st);                  \
+                                                               max_sweeps, info, rot, st, wl);              \
     }
     if constexpr (sizeof(T) == 4) {
         BSVD_TRY(16, 2, 16, 16, 16, true)   // n <= 32, m <= 32: one warp per matrix
@@ -392,9 +395,9 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
 
 template int launch_jacobi_reg<float>(int, int, int, int, void* const*, const int*, const int*, const int*,
                                       void* const*, void* const*, const int*, void* const*, const int*, double, int,
-                                      int*, long long*, cudaStream_t);
+                                      int*, long long*, cudaStream_t, ItemList);
 template int launch_jacobi_reg<double>(int, int, int, int, void* const*, const int*, const int*, const int*,
                                        void* const*, void* const*, const int*, void* const*, const int*, double, int,
-                                       int*, long long*, cudaStream_t);
+                                       int*, long long*, cudaStream_t, ItemList);
 
 }  // namespace bsvd

@@ -14,13 +14,15 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "launch.cuh"
 
 namespace bsvd {
 
 template <typename T, typename P, int G, int MAXR>
 __global__ void __launch_bounds__(64 * G > 1024 ? 1024 : 64 * G) jacobi_smem_kernel(int batch, int max_mm, int max_np, T* const* A, const int* M, const int* N,
                                    const int* LDA, T* const* Sout, T* const* U, const int* LDU, T* const* V,
-                                   const int* LDV, double tol_in, int max_sweeps, int* info, long long* rot_out)
+                                   const int* LDV, double tol_in, int max_sweeps, int* info, long long* rot_out,
+                                   ItemList wl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ldw = max_mm | 1;  // odd leading dimensions spread columns over the banks
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(64 * G > 1024 ? 1024 : 64 * G) jacobi_smem_ker
     const int gl = tid % G;          // lane inside the pair group
     const int nthreads = blockDim.x;
 
-    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+    for (int b = item_first(wl, batch); b >= 0; b = item_next(wl, batch, b)) {
         const int m = M[b], n = N[b], lda = LDA[b];
         const bool tr = m < n;
         const int mm = tr ? n : m;   // working rows
@@ -206,16 +208,17 @@ static size_t jacobi_smem_bytes(int max_mm, int max_np)
 template <typename T, typename P, int G, int MAXR>
 static int launch_g(int batch, int max_mm, int max_np, void* const* A, const int* M, const int* N, const int* LDA,
                     void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
-                    int max_sweeps, int* info, long long* rot, cudaStream_t st)
+                    int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
     auto kern = jacobi_smem_kernel<T, P, G, MAXR>;
     const size_t smem = jacobi_smem_bytes<T>(max_mm, max_np);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return BSVD_ERR_CUDA;
     const int threads = (max_np / 2) * G < 32 ? 32 : (max_np / 2) * G;
-    const int grid = batch < (1 << 30) ? batch : (1 << 30);
+    const int grid = item_grid(kern, threads, smem, wl, batch, st);
+    if (grid == 0) return BSVD_ERR_CUDA;
     kern<<<grid, threads, smem, st>>>(batch, max_mm, max_np, (T* const*)A, M, N, LDA, (T* const*)S, (T* const*)U, LDU,
-                                      (T* const*)V, LDV, tol, max_sweeps, info, rot);
+                                      (T* const*)V, LDV, tol, max_sweeps, info, rot, wl);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
@@ -223,7 +226,7 @@ static int launch_g(int batch, int max_mm, int max_np, void* const* A, const int
 template <typename T>
 int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
-                       int max_sweeps, int* info, long long* rot, cudaStream_t st)
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
     const int max_mm = max_m > max_n ? max_m : max_n;
     const int max_nn = max_m > max_n ? max_n : max_m;
@@ -231,13 +234,14 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
     const int maxk_lim = sizeof(T) == 4 ? 128 : 64;
     if (max_mm > 256 || max_nn > maxk_lim) return BSVD_ERR_UNSUPPORTED;
     if (max_np == 0) return launch_g<T, T, 1, 16>(batch, max_mm, 2, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps,
-                                                 info, rot, st);
+                                                 info, rot, st, wl);
     if (jacobi_smem_bytes<T>(max_mm, max_np) > 220 * 1024) return BSVD_ERR_UNSUPPORTED;
     int g = 1;
     while (g * 16 < max_mm) g *= 2;
     if ((max_np / 2) * g > 1024) return BSVD_ERR_UNSUPPORTED;
 #define BSVD_LAUNCH_G(GG) \
-    return launch_g<T, T, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info, rot, st)
+    return launch_g<T, T, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info, rot, st, \
+                              wl)
     switch (g) {
         case 1: BSVD_LAUNCH_G(1);
         case 2: BSVD_LAUNCH_G(2);
@@ -250,9 +254,9 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
 
 template int launch_jacobi_smem<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
                                        void* const*, const int*, void* const*, const int*, double, int, int*,
-                                       long long*, cudaStream_t);
+                                       long long*, cudaStream_t, ItemList);
 template int launch_jacobi_smem<double>(int, int, int, void* const*, const int*, const int*, const int*,
                                         void* const*, void* const*, const int*, void* const*, const int*, double, int,
-                                        int*, long long*, cudaStream_t);
+                                        int*, long long*, cudaStream_t, ItemList);
 
 }  // namespace bsvd

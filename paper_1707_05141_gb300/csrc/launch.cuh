@@ -1,0 +1,39 @@
+// launch.cuh -- the library's internal launchers, shared by the C boundary (api.cu) and the
+// composed drivers (block_jacobi.cu, rsvd.cu).  Every launcher takes device pointer / size arrays
+// of one batch, enqueues on `st` and returns a BSVD_* status; `wl` restricts the launch to a device
+// list of items (see ItemList).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bsvd {
+
+template <typename T>
+int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st,
+              ItemList wl = all_items());
+template <typename T>
+int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
+                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
+                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st,
+                      ItemList wl = all_items());
+template <typename T>
+int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                       void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl = all_items());
+template <typename T>
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
+template <typename T>
+int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
+                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
+size_t rsvd_workspace(int batch, int max_m, int max_n, const int* h_m, const int* h_n);
+int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                const int* hint, const int* kmax, double eps, int p, int rounds, unsigned long long seed,
+                void* const* dU, const int* LDU, void* const* dS, void* const* dV, const int* LDV, int* rank_out,
+                float* err_est, int* samples, int* info, void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace bsvd

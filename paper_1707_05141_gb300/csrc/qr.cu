@@ -11,13 +11,14 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "launch.cuh"
 
 namespace bsvd {
 
 template <typename T>
 __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const int* M, const int* N,
                           const int* LDA, T* const* Q, const int* LDQ, T* const* R, const int* LDR,
-                          int* info)
+                          int* info, ItemList wl)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
@@ -29,7 +30,7 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
     const int warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
 
-    for (int b = blockIdx.x; b < batch; b += gridDim.x) {
+    for (int b = item_first(wl, batch); b >= 0; b = item_next(wl, batch, b)) {
         const int m = M[b], n = N[b], lda = LDA[b];
         const int ldq = Q ? LDQ[b] : m, ldr = R ? LDR[b] : n;
         const bool bad = m < 0 || n < 0 || m < n || m > max_m || n > max_n || lda < (m > 1 ? m : 1) ||
@@ -114,7 +115,8 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
 
 template <typename T>
 int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
-              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st)
+              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st,
+              ItemList wl)
 {
     const size_t smem = ((size_t)max_m * max_n + max_n) * sizeof(T);
     const int threads = max_n <= 32 ? 128 : 256;
@@ -122,15 +124,16 @@ int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, con
         if (cudaFuncSetAttribute(qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BSVD_ERR_CUDA;
     }
-    const int grid = batch < (1 << 30) ? batch : (1 << 30);
+    const int grid = item_grid(qr_kernel<T>, threads, smem, wl, batch, st);
+    if (grid == 0) return BSVD_ERR_CUDA;
     qr_kernel<T><<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ,
-                                              (T* const*)R, LDR, info);
+                                              (T* const*)R, LDR, info, wl);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
 template int launch_qr<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                              const int*, void* const*, const int*, int*, cudaStream_t);
+                              const int*, void* const*, const int*, int*, cudaStream_t, ItemList);
 template int launch_qr<double>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                               const int*, void* const*, const int*, int*, cudaStream_t);
+                               const int*, void* const*, const int*, int*, cudaStream_t, ItemList);
 
 }  // namespace bsvd

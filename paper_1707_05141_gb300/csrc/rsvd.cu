@@ -23,28 +23,10 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "launch.cuh"
 #include "philox.cuh"
 
 namespace bsvd {
-
-template <typename T>
-int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
-              void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st);
-template <typename T>
-int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
-                      const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
-                      double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st);
-template <typename T>
-int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
-                       void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
-                       int max_sweeps, int* info, long long* rot, cudaStream_t st);
-template <typename T>
-size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
-template <typename T>
-int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
-                        const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
-                        const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
-                        cudaStream_t st);
 
 constexpr int kProbes = 8;     // probe columns of the posterior estimate
 constexpr int kLCap = 128;     // sample cap: the small SVD stays in the register / shared tiers
@@ -93,8 +75,13 @@ struct RsArrays {
     int *m_smem, *n_smem;                 // ... for the shared tier
     int *m_blk, *n_blk;                   // ... for the block tier (min(m, n) > 128)
     int* info;                            // scratch info of the inner stages
+    // item lists (see ItemList) built with the arrays: blocks sampling in this round, split by
+    // the tier of their small SVD; full-rank blocks of the register and shared tiers
+    int *list_act, *list_lreg, *list_lsmem, *list_reg, *list_smem;
+    int* cnt;                             // their lengths, RL_* order
     RsState* st;
 };
+enum { RL_ACT = 0, RL_LREG, RL_LSMEM, RL_REG, RL_SMEM, RL_COUNT };
 
 // ------------------------------------------------------------------------------------------------
 // batched GEMM  C (M x N) = op(A) (M x K) * B (K x N), FP32, per-block sizes.
@@ -104,17 +91,14 @@ struct RsArrays {
 // 64 x 64 output tile per CTA, 256 threads with a 4 x 4 register tile, K staged 16 at a time.
 // ------------------------------------------------------------------------------------------------
 template <bool TRANS_A, bool OMEGA>
-__global__ void __launch_bounds__(256) gemm_batched_kernel(float* const* A, const int* LDA, float* const* B,
-                                                           const int* LDB, float* const* C, const int* LDC,
-                                                           const int* M, const int* N, const int* K,
-                                                           const int* NOMEGA, unsigned long long seed)
+__device__ __forceinline__ void gemm_tile(int b, int tm, int tn, float* const* A, const int* LDA, float* const* B,
+                                          const int* LDB, float* const* C, const int* LDC, const int* M, const int* N,
+                                          const int* K, const int* NOMEGA, unsigned long long seed)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ float As[BK][BM + 4];
     __shared__ float Bs[BK][BN + 4];
-    const int b = blockIdx.x;
     const int Mb = M[b], Nb = N[b], Kb = K[b];
-    const int tm = blockIdx.y / ((kMaxDim + kProbes + BN - 1) / BN), tn = blockIdx.y % ((kMaxDim + kProbes + BN - 1) / BN);
     const int m0 = tm * BM, n0 = tn * BN;
     if (Mb <= 0 || Nb <= 0 || m0 >= Mb || n0 >= Nb) return;
     const float* a = A[b];
@@ -194,14 +178,28 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(float* const* A, cons
     }
 }
 
+// persistent over a list of matrices; a CTA computes every output tile of the matrix it claims
 template <bool TRANS_A, bool OMEGA>
-static int gemm(int batch, float* const* A, const int* LDA, float* const* B, const int* LDB, float* const* C,
-                const int* LDC, const int* M, const int* N, const int* K, const int* NOM, unsigned long long seed,
-                cudaStream_t st)
+__global__ void __launch_bounds__(256) gemm_batched_kernel(ItemList wl, float* const* A, const int* LDA,
+                                                           float* const* B, const int* LDB, float* const* C,
+                                                           const int* LDC, const int* M, const int* N, const int* K,
+                                                           const int* NOMEGA, unsigned long long seed)
 {
-    constexpr int tiles = ((kMaxDim + 63) / 64) * ((kMaxDim + kProbes + 63) / 64);
-    gemm_batched_kernel<TRANS_A, OMEGA><<<dim3(batch, tiles), 256, 0, st>>>(A, LDA, B, LDB, C, LDC, M, N, K, NOM,
-                                                                            seed);
+    for (int b = list_item(wl); b >= 0; b = list_item(wl)) {
+        const int tn_count = (N[b] + 63) / 64, tiles = ((M[b] + 63) / 64) * tn_count;
+        for (int t = 0; t < tiles; ++t)
+            gemm_tile<TRANS_A, OMEGA>(b, t / tn_count, t % tn_count, A, LDA, B, LDB, C, LDC, M, N, K, NOMEGA, seed);
+    }
+}
+
+template <bool TRANS_A, bool OMEGA>
+static int gemm(int batch, ItemList wl, float* const* A, const int* LDA, float* const* B, const int* LDB,
+                float* const* C, const int* LDC, const int* M, const int* N, const int* K, const int* NOM,
+                unsigned long long seed, cudaStream_t st)
+{
+    const int grid = item_grid(gemm_batched_kernel<TRANS_A, OMEGA>, 256, 0, wl, batch, st);
+    if (grid == 0) return BSVD_ERR_CUDA;
+    gemm_batched_kernel<TRANS_A, OMEGA><<<grid, 256, 0, st>>>(wl, A, LDA, B, LDB, C, LDC, M, N, K, NOM, seed);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
@@ -324,17 +322,23 @@ __global__ void rs_arrays_kernel(int batch, float* scratch, RsArrays ar, int fin
     ar.n_smem[b] = smem ? n : 0;
     ar.m_blk[b] = blk ? m : 0;
     ar.n_blk[b] = blk ? n : 0;
+    if (act) {
+        ar.list_act[atomicAdd(&ar.cnt[RL_ACT], 1)] = b;
+        if (l <= 64) ar.list_lreg[atomicAdd(&ar.cnt[RL_LREG], 1)] = b;
+        else ar.list_lsmem[atomicAdd(&ar.cnt[RL_LSMEM], 1)] = b;
+    }
+    if (reg) ar.list_reg[atomicAdd(&ar.cnt[RL_REG], 1)] = b;
+    if (smem) ar.list_smem[atomicAdd(&ar.cnt[RL_SMEM], 1)] = b;
 }
 
 // ------------------------------------------------------------------------------------------------
 // posterior estimate and the next round's decision (one CTA per active block)
 //   E = A Wp - Uw diag(S) (Vw^T Wp)  with A Wp = the probe columns of Y (kept since sampling)
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) rs_estimate_kernel(RsArrays ar, unsigned long long seed, double eps, int p)
+__device__ __forceinline__ void rs_estimate_item(int b, const RsArrays& ar, unsigned long long seed, double eps, int p)
 {
     __shared__ float t[kLCap][kProbes];   // S (Vw^T Wp)
     __shared__ double red[8];
-    const int b = blockIdx.x;
     RsState* s = ar.st + b;
     if (s->mode != RS_RSVD) return;
     const int m = s->m, n = s->n, l = s->ell;
@@ -392,6 +396,12 @@ __global__ void __launch_bounds__(256) rs_estimate_kernel(RsArrays ar, unsigned 
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256) rs_estimate_kernel(ItemList wl, RsArrays ar, unsigned long long seed, double eps,
+                                                          int p)
+{
+    for (int b = list_item(wl); b >= 0; b = list_item(wl)) rs_estimate_item(b, ar, seed, eps, p);
 }
 
 // blocks still sampling after the last round fall back to the full SVD
@@ -466,11 +476,11 @@ __global__ void __launch_bounds__(256) rs_finish_kernel(RsArrays ar, float* cons
 // host driver
 // ------------------------------------------------------------------------------------------------
 struct RsFixed {
-    size_t off_state, off_ptr, off_int, off_bjws, bj_bytes, off_scratch;
+    size_t off_state, off_ptr, off_int, off_ctr, off_bjws, bj_bytes, off_scratch;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr int kPtrArrays = 9, kIntArrays = 17;
+constexpr int kPtrArrays = 9, kIntArrays = 22;
 
 static RsFixed rs_fixed(int batch, int max_m, int max_n)
 {
@@ -482,6 +492,8 @@ static RsFixed rs_fixed(int batch, int max_m, int max_n)
     o = al256(o + sizeof(float*) * (size_t)batch * kPtrArrays);
     F.off_int = o;
     o = al256(o + sizeof(int) * (size_t)batch * kIntArrays);
+    F.off_ctr = o;
+    o = al256(o + sizeof(unsigned long long) * 8 + sizeof(int) * 8);  // claim counters, list lengths
     F.off_bjws = o;
     const int kmx = max_m < max_n ? max_m : max_n;
     F.bj_bytes = kmx > kLCap ? block_jacobi_workspace<float>(batch, max_m, max_n, 32, 0) : 0;
@@ -518,10 +530,14 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     int* ip = reinterpret_cast<int*>(w + F.off_int);
     int** islots[kIntArrays] = {&ar.m_act, &ar.n_act, &ar.l_act, &ar.lp_act, &ar.l_reg, &ar.l_smem,
                                 &ar.ld_m, &ar.ld_n, &ar.ld_l, &ar.m_reg, &ar.n_reg, &ar.m_smem,
-                                &ar.n_smem, &ar.m_blk, &ar.n_blk, &ar.info, nullptr};
+                                &ar.n_smem, &ar.m_blk, &ar.n_blk, &ar.info, &ar.list_act, &ar.list_lreg,
+                                &ar.list_lsmem, &ar.list_reg, &ar.list_smem, nullptr};
     for (int i = 0; i < kIntArrays; ++i)
         if (islots[i]) *islots[i] = ip + (size_t)i * batch;
     float* scratch = reinterpret_cast<float*>(w + F.off_scratch);
+    unsigned long long* claim = reinterpret_cast<unsigned long long*>(w + F.off_ctr);  // one launch at a time
+    ar.cnt = reinterpret_cast<int*>(claim + 8);
+    auto listed = [&](const int* idx, int which) { return ItemList{idx, ar.cnt + which, claim}; };
     const long long capacity = (long long)((ws_bytes - F.off_scratch) / sizeof(float));
 
     rs_plan_kernel<<<batch, 256, 0, st>>>(batch, max_m, max_n, (float* const*)A, M, N, LDA, hint, p, ar.st, info);
@@ -533,60 +549,65 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     const int kx = mx < nx ? mx : nx;
     const int lx = kx < kLCap ? kx : kLCap;
     int rc = BSVD_SUCCESS;
+    const ItemList act = listed(ar.list_act, RL_ACT);
     for (int r = 0; r < rounds && rc == BSVD_SUCCESS && lx > 0; ++r) {
+        if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RL_COUNT, st) != cudaSuccess) return BSVD_ERR_CUDA;
         rs_arrays_kernel<<<tb, 128, 0, st>>>(batch, scratch, ar, 0);
         // sample: Y = A [Omega | probes]
-        rc = gemm<false, true>(batch, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act, ar.n_act,
+        rc = gemm<false, true>(batch, act, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act, ar.n_act,
                                ar.l_act, seed, st);
         if (rc) break;
         rc = launch_qr<float>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY,
-                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
         if (rc) break;
         // power step: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
-        rc = gemm<true, false>(batch, fA, LDA, ar.pY, ar.ld_m, ar.pZ, ar.ld_n, ar.n_act, ar.l_act, ar.m_act, nullptr,
-                               seed, st);
+        rc = gemm<true, false>(batch, act, fA, LDA, ar.pY, ar.ld_m, ar.pZ, ar.ld_n, ar.n_act, ar.l_act, ar.m_act,
+                               nullptr, seed, st);
         if (rc) break;
         rc = launch_qr<float>(batch, nx, lx, (void* const*)ar.pZ, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pZ,
-                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
         if (rc) break;
-        rc = gemm<false, false>(batch, fA, LDA, ar.pZ, ar.ld_n, ar.pY, ar.ld_m, ar.m_act, ar.l_act, ar.n_act, nullptr,
-                                seed, st);
+        rc = gemm<false, false>(batch, act, fA, LDA, ar.pZ, ar.ld_n, ar.pY, ar.ld_m, ar.m_act, ar.l_act, ar.n_act,
+                                nullptr, seed, st);
         if (rc) break;
         rc = launch_qr<float>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY,
-                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
         if (rc) break;
         // project: B^T = A^T Q, [Q_B, R_B] = qr(B^T)
-        rc = gemm<true, false>(batch, fA, LDA, ar.pY, ar.ld_m, ar.pBt, ar.ld_n, ar.n_act, ar.l_act, ar.m_act, nullptr,
-                               seed, st);
+        rc = gemm<true, false>(batch, act, fA, LDA, ar.pY, ar.ld_m, ar.pBt, ar.ld_n, ar.n_act, ar.l_act, ar.m_act,
+                               nullptr, seed, st);
         if (rc) break;
         rc = launch_qr<float>(batch, nx, lx, (void* const*)ar.pBt, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pBt,
-                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st);
+                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
         if (rc) break;
         // small SVD of R_B (l x l): register tier up to 64, shared tier above
         const int lr = lx < 64 ? lx : 64;
         rc = launch_jacobi_reg<float>(batch, lr, lr, 0, (void* const*)ar.pR, ar.l_reg, ar.l_reg, ar.ld_l,
                                       (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
-                                      ar.ld_l, 0.0, 0, ar.info, nullptr, st);
+                                      ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_lreg, RL_LREG));
         if (rc) break;
         if (lx > 64) {
             rc = launch_jacobi_smem<float>(batch, lx, lx, (void* const*)ar.pR, ar.l_smem, ar.l_smem, ar.ld_l,
                                            (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
-                                           ar.ld_l, 0.0, 0, ar.info, nullptr, st);
+                                           ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_lsmem, RL_LSMEM));
             if (rc) break;
         }
         // U = Q V', V = Q_B U'
-        rc = gemm<false, false>(batch, ar.pY, ar.ld_m, ar.pVp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act, ar.l_act,
-                                nullptr, seed, st);
+        rc = gemm<false, false>(batch, act, ar.pY, ar.ld_m, ar.pVp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act,
+                                ar.l_act, nullptr, seed, st);
         if (rc) break;
-        rc = gemm<false, false>(batch, ar.pBt, ar.ld_n, ar.pUp, ar.ld_l, ar.pVw, ar.ld_n, ar.n_act, ar.l_act, ar.l_act,
-                                nullptr, seed, st);
+        rc = gemm<false, false>(batch, act, ar.pBt, ar.ld_n, ar.pUp, ar.ld_l, ar.pVw, ar.ld_n, ar.n_act, ar.l_act,
+                                ar.l_act, nullptr, seed, st);
         if (rc) break;
-        rs_estimate_kernel<<<batch, 256, 0, st>>>(ar, seed, eps, p);
+        const int ge = item_grid(rs_estimate_kernel, 256, 0, act, batch, st);
+        if (ge == 0) return BSVD_ERR_CUDA;
+        rs_estimate_kernel<<<ge, 256, 0, st>>>(act, ar, seed, eps, p);
         if (cudaGetLastError() != cudaSuccess) rc = BSVD_ERR_CUDA;
     }
     if (rc) return rc;
     // full-rank blocks, and blocks whose estimate never passed, by the direct Jacobi tiers
     rs_fallback_kernel<<<tb, 128, 0, st>>>(batch, ar.st);
+    if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RL_COUNT, st) != cudaSuccess) return BSVD_ERR_CUDA;
     rs_arrays_kernel<<<tb, 128, 0, st>>>(batch, scratch, ar, 1);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     const int mm_x = mx > nx ? mx : nx;
@@ -594,15 +615,16 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
         // bounds cover every block routed to each tier (max(m, n), min(m, n) order is what counts)
         rc = launch_jacobi_reg<float>(batch, mm_x < 128 ? mm_x : 128, kx < 64 ? kx : 64, 0, A, ar.m_reg, ar.n_reg, LDA,
                                       (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n,
-                                      0.0, 0, ar.info, nullptr, st);
+                                      0.0, 0, ar.info, nullptr, st, listed(ar.list_reg, RL_REG));
         if (rc) return rc;
         if (mm_x > 128 || kx > 64) {
             rc = launch_jacobi_smem<float>(batch, mm_x, kx < kLCap ? kx : kLCap, A, ar.m_smem, ar.n_smem, LDA,
                                            (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw,
-                                           ar.ld_n, 0.0, 0, ar.info, nullptr, st);
+                                           ar.ld_n, 0.0, 0, ar.info, nullptr, st, listed(ar.list_smem, RL_SMEM));
             if (rc) return rc;
         }
         if (kx > kLCap) {
+            // the block tier keeps its own list of live matrices: blocks not routed to it are 0 x 0
             rc = launch_block_jacobi<float>(batch, mx, nx, 32, 0, A, ar.m_blk, ar.n_blk, LDA, (void* const*)ar.pS,
                                             (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n, 0.0, 0,
                                             ar.info, nullptr, w + F.off_bjws, F.bj_bytes, st);
