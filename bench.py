@@ -50,13 +50,21 @@ def measured_hbm_gbs() -> float:
 
 # DRAM bytes (read + write) per launch of a dominant kernel from one ncu capture, keyed by the
 # digest of the kernel source it was taken on (a changed kernel reports null, not stale counters).
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch from an ncu capture, keyed by the digest of the kernel's
+# sources at capture time; a changed kernel has no entry (traffic null).  profiles/ holds the
+# capture summaries.
+TRAFFIC = {
+    # jacobi_reg_kernel, 64x64 FP32 tier 0x101: 441.9 MB for 10 000 matrices, scaled to 20 000
+    "jacobi_reg:529d842f827b78e0": 883.8e6,
+}
 
 
-def kernel_digest(name: str) -> str:
-    p = os.path.join(ROOT, "paper_1707_05141_gb300", "csrc", name)
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_digest(*names: str) -> str:
+    h = hashlib.sha256()
+    for name in names + ("common.cuh",):
+        with open(os.path.join(ROOT, "paper_1707_05141_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ----------------------------------------------------------------------------------------------
@@ -152,10 +160,12 @@ class SvdQr64:
         self.nb, self.nq = args.svd_batch, args.qr_batch
 
     def config(self, world):
-        return {"workload": "svd64_qr128: Jacobi SVD (U,S,V) of 20000 FP32 64x64 + Householder QR (Q,R) of 20000 "
-                            "FP32 128x32 per GPU per step; sigma_i = exp(-i/8), Haar U, V",
+        mb = (self.nb * 64 * 64 + self.nq * 128 * 32) * 4 / 1e6
+        return {"workload": f"svd64_qr128: Jacobi SVD (U,S,V) of {self.nb} FP32 64x64 + Householder QR (Q,R) of "
+                            f"{self.nq} FP32 128x32 per GPU per step; sigma_i = exp(-i/8), Haar U, V",
                 "svd_batch_per_gpu": self.nb, "qr_batch_per_gpu": self.nq, "m": 64, "n": 64, "qr_m": 128,
-                "qr_n": 32, "l2": "inputs (656 MB per GPU) larger than L2; no flush",
+                "qr_n": 32, "l2": f"inputs ({mb:.0f} MB per GPU) {'larger' if mb > 129 else 'smaller'} than L2; "
+                                  "no flush",
                 "parallelism": f"independent batches per GPU x{world}"}
 
     def setup(self, rank, dev):
@@ -205,7 +215,9 @@ class SvdQr64:
         tier = int(self.tuned["tier"])
         reg = (tier & 0xff) == bs.TIER_REGISTER
         kname = ("jacobi_reg_kernel" if reg else "jacobi_smem_kernel") + f" (tier {tier:#x})"
-        traffic = TRAFFIC.get(kernel_digest("jacobi_reg.cu" if reg else "jacobi_smem.cu"))
+        traffic = TRAFFIC.get("jacobi_reg:" + kernel_digest("jacobi_reg.cu")) if reg else None
+        if traffic is not None:
+            traffic *= self.nb / 20000  # per launch: scales with the matrix count
         roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "ms_per_launch": kernel_ms,
                 "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (max SM clock)"}
