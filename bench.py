@@ -333,7 +333,8 @@ class Block512:
 
     def config(self, world):
         return {"workload": "block512: block-Jacobi SVD (U,S,V) of 500 FP32 512x512 per GPU per step, GRAM "
-                            "method, block width 32; sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
+                            "method, block width 32, pair Gram products on the tensor cores (TF32 hi/lo split, "
+                            "FP32 accumulation), updates on FP32 SIMT; sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
                 "l2": "inputs (524 MB per GPU) larger than L2", "parallelism": f"independent batches per GPU x{world}"}
 
     def setup(self, rank, dev):
@@ -383,6 +384,28 @@ class Block512:
                  "peak_note": "FP32 SIMT; achieved counts Gram + update flops of the pairs of every sweep run"},
                 {"sweeps_mean": float(np.mean(sweeps)), "sweeps_max": int(np.max(sweeps)),
                  "max_sigma_err_vs_generator": err})
+
+    def plain_ms(self, stream):
+        """The same call with the Gram products on the FP32 SIMT pipes (the plain FP32 form), timed
+        once after a warm-up run, for the mixed-vs-plain comparison."""
+        import torch
+
+        def run():
+            self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
+                                             max_sweeps=20, block_width=32, method=self.bs.BLOCK_SIMT_PRODUCTS,
+                                             stream=stream)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info_h = self.info.cpu().numpy()
+        sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
+        err = float(np.abs(self.S.cpu().numpy()[:, 0, :] - self.sigma).max())
+        return {"plain_simt_ms": e0.elapsed_time(e1), "plain_sweeps_mean": float(np.mean(sweeps)),
+                "plain_max_sigma_err_vs_generator": err}
 
     def cpu_sample(self, n):
         import gen

@@ -48,6 +48,8 @@ extern "C" {
 #define BSVD_INFO_NO_SCRATCH (-2)         /* batched_rsvd: workspace too small for this matrix */
 #define BSVD_INFO_RANK_CAPPED (1 << 21)   /* batched_rsvd: the rank needed exceeds kmax */
 #define BSVD_INFO_FALLBACK (1 << 22)      /* batched_rsvd: sampling did not pass, full SVD used */
+#define BSVD_INFO_DEVICE_TIMEOUT (-3)     /* a bounded on-device wait (tensor-core completion) gave up;
+                                             the results of this call are not valid */
 
 /* Jacobi memory tiers (argument `tier` of batched_svd_jacobi).  `tier` may carry a variant in
    bits 8 and up: BSVD_TIER_REGISTER | (k << 8) forces the k-th register variant that fits the
@@ -131,6 +133,11 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
 /* Block-Jacobi methods (argument `method` of batched_svd_block_jacobi), Algorithm 3 */
 #define BSVD_BLOCK_GRAM 0   /* Section 6.1: pair Gram matrix G, its eigenvectors as the block rotation */
 #define BSVD_BLOCK_DIRECT 1 /* Section 6.2: pair QR, SVD of the triangular factor */
+/* Flag for `method`: FP32 data with block width 32 form the pair Gram matrices on the tensor cores
+ * by default (TF32 operands split into a high and a low part, all four products, FP32
+ * accumulation: FP32-level accuracy); this flag forms them with FP32 SIMT dot products instead
+ * (the plain FP32 form).  The block updates run on the FP32 SIMT pipes either way. */
+#define BSVD_BLOCK_SIMT_PRODUCTS (1 << 16)
 
 /*
  * batched_svd_block_jacobi_workspace -- bytes of DEVICE workspace batched_svd_block_jacobi needs
@@ -153,6 +160,8 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *   block_width   bw = 16 or 32 columns per block (the paper uses 32, Section 6.3).
  *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
  *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
+ *                 | BSVD_BLOCK_SIMT_PRODUCTS keeps the Gram products on the FP32 SIMT pipes (FP32
+ *                 data with bw = 32 form them on the tensor cores otherwise).
  *                 DIRECT needs max(m, n) * 2 bw * sizeof(element) <= 200 KiB (the pair's QR runs on
  *                 chip); its default tol is 8 sqrt(max(m, n)) u, since its rotations are only as
  *                 orthogonal as the pair's Householder Q.
@@ -160,7 +169,8 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *                 the caller, contents need not be initialised; not used after the stream work
  *                 completes.  Smaller -> BSVD_ERR_WORKSPACE.
  *   d_info[b]     block sweeps run (the last one rotates no pair), or BSVD_INFO_NOT_CONVERGED +
- *                 sweeps, or BSVD_INFO_BAD_SHAPE.
+ *                 sweeps, or BSVD_INFO_BAD_SHAPE, or BSVD_INFO_DEVICE_TIMEOUT (every matrix of the
+ *                 call) when a tensor-core completion wait gave up.
  *   d_rotations[b] (nullable) number of block-pair rotations applied.
  * Limits: max(m, n) <= 16384.  Host launches max_sweeps * (nb - 1) steps without synchronising.
  */

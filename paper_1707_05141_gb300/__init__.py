@@ -27,6 +27,8 @@ INFO_NOT_CONVERGED = 1 << 20
 INFO_NO_SCRATCH = -2
 INFO_RANK_CAPPED = 1 << 21
 INFO_FALLBACK = 1 << 22
+INFO_DEVICE_TIMEOUT = -3
+BLOCK_SIMT_PRODUCTS = 1 << 16
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
 
 _lock = threading.Lock()

@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "launch.cuh"
+#include "tcgen05.cuh"
 
 namespace bsvd {
 
@@ -48,7 +49,8 @@ struct BjCounters {
     unsigned long long claim[8];  // gram, pack, polish, update, QR, inner SVD
     int pcount;                   // rotating pairs of the current step (plist)
     int mcount;                   // matrices not yet converged (mlist)
-    int pad[2];
+    int timeouts;                 // tensor-core completion waits that gave up (0 in a valid run)
+    int pad;
 };
 constexpr size_t kStepCounterBytes = offsetof(BjCounters, mcount);  // claims + pcount: zeroed every step
 
@@ -200,10 +202,11 @@ __device__ __forceinline__ void bj_gram_item(int it, int batch, int npairs, int 
     const int mm = st->mm, nn = st->nn, nblk = st->nblk;
     const int nbp = nblk + (nblk & 1);
     int bi = 0, bj = 0;
-    if (k < nbp / 2) round_robin_pair(nbp, step, k, bi, bj);
+    if (k < nbp / 2 && step < nbp - 1) round_robin_pair(nbp, step, k, bi, bj);
     // pairs with the virtual block (odd nb) are skipped, except for a single block, which is
-    // orthogonalised internally through its pair with the empty block
-    const bool live = !st->converged && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn;
+    // orthogonalised internally through its pair with the empty block; a matrix with fewer blocks
+    // than the batch's largest runs its own nbp - 1 steps of each sweep and idles in the rest
+    const bool live = !st->converged && step < nbp - 1 && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn;
     if (!live) {
         if (threadIdx.x == 0) im[it] = in[it] = 0;
         return;
@@ -373,7 +376,9 @@ __device__ __forceinline__ void bj_polish_item(int it, unsigned char* ws, const 
         for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[k][or0 + q], e, acc[q]);
     }
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = xs[oc][or0 + q] - T(0.5) * acc[q];
+    for (int q = 0; q < TPO; ++q) acc[q] = xs[oc][or0 + q] - T(0.5) * acc[q];
+#pragma unroll
+    for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = acc[q];
 }
 
 template <typename T, int K2>
@@ -482,6 +487,275 @@ __global__ void __launch_bounds__(256) bj_update_kernel(int tiles, int npairs, i
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Tensor-core Gram stage (FP32 data, bw = 32: pair width 64).  G = X^T X runs on tcgen05 in TF32
+// with FP32 accumulation; every FP32 element x is split as x = hi + lo with hi = tf32(x) and
+// lo = tf32(x - hi), both rounded to nearest (x carried to 2^-23 relative, without bias), and all
+// four products hi^T hi, hi^T lo, lo^T hi, lo^T lo are formed.  Operands are staged through
+// registers into the K-major core-matrix layout of tcgen05.cuh; the accumulator lives in tensor
+// memory.  The update stays on the SIMT pipes: measured on this GPU, the tensor core's FP32
+// accumulation rounds toward zero (mean error -2.7e-7 relative for a K = 64 product of exact
+// TF32 values, FP32 FMA +2e-9), a bias that V, updated ~200 times per column, accumulates to
+// ||V^T V - I|| ~ 2e-5, above the 1e-5 gate; the Gram only feeds the pair test and the inner
+// SVD, whose rotation is re-orthogonalised, so its bias does not accumulate.
+// ------------------------------------------------------------------------------------------------
+constexpr int kTcGramKc = 32;                                   // rows of X per staged chunk
+constexpr uint32_t kTcLbo = 128;                                // K-adjacent core matrices
+constexpr uint32_t kTcGramSbo = (kTcGramKc / 4) * 128;          // 1024 B between 8-row groups
+constexpr uint32_t kTcGramStage = 128u * kTcGramKc * 4u;        // 16 KB: 64 hi + 64 lo rows x KC
+constexpr int kTcGramStages = 3;
+// 3 stages (48 KB) + alignment: at most four CTAs fit an SM, so 4 x 128 TMEM columns <= 512
+constexpr size_t kTcGramSmem = kTcGramStages * kTcGramStage + 1024 + 64;
+
+// next claimed position, or "none" once any tensor-core wait of the call has given up (uniform
+// over the CTA: thread 0 decides, the barrier publishes)
+__device__ __forceinline__ long long tc_next(BjCounters* C, int which)
+{
+    __shared__ long long s_pos;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_pos = *reinterpret_cast<volatile int*>(&C->timeouts) != 0 ? (1ll << 62)
+                                                                     : (long long)atomicAdd(&C->claim[which], 1ull);
+    __syncthreads();
+    return s_pos;
+}
+
+__device__ __forceinline__ unsigned char* align1k(unsigned char* p)
+{
+    return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+__device__ __forceinline__ float4 tc_hi(float4 v)
+{
+    return make_float4(tc::to_tf32(v.x), tc::to_tf32(v.y), tc::to_tf32(v.z), tc::to_tf32(v.w));
+}
+
+__device__ __forceinline__ float4 tc_lo(float4 v, float4 h)
+{
+    return make_float4(tc::to_tf32(v.x - h.x), tc::to_tf32(v.y - h.y), tc::to_tf32(v.z - h.z),
+                       tc::to_tf32(v.w - h.w));
+}
+
+__device__ __forceinline__ void tc_split_store(unsigned char* hi_base, unsigned char* lo_base, uint32_t off,
+                                               float4 v)
+{
+    const float4 h = tc_hi(v);
+    *reinterpret_cast<float4*>(hi_base + off) = h;
+    *reinterpret_cast<float4*>(lo_base + off) = tc_lo(v, h);
+}
+
+// Gram of one pair item: D = [X_hi X_lo]^T [X_hi X_lo] (128 x 128, M = N = 128, K = rows), then
+// G = D11 + D12 + D21 + D22 = hi^T hi + hi^T lo + lo^T hi + lo^T lo: X^T X up to the TF32 reading
+// of lo (relative 2^-22).
+// Pair test as the SIMT kernel's: max |G_pq| / sqrt(G_pp G_qq), located in FP32 and evaluated in
+// FP64 for the winning element.
+__device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, int bw, float* const* U,
+                                                const int* LDU, float* const* V, const int* LDV, const int* M,
+                                                const int* N, unsigned char* ws, const BjLayout& L, double tol,
+                                                unsigned char* sm, uint32_t tmem, uint64_t* bars,
+                                                uint32_t& phase, BjCounters* C)
+{
+    constexpr int K2 = 64;
+    __shared__ float gd[K2];
+    __shared__ float redv[4];
+    __shared__ int redi[4];
+    const int b = it / npairs, k = it - b * npairs;
+    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    int* im = reinterpret_cast<int*>(ws + L.off_m);
+    int* in = reinterpret_cast<int*>(ws + L.off_n);
+    const int mm = st->mm, nn = st->nn, nblk = st->nblk;
+    const int nbp = nblk + (nblk & 1);
+    int bi = 0, bj = 0;
+    if (k < nbp / 2 && step < nbp - 1) round_robin_pair(nbp, step, k, bi, bj);
+    const bool live = !st->converged && step < nbp - 1 && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn &&
+                      mm > 0;  // (the SIMT item explains each condition)
+    if (!live) {
+        if (threadIdx.x == 0) im[it] = in[it] = 0;
+        return;
+    }
+    const bool tr = M[b] < N[b];
+    const float* W = tr ? V[b] : U[b];
+    const int ldw = tr ? LDV[b] : LDU[b];
+    const int tid = threadIdx.x;
+    const bool vec = (ldw & 3) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+    const int nch = (mm + kTcGramKc - 1) / kTcGramKc;
+    constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const int s = c % kTcGramStages;
+        unsigned char* stage = sm + s * kTcGramStage;
+        if (c >= kTcGramStages) {  // the MMAs of chunk c - 3 read this stage
+            if (ok) ok = tc::mbar_wait(&bars[s], (phase >> s) & 1u);  // after a failure: no more waits
+            phase ^= 1u << s;
+        }
+        const int r0 = c * kTcGramKc;
+        // unit (column i, 4-row group g): consecutive threads take consecutive columns, so eight
+        // threads write one 128-byte core matrix
+#pragma unroll
+        for (int j = 0; j < (K2 * kTcGramKc / 4) / 128; ++j) {
+            const int u = tid + 128 * j;
+            const int i = u & (K2 - 1), g = u / K2;
+            const int col = bj_col(bi, bj, bw, i, nn);
+            const int r = r0 + 4 * g;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (col >= 0) {
+                const float* src = W + (size_t)col * ldw + r;
+                if (vec && r + 3 < mm) {
+                    v = *reinterpret_cast<const float4*>(src);
+                } else {
+                    if (r + 0 < mm) v.x = src[0];
+                    if (r + 1 < mm) v.y = src[1];
+                    if (r + 2 < mm) v.z = src[2];
+                    if (r + 3 < mm) v.w = src[3];
+                }
+            }
+            // hi to operand rows 0..63, lo to rows 64..127 of the same stage
+            tc_split_store(stage + tc::kmajor_offset(i, 4 * g, kTcLbo, kTcGramSbo),
+                           stage + tc::kmajor_offset(K2 + i, 4 * g, kTcLbo, kTcGramSbo), 0u, v);
+        }
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t base = tc::smem_u32(stage);
+#pragma unroll
+            for (int kk = 0; kk < kTcGramKc / 8; ++kk) {
+                const uint64_t d = tc::desc_kmajor(base + kk * 2 * kTcLbo, kTcLbo, kTcGramSbo);
+                tc::mma_tf32(tmem, d, d, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bars[s]);
+        }
+    }
+    // drain: the last (up to three) chunks' commits, one per barrier
+    for (int c = nch > kTcGramStages ? nch - kTcGramStages : 0; c < nch; ++c) {
+        const int s = c % kTcGramStages;
+        if (ok) ok = tc::mbar_wait(&bars[s], (phase >> s) & 1u);
+        phase ^= 1u << s;
+    }
+    tc::fence_after_sync();
+    // epilogue: lane (row) i of D; P = D(i, 0:64) + D(i, 64:128)
+    const int warp = tid >> 5, lane = tid & 31;
+    const int row = warp * 32 + lane;
+    float p[K2];
+    {
+        float a[32], c2[32];
+        const uint32_t t = tmem + ((uint32_t)(warp * 32) << 16);
+        tc::tmem_ld32(t + 0, a);
+        tc::tmem_ld32(t + 64, c2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) p[j] = a[j] + c2[j];
+        tc::tmem_ld32(t + 32, a);
+        tc::tmem_ld32(t + 96, c2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) p[32 + j] = a[j] + c2[j];
+    }
+    tc::fence_before_sync();
+    float* Gs = reinterpret_cast<float*>(sm);  // 64 x 65, row-major, over the (idle) stages
+    __syncthreads();
+    if (row >= K2) {
+#pragma unroll
+        for (int j = 0; j < K2; ++j) Gs[(row - K2) * (K2 + 1) + j] = p[j];
+    }
+    __syncthreads();
+    if (row < K2) {
+#pragma unroll
+        for (int j = 0; j < K2; ++j) Gs[row * (K2 + 1) + j] += p[j];
+    }
+    __syncthreads();
+    if (!ok && tid == 0) atomicAdd(&C->timeouts, 1);
+    // G to the item's buffer (column-major; G is symmetric up to rounding), diagonal to gd
+    float* G = reinterpret_cast<float* const*>(ws + L.off_pG)[it];
+    for (int e = tid; e < K2 * K2; e += 128) {
+        const int gc = e / K2, gr = e - gc * K2;
+        G[e] = Gs[gr * (K2 + 1) + gc];
+    }
+    if (tid < K2) gd[tid] = Gs[tid * (K2 + 1) + tid];
+    __syncthreads();
+    // largest scaled off-diagonal element: located in FP32 ...
+    float best = -1.f;
+    int bidx = 0;
+    for (int e = tid; e < K2 * K2; e += 128) {
+        const int r = e / K2, c = e - r * K2;
+        if (r == c) continue;
+        const float dr = gd[r], dc = gd[c];
+        if (!(dr > 0.f) || !(dc > 0.f)) continue;
+        const float v = fabsf(Gs[r * (K2 + 1) + c]) * rsqrtf(dr) * rsqrtf(dc);
+        if (v > best) {
+            best = v;
+            bidx = e;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ov > best || (ov == best && oi < bidx)) {
+            best = ov;
+            bidx = oi;
+        }
+    }
+    if (lane == 0) {
+        redv[warp] = best;
+        redi[warp] = bidx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < 4; ++w)
+            if (redv[w] > best || (redv[w] == best && redi[w] < bidx)) {
+                best = redv[w];
+                bidx = redi[w];
+            }
+        // ... and evaluated in FP64
+        double em = 0.0;
+        if (best >= 0.f) {
+            const int r = bidx / K2, c = bidx - r * K2;
+            em = fabs((double)Gs[r * (K2 + 1) + c]) / sqrt((double)gd[r] * (double)gd[c]);
+        }
+        const bool rot = em > tol;
+        im[it] = rot ? K2 : 0;
+        in[it] = rot ? K2 : 0;
+        if (rot) {
+            atomicAdd(&st->rot_sweep, 1);
+            reinterpret_cast<int*>(ws + L.off_plist)[atomicAdd(&C->pcount, 1)] = it;
+        }
+        atomicMax(reinterpret_cast<unsigned long long*>(&st->emax), (unsigned long long)__double_as_longlong(em));
+    }
+}
+
+// TMEM and barriers are set up once per CTA; the CTA then claims pair items of the live matrices
+__global__ void __launch_bounds__(128) bj_gram_tc_kernel(int npairs, int step, int bw, float* const* U,
+                                                         const int* LDU, float* const* V, const int* LDV,
+                                                         const int* M, const int* N, unsigned char* ws, BjLayout L,
+                                                         double tol)
+{
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    __shared__ uint64_t bars[kTcGramStages];
+    __shared__ uint32_t tmem_slot;
+    unsigned char* sm = align1k(tc_raw);
+    BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&tmem_slot, 128);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcGramStages; ++s) tc::mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    uint32_t phase = 0;
+    const int* mlist = reinterpret_cast<const int*>(ws + L.off_mlist);
+    const long long items = (long long)C->mcount * npairs;
+    for (long long j = tc_next(C, 0); j < items; j = tc_next(C, 0)) {
+        const int b = mlist[j / npairs], k = (int)(j % npairs);
+        bj_gram_tc_item(b * npairs + k, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L, tol, sm, tmem, bars, phase, C);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 128);
+}
+
 // end of a sweep: a matrix whose sweep rotated nothing is converged
 __global__ void bj_sweep_end_kernel(int batch, int max_sweeps, int sweep, unsigned char* ws, BjLayout L, int* info)
 {
@@ -518,6 +792,10 @@ __global__ void __launch_bounds__(256) bj_finalize_kernel(int batch, T* const* S
     const int b = blockIdx.x;
     BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
     if (info[b] == BSVD_INFO_BAD_SHAPE) return;
+    if (reinterpret_cast<const BjCounters*>(ws + L.off_ctr)->timeouts != 0) {  // results not valid
+        if (threadIdx.x == 0) info[b] = BSVD_INFO_DEVICE_TIMEOUT;
+        return;
+    }
     const int mm = st->mm, nn = st->nn;
     if (threadIdx.x == 0 && rot_out) rot_out[b] = st->rotations;
     if (nn == 0) return;
@@ -603,7 +881,8 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                      int max_sweeps, int method, int* info, long long* rot, unsigned char* ws, cudaStream_t st)
 {
     const int bw = K2 / 2;
-    const int inner_variant = method >> 8;  // register-tier variant of the inner SVD (0: first fitting)
+    const int inner_variant = (method >> 8) & 0xff;  // register-tier variant of the inner SVD (0: first fitting)
+    const bool simt = (method & BSVD_BLOCK_SIMT_PRODUCTS) != 0;
     method &= 0xff;
     const bool direct = method != 0;
     const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
@@ -641,11 +920,24 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     const int g_pack = persistent_grid(bj_pack_kernel<T, K2>, 256, 0, items);
     const int g_polish = persistent_grid(bj_polish_kernel<T, K2>, 256, polish_smem, items);
     const int g_update = persistent_grid(bj_update_kernel<T, K2>, 256, 0, (long long)items * tiles);
+    // tensor-core Gram (FP32 data, bw = 32)
+    const bool tc_gram = sizeof(T) == 4 && K2 == 64 && !simt;
+    int g_gram_tc = 1;
+    if (tc_gram) {
+        if (cudaFuncSetAttribute(bj_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcGramSmem) !=
+            cudaSuccess)
+            return BSVD_ERR_CUDA;
+        g_gram_tc = persistent_grid(bj_gram_tc_kernel, 128, kTcGramSmem, items);
+    }
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int step = 0; step < nbp - 1; ++step) {
             if (cudaMemsetAsync(ctr, 0, kStepCounterBytes, st) != cudaSuccess) return BSVD_ERR_CUDA;
-            bj_gram_kernel<T, K2><<<g_gram, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU, (T* const*)V,
-                                                          LDV, M, N, ws, L, tol_outer);
+            if (tc_gram)
+                bj_gram_tc_kernel<<<g_gram_tc, 128, kTcGramSmem, st>>>(npairs, step, bw, (float* const*)U, LDU,
+                                                                      (float* const*)V, LDV, M, N, ws, L, tol_outer);
+            else
+                bj_gram_kernel<T, K2><<<g_gram, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU,
+                                                              (T* const*)V, LDV, M, N, ws, L, tol_outer);
             if (!direct) {
                 const int rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, im, in, ild, pS, nullptr, nullptr,
                                                     pX, ild, 0.0, 0, iinfo, nullptr, st,

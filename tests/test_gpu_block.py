@@ -31,11 +31,14 @@ def w2():
     return b, mats, So
 
 
-@pytest.mark.parametrize("method,bw", [(0, 32), (1, 32), (0, 16), (1, 16)])
+@pytest.mark.parametrize("method,bw", [(0, 32), (1, 32), (0, 16), (1, 16), (0 | (1 << 16), 32)])
 def test_block_512_log_uniform_sigma(bs, w2, method, bw):
+    """FP32 with bw = 32 forms the pair Gram matrices on the tensor cores; the BLOCK_SIMT_PRODUCTS
+    flag keeps them on the SIMT pipes."""
     b, mats, So = w2
     a = torch.from_numpy(b.a).cuda()
     u, s, v, info, rots = bs.svd_block(a, block_width=bw, method=method, max_sweeps=30)
+    method &= 0xff
     torch.cuda.synchronize()
     u, s, v = _host(u, s, v)
     info = info.cpu().numpy()
@@ -52,9 +55,10 @@ def test_block_512_log_uniform_sigma(bs, w2, method, bw):
             assert e["orth_u"] <= 4e-5, (i, e)
 
 
+@pytest.mark.parametrize("bw", [16, 32])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("method", [0, 1])
-def test_block_ragged_shapes(bs, dt, method):
+def test_block_ragged_shapes(bs, dt, method, bw):
     """Partial last block, a virtual empty block, wide input, tiny block counts."""
     shapes = [(96, 80), (70, 130), (64, 64), (200, 33), (33, 33), (5, 3)]
     rng = np.random.default_rng(21)
@@ -66,7 +70,7 @@ def test_block_ragged_shapes(bs, dt, method):
         sig = np.sort(10.0 ** rng.uniform(-2, 0, k))[::-1]
         a64 = (uu * sig) @ vv.T
         a = torch.from_numpy(np.ascontiguousarray(a64.T.astype(dt))[None]).cuda()
-        u, s, v, info, rots = bs.svd_block(a, block_width=16, method=method, max_sweeps=30)
+        u, s, v, info, rots = bs.svd_block(a, block_width=bw, method=method, max_sweeps=30)
         torch.cuda.synchronize()
         u, s, v = _host(u, s, v)
         assert 0 < int(info[0]) < (1 << 20), ((m, n), int(info[0]))
@@ -74,6 +78,56 @@ def test_block_ragged_shapes(bs, dt, method):
         _, so, _, _, _ = O.svd(ad)
         e = svd_errors(ad, u[0].T, s[0], v[0].T, so)
         assert max(e.values()) <= 4 * g, ((m, n), e)
+
+
+@pytest.mark.parametrize("method", [0, 1 << 16])
+def test_block_packed_uneven_batch(bs, method):
+    """One call over matrices of different shapes and odd leading dimensions (the tensor-core
+    Gram's scalar-load path and partial 32-row chunks), FP32, bw = 32."""
+    shapes = [(300, 200), (130, 257), (64, 64), (211, 97), (257, 300), (40, 190)]
+    rng = np.random.default_rng(5)
+    mats, offs, lds, o = [], [], [], 0
+    for (m, n) in shapes:
+        k = min(m, n)
+        uu, _ = np.linalg.qr(rng.standard_normal((m, k)))
+        vv, _ = np.linalg.qr(rng.standard_normal((n, k)))
+        sig = np.sort(10.0 ** rng.uniform(-4, 0, k))[::-1]
+        a64 = ((uu * sig) @ vv.T).astype(np.float32).astype(np.float64)
+        ld = m + 3                                   # not a multiple of 4
+        mats.append(a64)
+        offs.append(o)
+        lds.append(ld)
+        o += ld * n
+    flat = np.zeros(o, np.float32)
+    for a64, off, ld in zip(mats, offs, lds):
+        m, n = a64.shape
+        buf = np.zeros((n, ld), np.float32)
+        buf[:, :m] = a64.T
+        flat[off:off + ld * n] = buf.reshape(-1)
+    dev = torch.device("cuda")
+    A = bs.Batch.packed(torch.from_numpy(flat).to(dev), offs, [s[0] for s in shapes], [s[1] for s in shapes], lds)
+    ks = [min(s) for s in shapes]
+    ou = np.cumsum([0] + [m * k for (m, _), k in zip(shapes, ks)])
+    ov = np.cumsum([0] + [n * k for (_, n), k in zip(shapes, ks)])
+    oks = np.cumsum([0] + ks)
+    U = torch.zeros(int(ou[-1]), device=dev)
+    V = torch.zeros(int(ov[-1]), device=dev)
+    S = torch.zeros(int(oks[-1]), device=dev)
+    Ub = bs.Batch.packed(U, ou[:-1], [s[0] for s in shapes], ks)
+    Vb = bs.Batch.packed(V, ov[:-1], [s[1] for s in shapes], ks)
+    Sb = bs.Batch.packed(S, oks[:-1], ks, [1] * len(ks))
+    info = torch.zeros(len(shapes), dtype=torch.int32, device=dev)
+    ws = torch.empty(bs.batched_svd_block_jacobi_workspace(A, 32, method), dtype=torch.uint8, device=dev)
+    bs.batched_svd_block_jacobi(A, Sb, Ub, Vb, info, ws, block_width=32, method=method, max_sweeps=30)
+    torch.cuda.synchronize()
+    Uh, Vh, Sh = (t.cpu().numpy().astype(np.float64) for t in (U, V, S))
+    for i, ((m, n), k) in enumerate(zip(shapes, ks)):
+        assert 0 < int(info[i]) < (1 << 20), (i, int(info[i]))
+        u = Uh[ou[i]:ou[i + 1]].reshape(k, m).T
+        v = Vh[ov[i]:ov[i + 1]].reshape(k, n).T
+        _, so, _, _, _ = O.svd(mats[i])
+        e = svd_errors(mats[i], u, Sh[oks[i]:oks[i + 1]], v, so)
+        assert max(e.values()) <= 1e-5, ((m, n), e)
 
 
 def test_block_matches_register_tier_on_64x64(bs):
