@@ -329,13 +329,15 @@ class Block512:
 
     def __init__(self, args):
         self.args = args
-        self.nb = 500
+        self.nb = args.block_batch
 
     def config(self, world):
-        return {"workload": "block512: block-Jacobi SVD (U,S,V) of 500 FP32 512x512 per GPU per step, GRAM "
+        return {"workload": f"block512: block-Jacobi SVD (U,S,V) of {self.nb} FP32 512x512 per GPU per step, GRAM "
                             "method, block width 32, pair Gram products on the tensor cores (TF32 hi/lo split, "
                             "FP32 accumulation), updates on FP32 SIMT; sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
-                "l2": "inputs (524 MB per GPU) larger than L2", "parallelism": f"independent batches per GPU x{world}"}
+                "l2": f"inputs ({self.nb * 512 * 512 * 4 / 1e6:.0f} MB per GPU) "
+                      f"{'larger' if self.nb * 512 * 512 * 4 > 129e6 else 'smaller'} than L2",
+                "parallelism": f"independent batches per GPU x{world}"}
 
     def setup(self, rank, dev):
         import torch
@@ -736,6 +738,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="svd64_qr128")
     ap.add_argument("--svd-batch", type=int, default=20000)
     ap.add_argument("--qr-batch", type=int, default=20000)
+    ap.add_argument("--block-batch", type=int, default=500, help="block512: matrices per GPU")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -580,38 +580,51 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
     const bool vec = (ldw & 3) == 0 && (reinterpret_cast<uintptr_t>(W) & 15) == 0;
     const int nch = (mm + kTcGramKc - 1) / kTcGramKc;
     constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
+    constexpr int kUnits = (K2 * kTcGramKc / 4) / 128;  // float4 units per thread per chunk
+    // unit j of this thread: column i, 4-row group g (consecutive threads take consecutive columns,
+    // so eight threads write one 128-byte core matrix)
+    auto load_unit = [&](int j, int c) {
+        const int u = tid + 128 * j;
+        const int i = u & (K2 - 1), g = u / K2;
+        const int col = bj_col(bi, bj, bw, i, nn);
+        const int r = c * kTcGramKc + 4 * g;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col >= 0) {
+            const float* src = W + (size_t)col * ldw + r;
+            if (vec && r + 3 < mm) {
+                v = *reinterpret_cast<const float4*>(src);
+            } else {
+                if (r + 0 < mm) v.x = src[0];
+                if (r + 1 < mm) v.y = src[1];
+                if (r + 2 < mm) v.z = src[2];
+                if (r + 3 < mm) v.w = src[3];
+            }
+        }
+        return v;
+    };
+    float4 cur[kUnits], nxt[kUnits];
+#pragma unroll
+    for (int j = 0; j < kUnits; ++j) cur[j] = load_unit(j, 0);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
         const int s = c % kTcGramStages;
         unsigned char* stage = sm + s * kTcGramStage;
+        // the next chunk's loads are in flight while this one is split, stored and multiplied
+        if (c + 1 < nch) {
+#pragma unroll
+            for (int j = 0; j < kUnits; ++j) nxt[j] = load_unit(j, c + 1);
+        }
         if (c >= kTcGramStages) {  // the MMAs of chunk c - 3 read this stage
             if (ok) ok = tc::mbar_wait(&bars[s], (phase >> s) & 1u);  // after a failure: no more waits
             phase ^= 1u << s;
         }
-        const int r0 = c * kTcGramKc;
-        // unit (column i, 4-row group g): consecutive threads take consecutive columns, so eight
-        // threads write one 128-byte core matrix
 #pragma unroll
-        for (int j = 0; j < (K2 * kTcGramKc / 4) / 128; ++j) {
+        for (int j = 0; j < kUnits; ++j) {
             const int u = tid + 128 * j;
             const int i = u & (K2 - 1), g = u / K2;
-            const int col = bj_col(bi, bj, bw, i, nn);
-            const int r = r0 + 4 * g;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (col >= 0) {
-                const float* src = W + (size_t)col * ldw + r;
-                if (vec && r + 3 < mm) {
-                    v = *reinterpret_cast<const float4*>(src);
-                } else {
-                    if (r + 0 < mm) v.x = src[0];
-                    if (r + 1 < mm) v.y = src[1];
-                    if (r + 2 < mm) v.z = src[2];
-                    if (r + 3 < mm) v.w = src[3];
-                }
-            }
             // hi to operand rows 0..63, lo to rows 64..127 of the same stage
             tc_split_store(stage + tc::kmajor_offset(i, 4 * g, kTcLbo, kTcGramSbo),
-                           stage + tc::kmajor_offset(K2 + i, 4 * g, kTcLbo, kTcGramSbo), 0u, v);
+                           stage + tc::kmajor_offset(K2 + i, 4 * g, kTcLbo, kTcGramSbo), 0u, cur[j]);
         }
         tc::fence_smem_to_async();
         __syncthreads();
@@ -624,6 +637,10 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
                 tc::mma_tf32(tmem, d, d, idesc, (c > 0 || kk > 0) ? 1u : 0u);
             }
             tc::mma_commit(&bars[s]);
+        }
+        if (c + 1 < nch) {
+#pragma unroll
+            for (int j = 0; j < kUnits; ++j) cur[j] = nxt[j];
         }
     }
     // drain: the last (up to three) chunks' commits, one per barrier
@@ -927,7 +944,12 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
         if (cudaFuncSetAttribute(bj_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcGramSmem) !=
             cudaSuccess)
             return BSVD_ERR_CUDA;
-        g_gram_tc = persistent_grid(bj_gram_tc_kernel, 128, kTcGramSmem, items);
+        // four CTAs per SM: what shared memory admits, and 4 x 128 = 512 TMEM columns (the
+        // occupancy query undercounts this kernel, so the grid is set from the two limits)
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_gram_tc = items < 4 * sms ? items : 4 * sms;
     }
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int step = 0; step < nbp - 1; ++step) {
