@@ -397,93 +397,141 @@ __global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLay
 //   GRAM  : src = dst = [W_i W_j] (in place, row tiles), X = accumulated rotation of G
 //   DIRECT: src = Q (packed), X = U_R with columns scaled by S_R, dst = [W_i W_j]
 //   V     : src = dst = [V_i V_j], X = accumulated rotation (GRAM) or V_R (DIRECT)
-// grid: (items, row tiles of W + row tiles of V)
+// A CTA takes a 128-row tile: the source tile is staged k-major (row index contiguous, straight
+// from the column-major matrix), the multiplier once per tile, and each of the 256 threads
+// accumulates a 4-row x (2bw / 8)-column block in registers (one 4-wide and two (2bw/16)-wide
+// shared loads per 4 x 2bw/8 FMAs).
 // ------------------------------------------------------------------------------------------------
-template <typename T>
-constexpr int bj_rows_per_tile() { return sizeof(T) == 4 ? 32 : 16; }
+constexpr int kUpdRows = 128;
+
+// V consecutive shared-memory values starting at a 16-byte aligned address, in 16-byte loads
+template <typename T, int V>
+__device__ __forceinline__ void ld_shared_vec(const T* p, T (&v)[V])
+{
+    static_assert((V * sizeof(T)) % 16 == 0, "whole 16-byte vectors");
+    if constexpr (sizeof(T) == 8) {
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int i = 0; i < V / 2; ++i) {
+            const double2 x = q[i];
+            v[2 * i] = x.x;
+            v[2 * i + 1] = x.y;
+        }
+    } else {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const float4 x = q[i];
+            v[4 * i] = x.x;
+            v[4 * i + 1] = x.y;
+            v[4 * i + 2] = x.z;
+            v[4 * i + 3] = x.w;
+        }
+    }
+}
+
+template <int K2>
+constexpr int bj_upd_cols() { return K2 / 8; }  // output columns per thread
+
+template <typename T, int K2>
+constexpr size_t bj_update_smem()
+{
+    return sizeof(T) * ((size_t)K2 * (kUpdRows + 4) + (size_t)K2 * K2);
+}
 
 template <typename T, int K2>
 __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int step, int bw, int direct, T* const* U,
                                                const int* LDU, T* const* V, const int* LDV, const int* M,
-                                               const int* N, unsigned char* ws, const BjLayout& L)
+                                               const int* N, unsigned char* ws, const BjLayout& L,
+                                               unsigned char* upd_sm)
 {
-    constexpr int RT = bj_rows_per_tile<T>();
-    constexpr int TPO = (RT * K2) / 256;    // outputs per thread
-    __shared__ T xm[K2][K2 + 1];            // multiplier X (column-scaled for DIRECT)
-    __shared__ T ts[K2][RT + 1];            // source tile, column-major
+    constexpr int LDA = kUpdRows + 4;            // padded row length of the k-major source tile
+    constexpr int NC = bj_upd_cols<K2>();        // output columns per thread (8 for K2 = 64)
+    T* As = reinterpret_cast<T*>(upd_sm);        // As[k * LDA + r] = src(r0 + r, k)
+    T* Bs = As + (size_t)K2 * LDA;               // Bs[k * K2 + n] = multiplier(k, n)
     const int b = it / npairs, k = it - b * npairs;
-    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
-    if (in[it] == 0) return;
     BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
     const int mm = st->mm, nn = st->nn, nblk = st->nblk;
     const int nbp = nblk + (nblk & 1);
+    const int tilesW = (mm + kUpdRows - 1) / kUpdRows, tilesV = (nn + kUpdRows - 1) / kUpdRows;
+    if (tile >= tilesW + tilesV) return;
     int bi, bj;
     round_robin_pair(nbp, step, k, bi, bj);
-    const int tilesW = (mm + RT - 1) / RT, tilesV = (nn + RT - 1) / RT;
-    if (tile >= tilesW + tilesV) return;
     const bool onV = tile >= tilesW;
-    const int r0 = (onV ? tile - tilesW : tile) * RT;
+    const int r0 = (onV ? tile - tilesW : tile) * kUpdRows;
     const int rows = onV ? nn : mm;
     const bool tr = M[b] < N[b];
     T* dstM = onV ? (tr ? U[b] : V[b]) : (tr ? V[b] : U[b]);
     const int ldd = onV ? (tr ? LDU[b] : LDV[b]) : (tr ? LDV[b] : LDU[b]);
     // multiplier: the inner SVD's right factor X (GRAM: eigenvectors of G; DIRECT: V_R), or, for
-    // the W tile of DIRECT, U_R diag(S_R)
+    // the W tile of DIRECT, U_R diag(S_R); column-major K2 x K2, staged row-major (k, n)
     const T* Xv = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
     const T* URv = reinterpret_cast<T* const*>(ws + L.off_pUR)[it];
     const T* Sv = reinterpret_cast<T* const*>(ws + L.off_pS)[it];
     const bool useUR = direct && !onV;
-    for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) {
-        const int c = e / K2, r = e % K2;
-        xm[c][r] = useUR ? URv[e] * Sv[c] : Xv[e];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < K2 * K2; e += 256) {
+        const int n = e / K2, kk = e - n * K2;  // consecutive threads: consecutive k of column n
+        Bs[kk * K2 + n] = useUR ? URv[e] * Sv[n] : Xv[e];
     }
-    // source tile
+    // source tile, k-major: column kk of the pair (or of the packed Q), rows r0 .. r0 + 127
     const T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
-    for (int e = threadIdx.x; e < K2 * RT; e += blockDim.x) {
-        const int c = e / RT, r = e % RT;
+    const int ldp = mm > K2 ? mm : K2;
+    for (int e = tid; e < K2 * kUpdRows; e += 256) {
+        const int kk = e / kUpdRows, r = e - kk * kUpdRows;
         T v = T(0);
         if (r0 + r < rows) {
             if (useUR) {
-                v = P[(size_t)c * (mm > K2 ? mm : K2) + r0 + r];
+                v = P[(size_t)kk * ldp + r0 + r];
             } else {
-                const int col = bj_col(bi, bj, bw, c, nn);
+                const int col = bj_col(bi, bj, bw, kk, nn);
                 if (col >= 0) v = dstM[(size_t)col * ldd + r0 + r];
             }
         }
-        ts[c][r] = v;
+        As[kk * LDA + r] = v;
     }
     __syncthreads();
-    const int o0 = threadIdx.x * TPO;
-    const int oc = o0 / RT, or0 = o0 % RT;  // output column oc, rows or0 .. or0 + TPO - 1
-    T acc[TPO];
+    const int tx = tid & 31, ty = tid >> 5;       // rows 4 tx .. 4 tx + 3, columns NC ty .. NC ty + NC - 1
+    T acc[4][NC];
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
-#pragma unroll 8
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[i][j] = T(0);
+#pragma unroll 2
     for (int kk = 0; kk < K2; ++kk) {
-        const T x = xm[oc][kk];
+        T a[4], bv[NC];
+        ld_shared_vec<T, 4>(As + kk * LDA + 4 * tx, a);     // 16-byte aligned: LDA * size and 4 tx
+        ld_shared_vec<T, NC>(Bs + kk * K2 + NC * ty, bv);
 #pragma unroll
-        for (int q = 0; q < TPO; ++q) acc[q] = fma(ts[kk][or0 + q], x, acc[q]);
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < NC; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
-    const int col = bj_col(bi, bj, bw, oc, nn);
-    if (col >= 0) {
 #pragma unroll
-        for (int q = 0; q < TPO; ++q)
-            if (r0 + or0 + q < rows) dstM[(size_t)col * ldd + r0 + or0 + q] = acc[q];
+    for (int j = 0; j < NC; ++j) {
+        const int col = bj_col(bi, bj, bw, NC * ty + j, nn);
+        if (col < 0) continue;
+        T* d = dstM + (size_t)col * ldd + r0 + 4 * tx;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (r0 + 4 * tx + i < rows) d[i] = acc[i][j];
     }
 }
 
 // work items are (rotating pair, row tile) flattened; `tiles` is the bound on tiles per pair
 template <typename T, int K2>
-__global__ void __launch_bounds__(256) bj_update_kernel(int tiles, int npairs, int step, int bw, int direct,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) bj_update_kernel(int tiles, int npairs, int step, int bw, int direct,
                                                         T* const* U, const int* LDU, T* const* V, const int* LDV,
                                                         const int* M, const int* N, unsigned char* ws, BjLayout L)
 {
+    extern __shared__ __align__(16) unsigned char upd_sm[];
     BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
     const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
     const long long total = (long long)C->pcount * tiles;
     for (long long w = next_work(&C->claim[3]); w < total; w = next_work(&C->claim[3])) {
         const long long j = w / tiles;
-        bj_update_item<T, K2>(plist[j], (int)(w - j * tiles), npairs, step, bw, direct, U, LDU, V, LDV, M, N, ws, L);
+        bj_update_item<T, K2>(plist[j], (int)(w - j * tiles), npairs, step, bw, direct, U, LDU, V, LDV, M, N, ws, L,
+                              upd_sm);
     }
 }
 
@@ -924,8 +972,11 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     const int* ild = reinterpret_cast<const int*>(ws + L.off_ld);  // 2bw for every item
     const int* ildp = reinterpret_cast<const int*>(ws + L.off_ldp);
     int* iinfo = reinterpret_cast<int*>(ws + L.off_info);
-    constexpr int RT = bj_rows_per_tile<T>();
-    const int tiles = (mm + RT - 1) / RT + (nn + RT - 1) / RT;
+    const int tiles = (mm + kUpdRows - 1) / kUpdRows + (nn + kUpdRows - 1) / kUpdRows;
+    constexpr size_t upd_smem = bj_update_smem<T, K2>();
+    if (upd_smem > 48 * 1024 && cudaFuncSetAttribute(bj_update_kernel<T, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)upd_smem) != cudaSuccess)
+        return BSVD_ERR_CUDA;
     const int sweeps = max_sweeps > 0 ? max_sweeps : 20;
     const size_t polish_smem = 2 * sizeof(T) * K2 * (K2 + 1);
     if (polish_smem > 48 * 1024 && cudaFuncSetAttribute(bj_polish_kernel<T, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -936,7 +987,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     const int g_gram = persistent_grid(bj_gram_kernel<T, K2>, 256, 0, items);
     const int g_pack = persistent_grid(bj_pack_kernel<T, K2>, 256, 0, items);
     const int g_polish = persistent_grid(bj_polish_kernel<T, K2>, 256, polish_smem, items);
-    const int g_update = persistent_grid(bj_update_kernel<T, K2>, 256, 0, (long long)items * tiles);
+    const int g_update = persistent_grid(bj_update_kernel<T, K2>, 256, upd_smem, (long long)items * tiles);
     // tensor-core Gram (FP32 data, bw = 32)
     const bool tc_gram = sizeof(T) == 4 && K2 == 64 && !simt;
     int g_gram_tc = 1;
@@ -977,8 +1028,8 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                 if (rc != BSVD_SUCCESS) return rc;
             }
             bj_polish_kernel<T, K2><<<g_polish, 256, polish_smem, st>>>(ws, L);
-            bj_update_kernel<T, K2><<<g_update, 256, 0, st>>>(tiles, npairs, step, bw, direct ? 1 : 0, (T* const*)U,
-                                                              LDU, (T* const*)V, LDV, M, N, ws, L);
+            bj_update_kernel<T, K2><<<g_update, 256, upd_smem, st>>>(tiles, npairs, step, bw, direct ? 1 : 0,
+                                                                     (T* const*)U, LDU, (T* const*)V, LDV, M, N, ws, L);
             if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
         }
         if (cudaMemsetAsync(&ctr->mcount, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
