@@ -125,14 +125,27 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def jacobi_flops(m, n, info, rots):
+def jacobi_flops(m, n, info, rots, precond=False):
     """Algorithmic flops of one-sided Jacobi: every visited pair costs its 2x2 Gram (6 max(m,n)),
-    every applied rotation 6(m + n) (A and V columns); sweeps = info (or info - NOT_CONVERGED)."""
+    every applied rotation 6(m + n) (A and V columns); sweeps = info (or info - NOT_CONVERGED).
+    QR-preconditioned (square): plus the Householder factorisation 4n^3/3 and its application to
+    the accumulated rotations 2n^3, per matrix."""
     info = np.asarray(info)
     sweeps = np.where(info >= (1 << 20), info - (1 << 20), info).astype(np.float64)
     k = min(m, n)
     mm = max(m, n)
-    return float(np.sum(sweeps * (k * (k - 1) / 2) * 6 * mm + np.asarray(rots, np.float64) * 6 * (m + n)))
+    fl = float(np.sum(sweeps * (k * (k - 1) / 2) * 6 * mm + np.asarray(rots, np.float64) * 6 * (m + n)))
+    if precond:
+        fl += len(info) * (4.0 * n ** 3 / 3 + 2.0 * n ** 3)
+    return fl
+
+
+def tier_precond(bs, code, m, n, tier):
+    """True when the encoded register tier is a QR-preconditioned variant."""
+    if (tier & 0xff) != bs.TIER_REGISTER:
+        return False
+    k = tier >> 8 or 1
+    return bool(bs.jacobi_variant_desc(code, m, n, k)["qr_precond"])
 
 
 def max_over_ranks(x, world, dev):
@@ -210,7 +223,8 @@ class SvdQr64:
         bs = self.bs
         info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
         assert np.all(info_h > 0), "Jacobi reported a bad shape"
-        fl = jacobi_flops(64, 64, info_h, rots_h)
+        pre = tier_precond(bs, bs.F32, 64, 64, int(self.tuned["tier"]))
+        fl = jacobi_flops(64, 64, info_h, rots_h, pre)
         achieved = fl / (kernel_ms * 1e-3) / 1e12
         tier = int(self.tuned["tier"])
         reg = (tier & 0xff) == bs.TIER_REGISTER
@@ -296,7 +310,8 @@ class Fp64_32:
 
     def roofline(self, kernel_ms):
         info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
-        fl = jacobi_flops(32, 32, info_h, rots_h)
+        pre = tier_precond(self.bs, self.bs.F64, 32, 32, int(self.tuned["tier"]))
+        fl = jacobi_flops(32, 32, info_h, rots_h, pre)
         achieved = fl / (kernel_ms * 1e-3) / 1e12
         return ({"kernel": f"jacobi_reg_kernel<double> (tier {int(self.tuned['tier']):#x})", "bound": "alu",
                  "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

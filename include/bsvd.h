@@ -122,6 +122,17 @@ int batched_svd_jacobi(int dtype, int batch, int max_m, int max_n,
 int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier);
 
 /*
+ * bsvd_jacobi_variant_desc -- describe the k-th (k >= 1) register-tier variant that fits a batch
+ * bounded by max_m x max_n (the variant BSVD_TIER_REGISTER | (k << 8) launches).  desc (HOST, 7
+ * ints, caller-owned) receives {column-pair slots, row parts, rows of A per lane, rows of V per
+ * lane, resident CTAs per SM, scaled rotations (0/1), QR preconditioning (0/1)}.  QR
+ * preconditioning (square bounds only) factors A = Q R and runs the sweeps on R^T (the project's
+ * addition; the paper runs them on A).  Returns 0, a negative argument code, or
+ * BSVD_ERR_UNSUPPORTED when there is no k-th variant.  Host only; launches nothing.
+ */
+int bsvd_jacobi_variant_desc(int dtype, int max_m, int max_n, int k, int* desc);
+
+/*
  * bsvd_set_jacobi_choice -- record the encoded tier (tier | variant << 8) that BSVD_TIER_AUTO
  * uses for batches whose bounds fall in the same size bin as max_m x max_n (bins are powers of
  * two of max(m, n) and min(m, n), up to 256).  BSVD_TIER_AUTO clears the entry.  Host only, not

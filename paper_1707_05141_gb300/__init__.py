@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
             L.batched_svd_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, p, p, p]
             L.bsvd_jacobi_variants.restype = i
             L.bsvd_jacobi_variants.argtypes = [i, i, i, i]
+            L.bsvd_jacobi_variant_desc.restype = i
+            L.bsvd_jacobi_variant_desc.argtypes = [i, i, i, i, p]
             L.bsvd_set_jacobi_choice.restype = i
             L.bsvd_set_jacobi_choice.argtypes = [i, i, i, i]
             L.batched_svd_block_jacobi_workspace.restype = ctypes.c_size_t
@@ -99,6 +101,13 @@ def version() -> str:
 def jacobi_variants(dtype_code: int, max_m: int, max_n: int, tier: int) -> int:
     """Number of kernel variants of ``tier`` able to run a max_m x max_n batch."""
     return lib().bsvd_jacobi_variants(dtype_code, max_m, max_n, tier)
+
+
+def jacobi_variant_desc(dtype_code: int, max_m: int, max_n: int, k: int) -> dict:
+    """Shape parameters of the k-th (k >= 1) register-tier variant fitting max_m x max_n."""
+    d = (ctypes.c_int * 7)()
+    _check("bsvd_jacobi_variant_desc", lib().bsvd_jacobi_variant_desc(dtype_code, max_m, max_n, k, d))
+    return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond"), list(d)))
 
 
 def set_jacobi_choice(dtype_code: int, max_m: int, max_n: int, tier: int) -> None:

@@ -107,6 +107,16 @@ int batched_svd_jacobi(int dtype, int batch, int max_m, int max_n, void* const* 
                                                     d_ldv, tol, max_sweeps, d_info, d_rotations, st);
 }
 
+int bsvd_jacobi_variant_desc(int dtype, int max_m, int max_n, int k, int* desc)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (max_m < 0) return -2;
+    if (max_n < 0) return -3;
+    if (k < 1) return -4;
+    if (!desc) return -5;
+    return jacobi_reg_variant_desc(dtype == BSVD_F64, max_m, max_n, k, desc);
+}
+
 int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier)
 {
     if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;

@@ -19,6 +19,7 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
                       const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,
                       double tol, int max_sweeps, int* info, long long* rot, cudaStream_t st,
                       ItemList wl = all_items());
+int jacobi_reg_variant_desc(bool f64, int max_m, int max_n, int k, int* desc);
 template <typename T>
 int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "house.cuh"
 #include "launch.cuh"
 
 namespace bsvd {
@@ -47,34 +48,7 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         __syncthreads();
 
         // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
-        for (int i = 0; i < n; ++i) {
-            T* col = S + i * ld;
-            if (warp == 0) {
-                const T x0 = col[i];  // read by every lane before the shuffles below
-                T ss = T(0);
-                for (int r = i + lane; r < m; r += 32) ss += col[r] * col[r];
-                ss = warp_sum(ss);
-                const T alpha = dsqrt(ss);
-                if (alpha > T(0)) {
-                    const T sg = x0 >= T(0) ? T(1) : T(-1);
-                    // ||x + sign(x0) alpha e1||^2 = 2 alpha (alpha + |x0|)
-                    const T inv = drsqrt(T(2) * alpha * (alpha + dabs(x0)));
-                    for (int r = i + lane; r < m; r += 32) col[r] = (r == i ? x0 + sg * alpha : col[r]) * inv;
-                    if (lane == 0) diag[i] = -sg * alpha;
-                } else if (lane == 0) {
-                    diag[i] = T(0);  // zero column: v = 0 (already zero), identity reflector
-                }
-            }
-            __syncthreads();
-            for (int j = i + 1 + warp; j < n; j += nwarps) {
-                T* cj = S + j * ld;
-                T w = T(0);
-                for (int r = i + lane; r < m; r += 32) w += col[r] * cj[r];
-                w = T(2) * warp_sum(w);
-                for (int r = i + lane; r < m; r += 32) cj[r] -= w * col[r];
-            }
-            __syncthreads();
-        }
+        house_factor_smem(S, ld, diag, m, n);
 
         // ---- R: strict upper part from S, diagonal from diag, zeros below ----
         if (R) {

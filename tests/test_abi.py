@@ -78,3 +78,27 @@ def test_variant_counts_and_tuning_table(lib):
     assert L.bsvd_set_jacobi_choice(0, 64, 64, bs.TIER_AUTO) == 0
     assert L.bsvd_set_jacobi_choice(0, 512, 64, bs.TIER_AUTO) == -2
     assert L.bsvd_set_jacobi_choice(0, 64, 64, 7) == -4
+
+
+def test_variant_descriptions(lib):
+    """The k-th fitting register variant's shape; QR preconditioning only for square bounds, and
+    listed after every unpreconditioned variant (so variant 0 -- the first -- never has it)."""
+    _, bs = lib
+    L = bs.lib()
+    for code, (m, n) in [(0, (64, 64)), (0, (32, 32)), (1, (32, 32)), (1, (64, 64)), (0, (128, 48)), (1, (64, 60))]:
+        nv = L.bsvd_jacobi_variants(code, m, n, bs.TIER_REGISTER)
+        descs = [bs.jacobi_variant_desc(code, m, n, k) for k in range(1, nv + 1)]
+        pre = [d["qr_precond"] for d in descs]
+        assert pre == sorted(pre), (code, m, n, pre)             # preconditioned ones last
+        assert any(pre) == (m == n), (code, m, n, pre)
+        for d in descs:                                          # every one fits the bounds
+            assert min(m, n) <= 2 * d["slots"] and max(m, n) <= d["parts"] * d["rows_a"]
+            assert min(m, n) <= d["parts"] * d["rows_v"]
+        with pytest.raises(bs.BsvdError):
+            bs.jacobi_variant_desc(code, m, n, nv + 1)
+    import ctypes
+    d = (ctypes.c_int * 7)()
+    assert L.bsvd_jacobi_variant_desc(2, 64, 64, 1, d) == -1
+    assert L.bsvd_jacobi_variant_desc(0, -1, 64, 1, d) == -2
+    assert L.bsvd_jacobi_variant_desc(0, 64, 64, 0, d) == -4
+    assert L.bsvd_jacobi_variant_desc(0, 64, 64, 1, None) == -5

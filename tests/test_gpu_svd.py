@@ -189,7 +189,7 @@ def _variant_cases():
     import paper_1707_05141_gb300 as bsm
     cases = []
     for dt, (m, n) in [(np.float32, (64, 64)), (np.float32, (32, 32)), (np.float32, (128, 48)),
-                       (np.float32, (40, 100)), (np.float64, (32, 32)), (np.float64, (64, 60)),
+                       (np.float32, (40, 100)), (np.float64, (32, 32)), (np.float64, (64, 64)), (np.float64, (64, 60)),
                        (np.float64, (20, 50))]:
         code = 0 if dt == np.float32 else 1
         nv = bsm.jacobi_variants(code, m, n, bsm.TIER_REGISTER) if os.path.exists(bsm.LIB) else 0
