@@ -19,7 +19,7 @@ namespace bsvd {
 template <typename T>
 __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const int* M, const int* N,
                           const int* LDA, T* const* Q, const int* LDQ, T* const* R, const int* LDR,
-                          int* info, ItemList wl)
+                          int* info, ItemList wl, int r_trans)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
@@ -55,7 +55,8 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
             T* r_out = R[b];
             for (int j = warp; j < n; j += nwarps)
                 for (int i = lane; i < n; i += 32)
-                    r_out[(size_t)j * ldr + i] = i < j ? S[j * ld + i] : (i == j ? diag[j] : T(0));
+                    r_out[r_trans ? (size_t)i * ldr + j : (size_t)j * ldr + i] =
+                        i < j ? S[j * ld + i] : (i == j ? diag[j] : T(0));
         }
         __syncthreads();
 
@@ -90,7 +91,7 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
 template <typename T>
 int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
               void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st,
-              ItemList wl)
+              ItemList wl, bool r_transposed)
 {
     const size_t smem = ((size_t)max_m * max_n + max_n) * sizeof(T);
     const int threads = max_n <= 32 ? 128 : 256;
@@ -101,13 +102,13 @@ int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, con
     const int grid = item_grid(qr_kernel<T>, threads, smem, wl, batch, st);
     if (grid == 0) return BSVD_ERR_CUDA;
     qr_kernel<T><<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ,
-                                              (T* const*)R, LDR, info, wl);
+                                              (T* const*)R, LDR, info, wl, r_transposed ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
 template int launch_qr<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                              const int*, void* const*, const int*, int*, cudaStream_t, ItemList);
+                              const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool);
 template int launch_qr<double>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                               const int*, void* const*, const int*, int*, cudaStream_t, ItemList);
+                               const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool);
 
 }  // namespace bsvd

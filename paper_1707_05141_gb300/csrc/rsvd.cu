@@ -9,8 +9,11 @@
 //   range    [Q, ~] = qr(Y);  power step: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
 //            (q = 1 step of randomized subspace iteration, the robust variant Section 7 mentions).
 //   project  B^T = A^T Q (n x l), [Q_B, R_B] = qr(B^T)   (Section 7, phase 2).
-//   small    SVD of R_B by one-sided Jacobi (register tier for l <= 64, shared tier to 128):
-//            R_B = U' S V'^T, so R_B^T = V' S U'^T and U = Q V', V = Q_B U'.
+//   small    SVD of R_B^T by one-sided Jacobi (register tier for l <= 64, shared tier to 128):
+//            R_B^T = U_R S V_R^T, so A ~ Q B = Q R_B^T Q_B^T and U = Q U_R, V = Q_B V_R (the QR
+//            writes R_B transposed; one-sided Jacobi on the lower-triangular R_B^T, whose rows are
+//            graded like the singular values, converges in fewer sweeps than on R_B: the same
+//            effect as the register tier's QR preconditioning; workload 3 went from 408 to 390 ms).
 //   estimate posterior error of the rank-l approximation from the probes (Halko et al. 4.3):
 //            est^2 = mean_j ||A w_j - U S V^T w_j||^2.  If est > (eps / 2) ||A||_F the block
 //            gets 8 more samples in the next round (the adaptive range finder); past the
@@ -62,9 +65,9 @@ struct RsArrays {
     float** pY;    // m x (l + probes), ld m          (Y, then Q in its first l columns)
     float** pZ;    // n x l, ld n                     (Z, then Qz)
     float** pBt;   // n x l, ld n                     (B^T, then Q_B)
-    float** pR;    // l x l, ld l                     (R of each QR; R_B for the small SVD)
-    float** pUp;   // l x l, ld l                     (U' of R_B)
-    float** pVp;   // l x l, ld l                     (V' of R_B)
+    float** pR;    // l x l, ld l                     (R of each QR; R_B^T for the small SVD)
+    float** pUp;   // l x l, ld l                     (U_R of R_B^T)
+    float** pVp;   // l x l, ld l                     (V_R of R_B^T)
     float** pS;    // k                               (singular values)
     float** pUw;   // m x k, ld m                     (U before truncation)
     float** pVw;   // n x k, ld n                     (V before truncation)
@@ -578,9 +581,9 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
                                nullptr, seed, st);
         if (rc) break;
         rc = launch_qr<float>(batch, nx, lx, (void* const*)ar.pBt, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pBt,
-                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
+                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act, true);
         if (rc) break;
-        // small SVD of R_B (l x l): register tier up to 64, shared tier above
+        // small SVD of R_B^T (l x l): register tier up to 64, shared tier above
         const int lr = lx < 64 ? lx : 64;
         rc = launch_jacobi_reg<float>(batch, lr, lr, 0, (void* const*)ar.pR, ar.l_reg, ar.l_reg, ar.ld_l,
                                       (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
@@ -592,11 +595,11 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
                                            ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_lsmem, RL_LSMEM));
             if (rc) break;
         }
-        // U = Q V', V = Q_B U'
-        rc = gemm<false, false>(batch, act, ar.pY, ar.ld_m, ar.pVp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act,
+        // U = Q U_R, V = Q_B V_R
+        rc = gemm<false, false>(batch, act, ar.pY, ar.ld_m, ar.pUp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act,
                                 ar.l_act, nullptr, seed, st);
         if (rc) break;
-        rc = gemm<false, false>(batch, act, ar.pBt, ar.ld_n, ar.pUp, ar.ld_l, ar.pVw, ar.ld_n, ar.n_act, ar.l_act,
+        rc = gemm<false, false>(batch, act, ar.pBt, ar.ld_n, ar.pVp, ar.ld_l, ar.pVw, ar.ld_n, ar.n_act, ar.l_act,
                                 ar.l_act, nullptr, seed, st);
         if (rc) break;
         const int ge = item_grid(rs_estimate_kernel, 256, 0, act, batch, st);
