@@ -54,8 +54,9 @@ def measured_hbm_gbs() -> float:
 # sources at capture time; a changed kernel has no entry (traffic null).  profiles/ holds the
 # capture summaries.
 TRAFFIC = {
-    # jacobi_reg_kernel, 64x64 FP32 tier 0x101: 441.9 MB for 10 000 matrices, scaled to 20 000
-    "jacobi_reg:529d842f827b78e0": 883.8e6,
+    # jacobi_reg_kernel, 64x64 FP32, QR-preconditioned variant (tier 0x601): 440.9 MB for 10 000
+    # matrices, scaled to 20 000
+    "jacobi_reg:324d9b169c8f96bf": 881.8e6,
 }
 
 

@@ -995,12 +995,21 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
         if (cudaFuncSetAttribute(bj_gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcGramSmem) !=
             cudaSuccess)
             return BSVD_ERR_CUDA;
-        // four CTAs per SM: what shared memory admits, and 4 x 128 = 512 TMEM columns (the
-        // occupancy query undercounts this kernel, so the grid is set from the two limits)
-        int dev = 0, sms = 1;
+        // resident CTAs per SM from the kernel's registers and shared memory (at most four:
+        // 4 x 128 = 512 TMEM columns, so tcgen05.alloc never waits); the occupancy query reports
+        // one for any kernel that allocates tensor memory, so the grid is set from these limits
+        int dev = 0, sms = 1, regs_sm = 65536, smem_sm = 228 * 1024;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_gram_tc = items < 4 * sms ? items : 4 * sms;
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, bj_gram_tc_kernel) != cudaSuccess) return BSVD_ERR_CUDA;
+        const int by_regs = regs_sm / ((fa.numRegs > 0 ? fa.numRegs : 255) * 128);
+        const int by_smem = smem_sm / (int)(kTcGramSmem + fa.sharedSizeBytes + 1024);
+        int per = by_regs < by_smem ? by_regs : by_smem;
+        per = per < 1 ? 1 : (per > 4 ? 4 : per);
+        g_gram_tc = items < per * sms ? items : per * sms;
     }
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int step = 0; step < nbp - 1; ++step) {
