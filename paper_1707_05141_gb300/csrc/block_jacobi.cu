@@ -946,10 +946,28 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                      int max_sweeps, int method, int* info, long long* rot, unsigned char* ws, cudaStream_t st)
 {
     const int bw = K2 / 2;
-    const int inner_variant = (method >> 8) & 0xff;  // register-tier variant of the inner SVD (0: first fitting)
+    int inner_variant = (method >> 8) & 0xff;  // register-tier variant of the inner SVD (0: see below)
     const bool simt = (method & BSVD_BLOCK_SIMT_PRODUCTS) != 0;
     method &= 0xff;
     const bool direct = method != 0;
+    // GRAM's inner SVD by default runs the QR-preconditioned register variant and takes X from
+    // its U = Q V_w (orthogonal by construction, also for the zero singular values of padding
+    // columns; for the symmetric positive semidefinite G the left singular vectors are its
+    // eigenvectors): fewer sweeps than the plain variant on A = G.  DIRECT needs both factors of
+    // the SVD of R and keeps the first plain variant.
+    bool inner_u = false;
+    if (!direct && inner_variant == 0) {
+        int d[7];
+        for (int k = 1; jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, k, d) == BSVD_SUCCESS; ++k)
+            if (d[6]) {
+                inner_variant = k;
+                inner_u = true;
+                break;
+            }
+    } else if (!direct) {
+        int d[7];
+        inner_u = jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, inner_variant, d) == BSVD_SUCCESS && d[6];
+    }
     const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
     const int npairs = L.npairs, nbp = 2 * npairs;
@@ -1021,8 +1039,9 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                 bj_gram_kernel<T, K2><<<g_gram, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU,
                                                               (T* const*)V, LDV, M, N, ws, L, tol_outer);
             if (!direct) {
-                const int rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, im, in, ild, pS, nullptr, nullptr,
-                                                    pX, ild, 0.0, 0, iinfo, nullptr, st,
+                const int rc = launch_jacobi_reg<T>(items, K2, K2, inner_variant, pG, im, in, ild, pS,
+                                                    inner_u ? pX : nullptr, ild, inner_u ? nullptr : pX, ild, 0.0,
+                                                    0, iinfo, nullptr, st,
                                                     ItemList{pairs.idx, pairs.count, &ctr->claim[5]});
                 if (rc != BSVD_SUCCESS) return rc;
             } else {
