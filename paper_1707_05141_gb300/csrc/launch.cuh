@@ -13,7 +13,8 @@ namespace bsvd {
 template <typename T>
 int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
               void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st,
-              ItemList wl = all_items(), bool r_transposed = false);  // r_transposed: R^T written to R
+              ItemList wl = all_items(), bool r_transposed = false,  // r_transposed: R^T written to R
+              const int* a_trans = nullptr);  // a_trans[b] != 0: factor A^T (stored n x m, ld LDA)
 template <typename T>
 int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const* A, const int* M, const int* N,
                       const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV,

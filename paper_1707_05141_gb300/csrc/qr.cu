@@ -19,11 +19,11 @@ namespace bsvd {
 template <typename T>
 __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const int* M, const int* N,
                           const int* LDA, T* const* Q, const int* LDQ, T* const* R, const int* LDR,
-                          int* info, ItemList wl, int r_trans)
+                          int* info, ItemList wl, int r_trans, const int* a_trans)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
-    const int ld = max_m;
+    const int ld = max_m | 1;  // odd: the transposed load's stores spread over the banks
     T* diag = S + (size_t)ld * max_n;
 
     const int tid = threadIdx.x;
@@ -33,8 +33,9 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
 
     for (int b = item_first(wl, batch); b >= 0; b = item_next(wl, batch, b)) {
         const int m = M[b], n = N[b], lda = LDA[b];
+        const bool at = a_trans && a_trans[b];  // factor A^T: the stored matrix is n x m, ld lda
         const int ldq = Q ? LDQ[b] : m, ldr = R ? LDR[b] : n;
-        const bool bad = m < 0 || n < 0 || m < n || m > max_m || n > max_n || lda < (m > 1 ? m : 1) ||
+        const bool bad = m < 0 || n < 0 || m < n || m > max_m || n > max_n || lda < ((at ? n : m) > 1 ? (at ? n : m) : 1) ||
                          (Q && ldq < (m > 1 ? m : 1)) || (R && ldr < (n > 1 ? n : 1));
         if (bad) {
             if (tid == 0) info[b] = BSVD_INFO_BAD_SHAPE;
@@ -43,8 +44,14 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         if (tid == 0) info[b] = 0;
         if (n == 0) continue;
         const T* a = A[b];
-        for (int j = warp; j < n; j += nwarps)
-            for (int i = lane; i < m; i += 32) S[j * ld + i] = a[(size_t)j * lda + i];
+        if (!at) {
+            for (int j = warp; j < n; j += nwarps)
+                for (int i = lane; i < m; i += 32) S[j * ld + i] = a[(size_t)j * lda + i];
+        } else {
+            // S(i, j) = A(j, i): row i of S is column i of the stored matrix (coalesced reads)
+            for (int i = warp; i < m; i += nwarps)
+                for (int j = lane; j < n; j += 32) S[j * ld + i] = a[(size_t)i * lda + j];
+        }
         __syncthreads();
 
         // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
@@ -91,9 +98,9 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
 template <typename T>
 int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
               void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, cudaStream_t st,
-              ItemList wl, bool r_transposed)
+              ItemList wl, bool r_transposed, const int* a_trans)
 {
-    const size_t smem = ((size_t)max_m * max_n + max_n) * sizeof(T);
+    const size_t smem = ((size_t)(max_m | 1) * max_n + max_n) * sizeof(T);
     const int threads = max_n <= 32 ? 128 : 256;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -102,13 +109,13 @@ int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, con
     const int grid = item_grid(qr_kernel<T>, threads, smem, wl, batch, st);
     if (grid == 0) return BSVD_ERR_CUDA;
     qr_kernel<T><<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ,
-                                              (T* const*)R, LDR, info, wl, r_transposed ? 1 : 0);
+                                              (T* const*)R, LDR, info, wl, r_transposed ? 1 : 0, a_trans);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
 template int launch_qr<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                              const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool);
+                              const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool, const int*);
 template int launch_qr<double>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
-                               const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool);
+                               const int*, void* const*, const int*, int*, cudaStream_t, ItemList, bool, const int*);
 
 }  // namespace bsvd

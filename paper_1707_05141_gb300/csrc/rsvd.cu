@@ -74,12 +74,18 @@ struct RsArrays {
     int *m_act, *n_act, *l_act, *lp_act;  // sizes for active randomized blocks (0 otherwise)
     int *l_reg, *l_smem;                  // l for the small SVD: register tier (l <= 64) / shared
     int *ld_m, *ld_n, *ld_l;
-    int *m_reg, *n_reg;                   // full-rank blocks for the register tier (0 otherwise)
+    int *m_reg, *n_reg;                   // full-rank blocks with min(m, n) <= 64: QR sizes max(m, n),
+                                          // min(m, n) (0 otherwise)
     int *m_smem, *n_smem;                 // ... for the shared tier
     int *m_blk, *n_blk;                   // ... for the block tier (min(m, n) > 128)
     int* info;                            // scratch info of the inner stages
+    // full-rank blocks with min(m, n) <= 64 (A = Q R, or A^T = Q R when m < n; SVD of R^T = U~ S V~^T):
+    float** pQf;   // Q (max(m,n) x min(m,n), ld max(m,n)): pY, or pBt for A^T
+    float** pCf;   // Q V~: U (pUw) for A, V (pVw) for A^T
+    float** pDf;   // U~: V (pVw) for A, U (pUw) for A^T
+    int *qtr, *ld_q;                      // factor A^T; max(m, n)
     // item lists (see ItemList) built with the arrays: blocks sampling in this round, split by
-    // the tier of their small SVD; full-rank blocks of the register and shared tiers
+    // the tier of their small SVD; full-rank blocks of the QR path and of the shared tier
     int *list_act, *list_lreg, *list_lsmem, *list_reg, *list_smem;
     int* cnt;                             // their lengths, RL_* order
     RsState* st;
@@ -316,11 +322,18 @@ __global__ void rs_arrays_kernel(int batch, float* scratch, RsArrays ar, int fin
     ar.ld_l[b] = l > 1 ? l : 1;
     const bool full = final && s.mode == RS_FULL;
     const int mm = m > n ? m : n;
-    const bool reg = full && k <= 64 && mm <= 128;
+    const bool reg = full && k <= 64;  // the QR path (max(m, n) <= 256)
     const bool blk = full && k > kLCap;
     const bool smem = full && !reg && !blk;
-    ar.m_reg[b] = reg ? m : 0;
-    ar.n_reg[b] = reg ? n : 0;
+    const bool wide = m < n;
+    ar.m_reg[b] = reg ? mm : 0;
+    ar.n_reg[b] = reg ? k : 0;
+    ar.qtr[b] = wide ? 1 : 0;
+    ar.ld_q[b] = mm > 1 ? mm : 1;
+    ar.pQf[b] = wide ? ar.pBt[b] : ar.pY[b];
+    ar.pCf[b] = wide ? ar.pVw[b] : ar.pUw[b];
+    ar.pDf[b] = wide ? ar.pUw[b] : ar.pVw[b];
+    if (reg) ar.ld_l[b] = k > 1 ? k : 1;
     ar.m_smem[b] = smem ? m : 0;
     ar.n_smem[b] = smem ? n : 0;
     ar.m_blk[b] = blk ? m : 0;
@@ -407,6 +420,17 @@ __global__ void __launch_bounds__(256) rs_estimate_kernel(ItemList wl, RsArrays 
     for (int b = list_item(wl); b >= 0; b = list_item(wl)) rs_estimate_item(b, ar, seed, eps, p);
 }
 
+// U~ (k x k, ld k) to the side the GEMM does not write (QR path of the full-rank blocks)
+__global__ void __launch_bounds__(256) rs_copy_kernel(ItemList wl, RsArrays ar)
+{
+    for (int b = list_item(wl); b >= 0; b = list_item(wl)) {
+        const int k = ar.n_reg[b];
+        const float* src = ar.pUp[b];
+        float* dst = ar.pDf[b];
+        for (int e = threadIdx.x; e < k * k; e += blockDim.x) dst[e] = src[e];
+    }
+}
+
 // blocks still sampling after the last round fall back to the full SVD
 __global__ void rs_fallback_kernel(int batch, RsState* st)
 {
@@ -483,7 +507,7 @@ struct RsFixed {
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr int kPtrArrays = 9, kIntArrays = 22;
+constexpr int kPtrArrays = 12, kIntArrays = 24;
 
 static RsFixed rs_fixed(int batch, int max_m, int max_n)
 {
@@ -528,13 +552,14 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     RsArrays ar;
     ar.st = reinterpret_cast<RsState*>(w + F.off_state);
     float** pp = reinterpret_cast<float**>(w + F.off_ptr);
-    float*** slots[kPtrArrays] = {&ar.pY, &ar.pZ, &ar.pBt, &ar.pR, &ar.pUp, &ar.pVp, &ar.pS, &ar.pUw, &ar.pVw};
+    float*** slots[kPtrArrays] = {&ar.pY, &ar.pZ, &ar.pBt, &ar.pR, &ar.pUp, &ar.pVp, &ar.pS, &ar.pUw, &ar.pVw,
+                                  &ar.pQf, &ar.pCf, &ar.pDf};
     for (int i = 0; i < kPtrArrays; ++i) *slots[i] = pp + (size_t)i * batch;
     int* ip = reinterpret_cast<int*>(w + F.off_int);
     int** islots[kIntArrays] = {&ar.m_act, &ar.n_act, &ar.l_act, &ar.lp_act, &ar.l_reg, &ar.l_smem,
                                 &ar.ld_m, &ar.ld_n, &ar.ld_l, &ar.m_reg, &ar.n_reg, &ar.m_smem,
                                 &ar.n_smem, &ar.m_blk, &ar.n_blk, &ar.info, &ar.list_act, &ar.list_lreg,
-                                &ar.list_lsmem, &ar.list_reg, &ar.list_smem, nullptr};
+                                &ar.list_lsmem, &ar.list_reg, &ar.list_smem, &ar.qtr, &ar.ld_q, nullptr};
     for (int i = 0; i < kIntArrays; ++i)
         if (islots[i]) *islots[i] = ip + (size_t)i * batch;
     float* scratch = reinterpret_cast<float*>(w + F.off_scratch);
@@ -615,12 +640,28 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     const int mm_x = mx > nx ? mx : nx;
     if (kx > 0) {
-        // bounds cover every block routed to each tier (max(m, n), min(m, n) order is what counts)
-        rc = launch_jacobi_reg<float>(batch, mm_x < 128 ? mm_x : 128, kx < 64 ? kx : 64, 0, A, ar.m_reg, ar.n_reg, LDA,
-                                      (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n,
-                                      0.0, 0, ar.info, nullptr, st, listed(ar.list_reg, RL_REG));
+        // min(m, n) <= 64: A (A^T when m < n) = Q R with R written transposed, the SVD of
+        // R^T = U~ S V~^T in the register tier (R^T: the preconditioned form), then A = (Q V~) S U~^T:
+        // the Q side by the batched GEMM, U~ copied
+        const ItemList qlist = listed(ar.list_reg, RL_REG);
+        const int kq = kx < 64 ? kx : 64;
+        rc = launch_qr<float>(batch, mm_x, kq, A, ar.m_reg, ar.n_reg, LDA, (void* const*)ar.pQf, ar.ld_q,
+                              (void* const*)ar.pR, ar.ld_l, ar.info, st, qlist, true, ar.qtr);
         if (rc) return rc;
-        if (mm_x > 128 || kx > 64) {
+        rc = launch_jacobi_reg<float>(batch, kq, kq, 0, (void* const*)ar.pR, ar.n_reg, ar.n_reg, ar.ld_l,
+                                      (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
+                                      ar.ld_l, 0.0, 0, ar.info, nullptr, st, qlist);
+        if (rc) return rc;
+        rc = gemm<false, false>(batch, qlist, ar.pQf, ar.ld_q, ar.pVp, ar.ld_l, ar.pCf, ar.ld_q, ar.m_reg, ar.n_reg,
+                                ar.n_reg, nullptr, seed, st);
+        if (rc) return rc;
+        {
+            const int gc = item_grid(rs_copy_kernel, 256, 0, qlist, batch, st);
+            if (gc == 0) return BSVD_ERR_CUDA;
+            rs_copy_kernel<<<gc, 256, 0, st>>>(qlist, ar);
+            if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+        }
+        if (kx > 64) {  // 64 < min(m, n) <= 128
             rc = launch_jacobi_smem<float>(batch, mm_x, kx < kLCap ? kx : kLCap, A, ar.m_smem, ar.n_smem, LDA,
                                            (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw,
                                            ar.ld_n, 0.0, 0, ar.info, nullptr, st, listed(ar.list_smem, RL_SMEM));
