@@ -188,8 +188,8 @@ class SvdQr64:
         import paper_1707_05141_gb300 as bs
         from paper_1707_05141_gb300 import autotune
         self.bs = bs
-        a_svd = gen.workload1_svd(batch=self.nb, first=rank * self.nb)
-        a_qr = gen.workload1_qr(batch=self.nq, first=rank * self.nq)
+        a_svd = gen.svd64_exp8(batch=self.nb, first=rank * self.nb)
+        a_qr = gen.qr128x32_exp8(batch=self.nq, first=rank * self.nq)
         self.h_in = [torch.from_numpy(a_svd.a).pin_memory(), torch.from_numpy(a_qr.a).pin_memory()]
         self.d_svd, self.d_qr = (h.to(dev) for h in self.h_in)
         m = n = k = 64
@@ -259,8 +259,8 @@ class SvdQr64:
     def cpu_sample(self, n):
         import gen
         import oracle
-        a_svd = gen.workload1_svd(batch=n)
-        a_qr = gen.workload1_qr(batch=n)
+        a_svd = gen.svd64_exp8(batch=n)
+        a_qr = gen.qr128x32_exp8(batch=n)
         cores = oracle.default_threads()
         mats, qmats = [a_svd.a64(i) for i in range(n)], [a_qr.a64(i) for i in range(n)]
         t0 = time.time()
@@ -295,7 +295,7 @@ class Fp64_32:
         import paper_1707_05141_gb300 as bs
         from paper_1707_05141_gb300 import autotune
         self.bs = bs
-        b = gen.workload0(batch=self.nb, first=rank * self.nb)
+        b = gen.fp64_32_graded(batch=self.nb, first=rank * self.nb)
         self.h_in = [torch.from_numpy(b.a).pin_memory()]
         self.d = self.h_in[0].to(dev)
         self.d_in = [self.d]
@@ -340,7 +340,7 @@ class Fp64_32:
     def cpu_sample(self, n):
         import gen
         import oracle
-        b = gen.workload0(batch=n)
+        b = gen.fp64_32_graded(batch=n)
         mats = [b.a64(i) for i in range(n)]
         cores = oracle.default_threads()
         t0 = time.time()
@@ -376,7 +376,7 @@ class Block512:
         import gen
         import paper_1707_05141_gb300 as bs
         self.bs = bs
-        b = gen.workload2(batch=self.nb, first=rank * self.nb)
+        b = gen.block512_loguniform(batch=self.nb, first=rank * self.nb)
         self.h_in = [torch.from_numpy(b.a).pin_memory()]
         self.d = self.h_in[0].to(dev)
         self.d_in = [self.d]
@@ -445,7 +445,7 @@ class Block512:
         import gen
         import oracle
         n = max(1, min(n, 16))
-        b = gen.workload2(batch=n)
+        b = gen.block512_loguniform(batch=n)
         mats = [b.a64(i) for i in range(n)]
         cores = oracle.default_threads()
         t0 = time.time()
@@ -589,7 +589,7 @@ class RsvdUneven(RsvdBase):
         import gen
         import paper_1707_05141_gb300 as bs
         self.bs = bs
-        rb = gen.workload3(batch=self.nb, first=rank * self.nb)
+        rb = gen.rsvd_uneven_blocks(batch=self.nb, first=rank * self.nb)
         self._alloc(rb, dev, rb.extra["rank_hint"])
 
     def inner(self, stream):
@@ -599,7 +599,7 @@ class RsvdUneven(RsvdBase):
 
     def cpu_sample(self, n):
         import gen
-        rb = gen.workload3(batch=max(n, 1))
+        rb = gen.rsvd_uneven_blocks(batch=max(n, 1))
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, rb.extra["rank_hint"])
         return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{cnt} blocks of the same generator, fixed-width FP64 RSVD (hint + 8 columns, one "
@@ -628,7 +628,7 @@ class HmatrixMlp(RsvdBase):
         from paper_1707_05141_gb300 import rank_mlp
         self.bs = bs
         self.rank_mlp = rank_mlp
-        tr = gen.workload4(n_points=16384, seed_index=100 + rank)
+        tr = gen.kernel_blocks_3d(n_points=16384, seed_index=100 + rank)
         ft = torch.from_numpy(tr.flat).to(dev)
         ranks, _ = rank_mlp.plain_adaptive_ranks(ft, tr.offset, tr.m, tr.n, seed=5)
         feats = rank_mlp.features(ft, tr.offset, tr.m, tr.n, seed=6)
@@ -636,7 +636,7 @@ class HmatrixMlp(RsvdBase):
         self.params, hist = rank_mlp.train(feats, ranks, steps=2000, log_every=500)
         self.train_info = {"train_blocks": tr.batch, "final_loss": hist[-1][1], "train_s": time.time() - t0}
         del ft, feats
-        rb = gen.workload4(n_points=32768, seed_index=rank)
+        rb = gen.kernel_blocks_3d(n_points=32768, seed_index=rank)
         self.nblocks = rb.batch
         self._alloc(rb, dev, None)
         self.feats = torch.empty((rb.batch, 16), device=dev)
@@ -674,7 +674,7 @@ class HmatrixMlp(RsvdBase):
 
     def cpu_sample(self, n):
         import gen
-        rb = gen.workload4(n_points=8192, seed_index=0)
+        rb = gen.kernel_blocks_3d(n_points=8192, seed_index=0)
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, None)
         return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{cnt} kernel blocks (8192-point set), FP64 RSVD with 8 columns + power step, "

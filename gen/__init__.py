@@ -175,31 +175,31 @@ def _pack(ms, ns, dtype):
 # the five workloads (sizes as stated; ``batch`` may be reduced for parity tests)
 # ----------------------------------------------------------------------------------------------
 
-def workload0(batch: int = 1000, first: int = 0) -> UniformBatch:
+def fp64_32_graded(batch: int = 1000, first: int = 0) -> UniformBatch:
     """1000 x (32 x 32) FP64, sigma_i = 10^(-8 i/31): the plain Jacobi SVD and QR batch."""
     s = sigma_fp64_32()
     return uniform_batch(0, batch, 32, 32, np.float64, lambda i: s, first=first)
 
 
-def workload1_svd(batch: int = 20000, first: int = 0) -> UniformBatch:
+def svd64_exp8(batch: int = 20000, first: int = 0) -> UniformBatch:
     """20000 x (64 x 64) FP32, sigma_i = exp(-i/8)."""
     s = sigma_exp8(64)
     return uniform_batch(1, batch, 64, 64, np.float32, lambda i: s, first=first)
 
 
-def workload1_qr(batch: int = 20000, first: int = 0) -> UniformBatch:
+def qr128x32_exp8(batch: int = 20000, first: int = 0) -> UniformBatch:
     """20000 x (128 x 32) FP32, sigma_i = exp(-i/8), i = 0..31 (QR batch)."""
     s = sigma_exp8(32)
     return uniform_batch(101, batch, 128, 32, np.float32, lambda i: s, first=first)
 
 
-def workload2(batch: int = 500, first: int = 0, size: int = 512) -> UniformBatch:
+def block512_loguniform(batch: int = 500, first: int = 0, size: int = 512) -> UniformBatch:
     """500 x (512 x 512) FP32, sigma iid log-uniform on [1e-6, 1]."""
     return uniform_batch(2, batch, size, size, np.float32,
                          lambda i: sigma_loguniform(2, i, size), first=first, chunk=16)
 
 
-def workload3(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: float = 1e-5) -> RaggedBatch:
+def rsvd_uneven_blocks(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: float = 1e-5) -> RaggedBatch:
     """Uneven blocks: m, n iid uniform on ``sizes``; sigma_i = exp(-i/r0), r0 ~ U[2, 12].
 
     ``extra['r0']`` holds r0 and ``extra['rank_hint']`` the rank at which sigma falls to
@@ -230,7 +230,7 @@ def workload3(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: flo
 
 
 # ----------------------------------------------------------------------------------------------
-# workload 4: admissible blocks of an exponential covariance kernel over 3D points
+# kernel blocks: admissible blocks of an exponential covariance kernel over 3D points
 # ----------------------------------------------------------------------------------------------
 
 def _kd_tree(pts: np.ndarray, leaf: int):
@@ -265,7 +265,7 @@ def _admissible(a, b, eta):
     return min(da, db) <= eta * float(np.linalg.norm(gap))
 
 
-def workload4(n_points: int = 32768, seed_index: int = 0, leaf: int = 64, eta: float = 1.1, ell: float = 0.1,
+def kernel_blocks_3d(n_points: int = 32768, seed_index: int = 0, leaf: int = 64, eta: float = 1.1, ell: float = 0.1,
               lo: int = 64, hi: int = 256, max_blocks: int | None = None) -> RaggedBatch:
     """Admissible blocks K(t, s) = exp(-|x - y| / ell) of the dual traversal of a k-d tree over
     ``n_points`` uniform points in the unit cube, kept when lo <= |t|, |s| <= hi."""

@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) bj_update_kernel(
 // lo = tf32(x - hi), both rounded to nearest (x carried to 2^-23 relative, without bias), and all
 // four products hi^T hi, hi^T lo, lo^T hi, lo^T lo are formed.  Operands are staged through
 // registers into the K-major core-matrix layout of tcgen05.cuh; the accumulator lives in tensor
-// memory.  The update stays on the SIMT pipes: measured on this GPU, the tensor core's FP32
+// memory.  The update stays on the SIMT pipes: measured on a GB300, the tensor core's FP32
 // accumulation rounds toward zero (mean error -2.7e-7 relative for a K = 64 product of exact
 // TF32 values, FP32 FMA +2e-9), a bias that V, updated ~200 times per column, accumulates to
 // ||V^T V - I|| ~ 2e-5, above the 1e-5 gate; the Gram only feeds the pair test and the inner

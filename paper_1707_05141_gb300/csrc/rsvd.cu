@@ -13,7 +13,7 @@
 //            R_B^T = U_R S V_R^T, so A ~ Q B = Q R_B^T Q_B^T and U = Q U_R, V = Q_B V_R (the QR
 //            writes R_B transposed; one-sided Jacobi on the lower-triangular R_B^T, whose rows are
 //            graded like the singular values, converges in fewer sweeps than on R_B: the same
-//            effect as the register tier's QR preconditioning; workload 3 went from 408 to 390 ms).
+//            effect as the register tier's QR preconditioning).
 //   estimate posterior error of the rank-l approximation from the probes (Halko et al. 4.3):
 //            est^2 = mean_j ||A w_j - U S V^T w_j||^2.  If est > (eps / 2) ||A||_F the block
 //            gets 8 more samples in the next round (the adaptive range finder); past the
@@ -21,8 +21,9 @@
 //   finish   the smallest k with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 - 4 est^2 (FP64 sums,
 //            Section 8.2's relative Frobenius truncation), first k columns of U, V and k values
 //            of S to the caller.
-// Full-rank blocks go through batched_svd_jacobi's tiers (register / shared) or, for min(m, n)
-// above 128, the block-Jacobi tier, with per-block sizes (other blocks get size 0).
+// Full-rank blocks: min(m, n) <= 64 by A = Q R (A^T when m < n), the register-tier SVD of R^T and
+// a batched GEMM for the Q side; up to 128 by the shared tier; above by the block-Jacobi tier.
+// Every stage runs over a device list of the blocks it concerns.
 #include <cuda_runtime.h>
 
 #include "common.cuh"

@@ -25,7 +25,7 @@ def _host(*ts):
 @pytest.fixture(scope="module")
 def w2():
     """Four 512 x 512 FP32 matrices with sigma log-uniform on [1e-6, 1] and their oracle SVDs."""
-    b = gen.workload2(batch=4)
+    b = gen.block512_loguniform(batch=4)
     mats = [b.a64(i) for i in range(b.batch)]
     Uo, So, Vo, info, _ = O.svd_batch(mats)
     return b, mats, So
@@ -131,7 +131,7 @@ def test_block_packed_uneven_batch(bs, method):
 
 
 def test_block_matches_register_tier_on_64x64(bs):
-    b = gen.workload1_svd(batch=32)
+    b = gen.svd64_exp8(batch=32)
     a = torch.from_numpy(b.a).cuda()
     _, s_reg, _, _, _ = bs.svd(a)
     _, s_blk, _, info, _ = bs.svd_block(a, block_width=16, method=0)

@@ -24,7 +24,7 @@ def bs():
 
 @pytest.fixture(scope="module")
 def kernel_blocks():
-    return gen.workload4(n_points=4096, seed_index=11)
+    return gen.kernel_blocks_3d(n_points=4096, seed_index=11)
 
 
 def test_sketch_features_match_oracle(bs, kernel_blocks):
@@ -95,8 +95,8 @@ def test_training_learns_and_beats_plain_adaptive(bs):
     """Train on one point set's ranks (plain adaptive), predict on another: fewer sampling rounds
     at the same 1e-5 truncation error."""
     from paper_1707_05141_gb300 import rank_mlp
-    train_b = gen.workload4(n_points=8192, seed_index=21)
-    test_b = gen.workload4(n_points=8192, seed_index=22)
+    train_b = gen.kernel_blocks_3d(n_points=8192, seed_index=21)
+    test_b = gen.kernel_blocks_3d(n_points=8192, seed_index=22)
     ft = torch.from_numpy(train_b.flat).cuda()
     fe = torch.from_numpy(test_b.flat).cuda()
     ranks, _ = rank_mlp.plain_adaptive_ranks(ft, train_b.offset, train_b.m, train_b.n, seed=5)

@@ -14,7 +14,7 @@ def test_chunked_pipeline_matches_direct_call():
     from paper_1707_05141_gb300.pipeline import ChunkPipeline
     bs.build()
     dev = torch.device("cuda")
-    b = gen.workload1_svd(batch=1000)
+    b = gen.svd64_exp8(batch=1000)
     h_a = torch.from_numpy(b.a).pin_memory()
     d_a = h_a.to(dev)
     outs = [torch.empty((1000, 1, 64), device=dev), torch.empty((1000, 64, 64), device=dev),

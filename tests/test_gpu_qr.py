@@ -41,13 +41,13 @@ def _check_uniform(bs, batch_obj, idx, dtype):
 
 def test_qr_fp64_32x32_full_batch(bs):
     """1000 FP64 32 x 32 matrices, sigma_i = 10^(-8 i/31): every matrix against the oracle."""
-    b = gen.workload0(batch=1000)
+    b = gen.fp64_32_graded(batch=1000)
     _check_uniform(bs, b, range(1000), np.float64)
 
 
 def test_qr_fp32_128x32_full_batch_sampled(bs):
     """20000 FP32 128 x 32 matrices in one launch; 96 sampled matrices checked."""
-    b = gen.workload1_qr(batch=20000)
+    b = gen.qr128x32_exp8(batch=20000)
     idx = list(range(0, 20000, 20000 // 64))[:64] + list(range(19968, 20000))
     _check_uniform(bs, b, idx, np.float32)
 
@@ -147,7 +147,7 @@ def test_qr_host_argument_errors(bs):
 
 
 def test_qr_r_only_and_q_only(bs):
-    b = gen.workload1_qr(batch=16)
+    b = gen.qr128x32_exp8(batch=16)
     dev = torch.device("cuda")
     a = torch.from_numpy(b.a).to(dev)
     q1, r1, _ = bs.qr(a)

@@ -78,7 +78,7 @@ def _check_block(rb, res, b, compare_oracle=True):
 
 def test_rsvd_uneven_blocks_with_rank_hint(bs):
     """128 blocks of the uneven workload (m, n in {64, 128, 256}, sigma_i = exp(-i/r0))."""
-    rb = gen.workload3(batch=128)
+    rb = gen.rsvd_uneven_blocks(batch=128)
     res = _run(bs, rb, rb.extra["rank_hint"])
     full = res.samples_h == np.minimum(rb.m, rb.n)
     fallback = (res.info_h & (1 << 22)) != 0
@@ -90,7 +90,7 @@ def test_rsvd_uneven_blocks_with_rank_hint(bs):
 
 def test_rsvd_plain_adaptive_without_hint(bs):
     """No rank guess: 8 samples, then 8 more per round until the posterior estimate passes."""
-    rb = gen.workload3(batch=48, sizes=(64, 128))
+    rb = gen.rsvd_uneven_blocks(batch=48, sizes=(64, 128))
     res = _run(bs, rb, None, max_rounds=16)
     assert np.any((res.info_h & 0xff) > 1)        # some blocks needed more than one round
     for b in range(rb.batch):
@@ -124,7 +124,7 @@ def test_rsvd_exact_low_rank_is_recovered(bs):
 
 
 def test_rsvd_full_rank_hint_goes_to_jacobi(bs):
-    rb = gen.workload3(batch=24, sizes=(64, 128, 256))
+    rb = gen.rsvd_uneven_blocks(batch=24, sizes=(64, 128, 256))
     hint = np.minimum(rb.m, rb.n)              # guess = min(m, n): straight to the full SVD
     res = _run(bs, rb, hint)
     assert np.all(res.samples_h == np.minimum(rb.m, rb.n))
@@ -133,14 +133,14 @@ def test_rsvd_full_rank_hint_goes_to_jacobi(bs):
 
 
 def test_rsvd_rank_capped(bs):
-    rb = gen.workload3(batch=8, sizes=(128,))
+    rb = gen.rsvd_uneven_blocks(batch=8, sizes=(128,))
     res = _run(bs, rb, rb.extra["rank_hint"], kmax=np.full(8, 5, np.int32))
     assert np.all(res.rank_h == 5)
     assert np.all(res.info_h & (1 << 21))
 
 
 def test_rsvd_workspace_errors(bs):
-    rb = gen.workload3(batch=6, sizes=(64,))
+    rb = gen.rsvd_uneven_blocks(batch=6, sizes=(64,))
     flat = torch.from_numpy(rb.flat).cuda()
     A = bs.Batch.packed(flat, rb.offset, rb.m, rb.n)
     need = bs.batched_rsvd_workspace(A, rb.m, rb.n)

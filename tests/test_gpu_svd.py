@@ -44,7 +44,7 @@ def _check(b, idx, u, s, v, info, dtype, vec_c=64.0):
 
 def test_svd_fp64_32x32_full_batch(bs):
     """1000 FP64 32 x 32 matrices, kappa = 1e8: every matrix within 1e-12 of the oracle."""
-    b = gen.workload0(batch=1000)
+    b = gen.fp64_32_graded(batch=1000)
     u, s, v, info, rots = _run_uniform(bs, b)
     _check(b, range(1000), u, s, v, info, np.float64)
     # the generator's own sigma agrees to the same normwise bound
@@ -53,7 +53,7 @@ def test_svd_fp64_32x32_full_batch(bs):
 
 def test_svd_fp32_64x64_full_batch_sampled(bs):
     """20000 FP32 64 x 64 matrices in one launch (the benchmark's launch); 64 sampled + the tail."""
-    b = gen.workload1_svd(batch=20000)
+    b = gen.svd64_exp8(batch=20000)
     u, s, v, info, rots = _run_uniform(bs, b)
     idx = list(range(0, 20000, 20000 // 48))[:48] + list(range(19984, 20000))
     _check(b, idx, u, s, v, info, np.float32)
@@ -157,7 +157,7 @@ def test_svd_degenerate_inputs(bs):
 
 
 def test_svd_sweep_cap_reports_not_converged(bs):
-    b = gen.workload1_svd(batch=4)
+    b = gen.svd64_exp8(batch=4)
     u, s, v, info, rots = _run_uniform(bs, b, max_sweeps=1)
     assert np.all(info == bs.INFO_NOT_CONVERGED + 1)
     assert np.all(rots > 0) and np.all(rots <= 64 * 63 // 2)
@@ -176,7 +176,7 @@ def test_svd_bad_shape_flagged(bs):
 
 
 def test_svd_without_vectors_matches(bs):
-    b = gen.workload1_svd(batch=32)
+    b = gen.svd64_exp8(batch=32)
     dev = torch.device("cuda")
     a = torch.from_numpy(b.a).to(dev)
     u1, s1, v1, i1, r1 = bs.svd(a)

@@ -31,10 +31,10 @@ def _rank_main(rank, world, port, out_dir):
     try:
         per = 6
         shards = {
-            "w0": gen.workload0(batch=per, first=rank * per).a,
-            "w1": gen.workload1_svd(batch=per, first=rank * per).a,
-            "q1": gen.workload1_qr(batch=per, first=rank * per).a,
-            "w2": gen.workload2(batch=2, first=rank * 2, size=48).a,
+            "w0": gen.fp64_32_graded(batch=per, first=rank * per).a,
+            "w1": gen.svd64_exp8(batch=per, first=rank * per).a,
+            "q1": gen.qr128x32_exp8(batch=per, first=rank * per).a,
+            "w2": gen.block512_loguniform(batch=2, first=rank * 2, size=48).a,
         }
         # the bench's timing reduction: every rank reports the slowest rank's time
         t = bench.max_over_ranks(10.0 + 5.0 * rank, world, torch.device("cpu"))
@@ -53,8 +53,8 @@ def test_two_ranks_shard_the_batch_and_reduce_the_time(tmp_path):
     # max over ranks: rank 1 reported 15 ms, so both see 15
     assert [float(g["t"][0]) for g in got] == [15.0, 15.0]
     # the shards are the single-process batch, split: no matrix is duplicated or missing
-    whole = {"w0": gen.workload0(batch=12).a, "w1": gen.workload1_svd(batch=12).a,
-             "q1": gen.workload1_qr(batch=12).a, "w2": gen.workload2(batch=4, size=48).a}
+    whole = {"w0": gen.fp64_32_graded(batch=12).a, "w1": gen.svd64_exp8(batch=12).a,
+             "q1": gen.qr128x32_exp8(batch=12).a, "w2": gen.block512_loguniform(batch=4, size=48).a}
     for key, full in whole.items():
         joined = np.concatenate([g[key] for g in got])
         assert np.array_equal(joined, full), key

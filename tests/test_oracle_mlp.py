@@ -55,7 +55,7 @@ def test_features_definitions_on_a_rank_one_block():
 
 
 def test_workload4_blocks_are_kernel_blocks():
-    rb = gen.workload4(n_points=2048, seed_index=3)
+    rb = gen.kernel_blocks_3d(n_points=2048, seed_index=3)
     assert rb.batch > 0
     assert set(np.unique(rb.m)) <= {64, 128, 256} and set(np.unique(rb.n)) <= {64, 128, 256}
     a = rb.a64(0)

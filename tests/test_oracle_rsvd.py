@@ -84,7 +84,7 @@ def test_rsvd_full_width_equals_svd():
 
 def test_rsvd_error_bounded_below_by_eckart_young():
     """No rank-k approximation beats the truncated SVD (Section 1: the unique minimiser)."""
-    b = gen.workload3(batch=6)
+    b = gen.rsvd_uneven_blocks(batch=6)
     for i in range(b.batch):
         a = b.a64(i)
         k_full = min(a.shape)

@@ -104,7 +104,7 @@ def test_against_lapack_and_invariants(m, n):
 
 def test_known_sigma_workload0_matrices():
     """The 32 x 32 FP64 workload with sigma_i = 10^(-8i/31): normwise sigma error ~ u64."""
-    b = gen.workload0(batch=8)
+    b = gen.fp64_32_graded(batch=8)
     for i in range(b.batch):
         a = b.a64(i)
         u, s, v, info, rots = O.svd(a)
@@ -116,7 +116,7 @@ def test_known_sigma_workload0_matrices():
 
 
 def test_singular_vectors_match_lapack_up_to_sign():
-    b = gen.workload1_svd(batch=2)
+    b = gen.svd64_exp8(batch=2)
     a = b.a64(1)
     u, s, v, info, _ = O.svd(a)
     ul, sl, vlt = np.linalg.svd(a)
