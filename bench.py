@@ -576,13 +576,14 @@ class RsvdUneven(RsvdBase):
 
     def __init__(self, args):
         self.args = args
-        self.nb = 16384
+        self.nb = args.rsvd_batch
 
     def config(self, world):
-        return {"workload": "rsvd_uneven: randomized SVD to 1e-5 of 16384 FP32 blocks per GPU, m, n uniform on "
+        return {"workload": f"rsvd_uneven: randomized SVD to 1e-5 of {self.nb} FP32 blocks per GPU, m, n uniform on "
                             "{64, 128, 256}, sigma_i = exp(-i/r0), r0 ~ U[2, 12]; p = 8, one power step, rank hint "
                             "= the rank where sigma falls to 1e-5; one CUDA graph per step",
-                "batch_per_gpu": self.nb, "l2": "inputs (1.46 GB per GPU) larger than L2",
+                "batch_per_gpu": self.nb, "l2": f"inputs ({self.nb * 89335 / 1e9:.2f} GB per GPU on average) "
+                f"{'larger' if self.nb * 89335 > 129e6 else 'smaller'} than L2",
                 "parallelism": f"independent batches per GPU x{world}"}
 
     def setup(self, rank, dev):
@@ -784,6 +785,7 @@ def main():
     ap.add_argument("--svd-batch", type=int, default=20000)
     ap.add_argument("--qr-batch", type=int, default=20000)
     ap.add_argument("--block-batch", type=int, default=500, help="block512: matrices per GPU")
+    ap.add_argument("--rsvd-batch", type=int, default=16384, help="rsvd_uneven: blocks per GPU")
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="chunks of the end-to-end run whose copies overlap the computation (1: serial)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")

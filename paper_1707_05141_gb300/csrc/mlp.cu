@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(256) sketch_features_kernel(int batch, const f
 {
     __shared__ float cn[256];           // column norms squared
     __shared__ float ys[256][kProbesF]; // Y = A G (m x 8)
-    __shared__ double red[8][4];
     __shared__ double yy[kProbesF], ww[kProbesF];
     const int b = blockIdx.x;
     float* f = feat + (size_t)b * kF;
