@@ -3,22 +3,27 @@
 //
 // The working matrix W (A, or A^T when m < n, copied into the caller's U or V output) is split into
 // nb column blocks of width bw.  A sweep visits every block pair once in round-robin order (nb - 1
-// steps of nb/2 disjoint pairs, Section 5's ordering applied to blocks), and every step runs three
-// batched stages over all (matrix, pair) items at once:
-//   GRAM   : G = [W_i W_j]^T [W_i W_j] (2bw x 2bw), FP32 dot products, then e_l = the largest
-//            |G_pq| / sqrt(G_pp G_qq) in FP64 (the paper's scaledOffdiag, Section 6.1).  A pair with
-//            e_l <= tol is already orthogonal and is skipped by the next stages.
+// steps of nb/2 disjoint pairs, Section 5's ordering applied to blocks); a matrix with fewer
+// blocks than the batch's largest runs its own steps and idles in the rest.  Every step runs
+// batched stages over the pairs of the matrices not yet converged (device item lists: the GRAM
+// test lists the pairs that rotate, and only those reach the later stages):
+//   GRAM   : G = [W_i W_j]^T [W_i W_j] (2bw x 2bw) -- on the tensor cores for FP32 with bw = 32
+//            (TF32 operands split in a high and a low part, FP32 accumulation in tensor memory),
+//            by FP32 dot products otherwise -- then e_l = the largest |G_pq| / sqrt(G_pp G_qq),
+//            evaluated in FP64 (the paper's scaledOffdiag, Section 6.1).  A pair with e_l <= tol
+//            is already orthogonal and is skipped by the next stages.
 //   DIRECT : [W_i W_j] = Q R by the batched Householder QR, and R goes to the inner SVD instead of
 //            G (Section 6.2): robust for ill-conditioned blocks, where G loses the small singular
 //            values (Section 6.3).
 //   inner  : one-sided Jacobi of the 2bw x 2bw G (or R) with the register-tier kernel, which
-//            returns the accumulated rotation (eigenvectors of G; right singular vectors of R).
+//            returns the rotation X (GRAM: the QR-preconditioned variant's U = Q V_w, the
+//            eigenvectors of G; DIRECT: the right singular vectors of R).
 //   polish : one Newton-Schulz step makes X orthogonal to rounding level (see bj_polish_kernel).
-//   update : [W_i W_j] <- [W_i W_j] X (GRAM, X = accumulated rotation) or <- Q U_R diag(S_R)
-//            (DIRECT), and [V_i V_j] <- [V_i V_j] X, in FP32 on row tiles staged in shared memory.
+//   update : [W_i W_j] <- [W_i W_j] X (GRAM) or <- Q U_R diag(S_R) (DIRECT), and
+//            [V_i V_j] <- [V_i V_j] X, in FP32 on 128-row tiles staged in shared memory.
 // A matrix whose sweep rotated nothing is converged (the paper's "final sweep performs no
-// rotations"); its items are skipped from then on.  Finally sigma_j = ||w_j||, U = W / sigma and
-// the columns of U and V are sorted by descending sigma in place (cycle-following permutation).
+// rotations"); it leaves the lists.  Finally sigma_j = ||w_j||, U = W / sigma and the columns of
+// U and V are sorted by descending sigma in place (cycle-following permutation).
 #include <cuda_runtime.h>
 
 #include <cstddef>
