@@ -50,7 +50,8 @@ extern "C" {
 
 const char* bsvd_version(void)
 {
-    return "bsvd-gb300 0.4 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD, randomized SVD)";
+    return "bsvd-gb300 0.5 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD with QR "
+           "preconditioning and a tcgen05 block Gram, randomized SVD, learned rank predictor)";
 }
 
 int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
