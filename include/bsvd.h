@@ -172,7 +172,11 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
  *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
  *                 | BSVD_BLOCK_SIMT_PRODUCTS keeps the Gram products on the FP32 SIMT pipes (FP32
- *                 data with bw = 32 form them on the tensor cores otherwise).
+ *                 data with bw = 32 form them on the tensor cores otherwise).  | (s << 24) sets the sweep cap of
+ *                 each pair visit's inner SVD: 1 <= s <= 126 sweeps, 127 = to convergence (as
+ *                 Algorithm 3 states), 0 = the default (GRAM: 2, measured as fast with unchanged
+ *                 outer sweeps and errors; DIRECT: to convergence).  The outer sweeps continue
+ *                 until no pair rotates either way.
  *                 DIRECT needs max(m, n) * 2 bw * sizeof(element) <= 200 KiB (the pair's QR runs on
  *                 chip); its default tol is 8 sqrt(max(m, n)) u, since its rotations are only as
  *                 orthogonal as the pair's Householder Q.
