@@ -267,7 +267,7 @@ class SvdQr64:
         oracle.svd_batch(mats, nthreads=cores)
         oracle.qr_batch(qmats, nthreads=cores)
         dt = time.time() - t0
-        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+        return {"value": n / dt, "count": n, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{n} SVDs of 64x64 + {n} QRs of 128x32 (same generator), FP64, {dt:.2f} s wall"}
 
 
@@ -347,7 +347,7 @@ class Fp64_32:
         oracle.svd_batch(mats, nthreads=cores)
         oracle.qr_batch(mats, nthreads=cores)
         dt = time.time() - t0
-        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+        return {"value": n / dt, "count": n, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{n} SVDs + QRs of 32x32 FP64 (same generator), {dt:.2f} s wall"}
 
 
@@ -451,7 +451,7 @@ class Block512:
         t0 = time.time()
         oracle.svd_batch(mats, nthreads=cores)
         dt = time.time() - t0
-        return {"value": n / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+        return {"value": n / dt, "count": n, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{n} SVDs of 512x512 FP64 (same generator), {dt:.2f} s wall"}
 
 
@@ -602,7 +602,7 @@ class RsvdUneven(RsvdBase):
         import gen
         rb = gen.rsvd_uneven_blocks(batch=max(n, 1))
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, rb.extra["rank_hint"])
-        return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+        return {"value": cnt / dt, "count": cnt, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{cnt} blocks of the same generator, fixed-width FP64 RSVD (hint + 8 columns, one "
                           f"power step) or full Jacobi SVD, {dt:.2f} s wall"}
 
@@ -675,9 +675,11 @@ class HmatrixMlp(RsvdBase):
 
     def cpu_sample(self, n):
         import gen
-        rb = gen.kernel_blocks_3d(n_points=8192, seed_index=0)
+        rb = getattr(self, "_cpu_rb", None)
+        if rb is None:  # generated once: every sample times the first n blocks of the same set
+            rb = self._cpu_rb = gen.kernel_blocks_3d(n_points=8192, seed_index=0)
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, None)
-        return {"value": cnt / dt, "unit": self.unit, "cores": cores, "kind": "oracle",
+        return {"value": cnt / dt, "count": cnt, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
                 "sample": f"{cnt} kernel blocks (8192-point set), FP64 RSVD with 8 columns + power step, "
                           f"{dt:.2f} s wall"}
 
@@ -804,15 +806,23 @@ def main():
         # the reference arm is the FP64 oracle on the host cores (the paper ships no code)
         if rank != 0:
             return
-        vals = [W.cpu_sample(max(1, ns // 4)) for _ in range(min(max(args.steps, 1), 3))]
-        v = statistics.median(x["value"] for x in vals)
-        cb = dict(vals[0])
+        # W untimed warm-up samples, then K timed ones; each step a bounded sample (the default
+        # sample split over the K steps), the value total units / total oracle time
+        k = max(1, args.steps)
+        per = max(1, ns // k)
+        for _ in range(args.warmup):
+            W.cpu_sample(per)
+        vals = [W.cpu_sample(per) for _ in range(k)]
+        count = sum(x["count"] for x in vals)
+        seconds = sum(x["seconds"] for x in vals)
+        v = count / seconds
+        cb = {key: val for key, val in vals[0].items() if key not in ("count", "seconds")}
         cb["value"] = v
-        print(json.dumps({"impl": "reference", "metric": W.metric, "value": v, "unit": W.unit, "n_gpus": 0,
-                          "steps": len(vals), "warmup": 0,
-                          "ms_per_step": 1e3 * getattr(W, "nb", 0) / v if getattr(W, "nb", 0) else None,
+        cb["sample"] = f"{k} steps of {per}: " + cb["sample"]
+        print(json.dumps({"impl": "reference", "metric": W.metric, "value": v, "unit": W.unit, "n_gpus": world,
+                          "steps": k, "warmup": args.warmup, "ms_per_step": 1e3 * seconds / k,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": W.config(1), "cpu_baseline": cb,
+                          "data": "synthetic", "config": W.config(world), "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": W.unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
@@ -822,7 +832,7 @@ def main():
     res = run_ours(W, args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = W.cpu_sample(ns)
+        cb = {key: val for key, val in W.cpu_sample(ns).items() if key not in ("count", "seconds")}
     if rank == 0:
         line = {"metric": W.metric, "value": res["value"], "unit": W.unit, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
