@@ -181,6 +181,8 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
     if (!(tol == tol)) return -14;
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
+    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | (0x7f << 24))) return -17;
     if (!d_info) return -18;
     if (!workspace) return -20;
     cudaStream_t st = (cudaStream_t)stream;

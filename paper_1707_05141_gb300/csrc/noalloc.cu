@@ -75,6 +75,8 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
     if (!(tol == tol)) return -14;
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
+    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | (0x7f << 24))) return -17;
     if (!d_info) return -18;
     const size_t need = dtype == BSVD_F32
                             ? bsvd::block_jacobi_workspace<float>(batch, max_m, max_n, block_width, method & 0xff)

@@ -63,6 +63,12 @@ def test_host_argument_checks_without_gpu(lib):
     assert L.batched_svd_jacobi(0, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 0, z, z, z) == -5
     assert L.batched_svd_jacobi(1, 0, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 0, z, z, z) == 0
     assert L.batched_svd_jacobi(0, 1, 4, 4, z, z, z, z, z, z, z, z, z, 0.0, 0, 2 | (1 << 8), z, z, z) == -16
+    # block Jacobi: unknown `method` bits are refused before anything is launched (the pointers
+    # are never dereferenced: the checks return first)
+    p = 64
+    for bad in (1 << 17, 1 << 20, 2, -(1 << 30)):
+        assert L.batched_svd_block_jacobi(0, 1, 64, 64, p, p, p, p, p, p, p, p, p, 0.0, 0, 32, bad, p, z, p, 1 << 20,
+                                          z) == -17, bad
 
 
 def test_variant_counts_and_tuning_table(lib):
