@@ -60,3 +60,29 @@ def test_workload4_blocks_are_kernel_blocks():
     assert set(np.unique(rb.m)) <= {64, 128, 256} and set(np.unique(rb.n)) <= {64, 128, 256}
     a = rb.a64(0)
     assert np.all(a > 0) and np.all(a <= 1.0)
+
+
+def test_features_closed_forms_on_orthogonal_columns():
+    # A = Q diag(d) with orthonormal Q: column norms are d, ||A g||^2 = sum_j d_j^2 g_j^2 and
+    # ||A^T A g||^2 = sum_j d_j^4 g_j^2, so every feature has a closed form in d and the sketch G
+    # (the first 8 columns of Gaussian stream 2 of the matrix).
+    import oracle as O
+    m, n, seed, index = 40, 24, 5, 3
+    q, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((m, n)))
+    d = np.logspace(0.5, -3, n)[np.random.default_rng(2).permutation(n)]
+    a = q * d
+    f = OM.sketch_features(a, seed=seed, index=index)
+    G = O.omega(seed, index, 2, n, 0, 8)
+    fro2 = float((d * d).sum())
+    r = d / math.sqrt(fro2)
+    lr = np.log10(r)
+    yy = ((d[:, None] * G) ** 2).sum(0)
+    ww = ((d[:, None] ** 2 * G) ** 2).sum(0)
+    y = yy / fro2
+    w = ww / (yy * fro2)
+    top = n // 8
+    want = [m / 256, n / 256, 0.5 * math.log10(fro2), lr.max(), lr.min(), lr.mean(), lr.std(),
+            math.log10(y.mean()), y.std() / y.mean(), math.log10(w.mean()), math.log10(w.max()),
+            math.log10(w.min()), math.log10(y.max()), math.log10(y.min()),
+            math.log10(fro2 / (ww / yy).max()), np.sort(d * d)[-top:].sum() / fro2]
+    assert np.abs(f - np.array(want)).max() < 1e-12, np.abs(f - np.array(want))
