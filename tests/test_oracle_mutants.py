@@ -16,7 +16,7 @@ from concurrent.futures import ThreadPoolExecutor
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PINS = [os.path.join(ROOT, "tests", f"test_oracle_{k}.py") for k in ("qr", "svd", "rsvd", "mlp")]
+PINS = [os.path.join(ROOT, "tests", f"test_oracle_{k}.py") for k in ("qr", "svd", "rsvd", "mlp", "h2")]
 
 # (what the mistake is, file, exact text, replacement); each text occurs exactly once in its file.
 MUTANTS = [
@@ -117,6 +117,19 @@ MUTANTS = [
      "math.sqrt(max((lr * lr).mean() - lr.mean() ** 2, 0.0))", "math.sqrt(max((lr * lr).mean(), 0.0))"),
     ("features: sketch from the wrong Gaussian stream", "mlp.py",
      "G = omega(seed, index, 2, n, 0, 8)", "G = omega(seed, index, 1, n, 0, 8)"),
+    # H^2 basis-tree truncation (Section 8.2)
+    ("H2: parent projection without the singular values", "h2.py",
+     "T[l - 1].append(st[:, None] * wt.T)", "T[l - 1].append(wt.T)"),
+    ("H2: new transfers split at the second child's rank", "h2.py",
+     "r1 = ranks[l][c1]", "r1 = ranks[l][c2]"),
+    ("H2: threshold against the squared norm", "h2.py",
+     "trunc_rank(s, float(np.sqrt((s * s).sum())), eps)", "trunc_rank(s, float((s * s).sum()), eps)"),
+    ("H2: children swapped in TE", "h2.py",
+     "np.vstack([T[l][c1] @ transfers[l][c1], T[l][c2] @ transfers[l][c2]])",
+     "np.vstack([T[l][c2] @ transfers[l][c2], T[l][c1] @ transfers[l][c1]])"),
+    ("H2: TE from the transfers without the children's projections", "h2.py",
+     "np.vstack([T[l][c1] @ transfers[l][c1], T[l][c2] @ transfers[l][c2]])",
+     "np.vstack([transfers[l][c1][:ranks[l][c1]], transfers[l][c2][:ranks[l][c2]]])"),
 ]
 
 # Builds and imports the copy before any pin runs; a copy that does not build or import exits 97
@@ -132,7 +145,7 @@ _BOOT = ("import sys; sys.path.insert(0, sys.argv[1])\n"
 def _copy(dst, mutant=None):
     pkg = os.path.join(dst, "oracle")
     os.makedirs(pkg)
-    for f in ("__init__.py", "mlp.py", "oracle.c"):
+    for f in ("__init__.py", "mlp.py", "h2.py", "oracle.c"):
         shutil.copy(os.path.join(ROOT, "oracle", f), pkg)
     if mutant is not None:
         _, fname, old, new = mutant
