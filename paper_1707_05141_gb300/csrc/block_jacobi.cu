@@ -606,7 +606,7 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
                                                 const int* LDU, float* const* V, const int* LDV, const int* M,
                                                 const int* N, unsigned char* ws, const BjLayout& L, double tol,
                                                 unsigned char* sm, uint32_t tmem, uint64_t* bars,
-                                                uint32_t& phase, BjCounters* C)
+                                                uint32_t& phase, uint32_t& used, BjCounters* C)
 {
     constexpr int K2 = 64;
     __shared__ float gd[K2];
@@ -691,6 +691,7 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
             }
             tc::mma_commit(&bars[s]);
         }
+        used |= 1u << s;  // stages that have received a commit (for the failure path's drain)
         if (c + 1 < nch) {
 #pragma unroll
             for (int j = 0; j < kUnits; ++j) cur[j] = nxt[j];
@@ -814,12 +815,20 @@ __global__ void __launch_bounds__(128) bj_gram_tc_kernel(int npairs, int step, i
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    uint32_t phase = 0;
+    uint32_t phase = 0, used = 0;
     const int* mlist = reinterpret_cast<const int*>(ws + L.off_mlist);
     const long long items = (long long)C->mcount * npairs;
     for (long long j = tc_next(C, 0); j < items; j = tc_next(C, 0)) {
         const int b = mlist[j / npairs], k = (int)(j % npairs);
-        bj_gram_tc_item(b * npairs + k, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L, tol, sm, tmem, bars, phase, C);
+        bj_gram_tc_item(b * npairs + k, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L, tol, sm, tmem, bars, phase,
+                        used, C);
+    }
+    // after a wait that gave up (in any CTA of the call) this CTA's MMAs may still be in flight:
+    // wait once more, again bounded, for the last commit of every stage it used before its tensor
+    // memory is released (a CTA whose waits all succeeded finds every phase complete at once)
+    if (*reinterpret_cast<volatile int*>(&C->timeouts) != 0) {
+        for (int s = 0; s < kTcGramStages; ++s)
+            if ((used >> s) & 1u) tc::mbar_wait(&bars[s], ((phase >> s) & 1u) ^ 1u);
     }
     tc::fence_before_sync();
     __syncthreads();
