@@ -135,8 +135,9 @@ int bsvd_jacobi_variant_desc(int dtype, int max_m, int max_n, int k, int* desc);
 /*
  * bsvd_set_jacobi_choice -- record the encoded tier (tier | variant << 8) that BSVD_TIER_AUTO
  * uses for batches whose bounds fall in the same size bin as max_m x max_n (bins are powers of
- * two of max(m, n) and min(m, n), up to 256).  BSVD_TIER_AUTO clears the entry.  Host only, not
- * thread-safe against concurrent batched_svd_jacobi calls; returns 0 or a negative argument code.
+ * two of max(m, n) and min(m, n), up to 256).  BSVD_TIER_AUTO clears the entry.  Host only; may
+ * run concurrently with batched_svd_jacobi calls, which see either the old or the new entry (the
+ * choice applies to calls made after it returns); returns 0 or a negative argument code.
  * (This tuning table is the project's addition: the paper tunes its kernels by hand, Sections 3-5.)
  */
 int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);

@@ -2,6 +2,8 @@
 // selection and launches on the caller's stream.  No device allocation, no synchronisation.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "launch.cuh"
 
@@ -11,8 +13,10 @@ namespace {
 
 // Autotuning table: for each (dtype, size bin of max(m, n), size bin of min(m, n)) the encoded
 // tier | variant << 8 that BSVD_TIER_AUTO uses.  0 = not tuned (built-in preference order).
+// Entries are atomics so that recording a choice may race with calls that read it (relaxed
+// order: a call sees the old or the new entry, each a complete choice).
 constexpr int kBins = 9;  // bins 0..8 cover sizes <= 1, 2, 4, ..., 256
-int g_choice[2][kBins][kBins];
+std::atomic<int> g_choice[2][kBins][kBins];
 
 int size_bin(int x)
 {
@@ -29,7 +33,7 @@ int svd_dispatch(int batch, int max_m, int max_n, int tier, void* const* dA, con
     int base = tier & 0xff, variant = tier >> 8;
     if (base == BSVD_TIER_AUTO) {
         const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
-        const int c = g_choice[sizeof(T) == 8][size_bin(mm)][size_bin(nn)];
+        const int c = g_choice[sizeof(T) == 8][size_bin(mm)][size_bin(nn)].load(std::memory_order_relaxed);
         if (c) {
             base = c & 0xff;
             variant = c >> 8;
@@ -145,7 +149,8 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier)
     const int base = tier & 0xff;
     if (base != BSVD_TIER_AUTO && base != BSVD_TIER_REGISTER && base != BSVD_TIER_SHARED) return -4;
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
-    g_choice[dtype == BSVD_F64][size_bin(mm)][size_bin(nn)] = base == BSVD_TIER_AUTO ? 0 : tier;
+    g_choice[dtype == BSVD_F64][size_bin(mm)][size_bin(nn)].store(base == BSVD_TIER_AUTO ? 0 : tier,
+                                                                 std::memory_order_relaxed);
     return BSVD_SUCCESS;
 }
 
