@@ -253,7 +253,8 @@ int bsvd_sketch_features(int batch, int max_m, int max_n, void* const* dA, const
 
 /* bsvd_mlp_forward -- y = w3 . relu(W2 relu(W1 f + b1) + b2) + b3 for each feature row (y estimates
  * log(rank + 1)).  d_out (nullable) receives y; d_rank_hint (nullable) receives
- * clamp(ceil(exp(y) - 1 + margin), 1, min(m, n)) (min(m, n) only when d_m, d_n are given). */
+ * clamp(ceil(exp(y) - 1 + margin), 1, min(m, n)) (min(m, n) only when d_m, d_n are given, else
+ * 65536; a NaN margin gives 1). */
 int bsvd_mlp_forward(int batch, const float* d_features, const float* d_params, float* d_out, int* d_rank_hint,
                      float margin, const int* d_m, const int* d_n, void* stream);
 

@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(int batch, const float
     if (hint) {
         // predicted rank exp(y) - 1, plus a margin, at least 1, at most min(m, n)
         float r = expf(fminf(y, 8.f)) - 1.f + margin;
-        int h = (int)ceilf(r > 1.f ? r : 1.f);
+        r = r > 1.f ? (r < 65536.f ? r : 65536.f) : 1.f;  // also maps a NaN margin to 1: the int below is defined
+        int h = (int)ceilf(r);
         if (M && N) {
             const int k = M[s] < N[s] ? M[s] : N[s];
             h = h < k ? h : k;

@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(int batch, int max_m, int 
         r.m = bad ? 0 : m;
         r.n = bad ? 0 : n;
         r.k = bad ? 0 : (m < n ? m : n);
-        const int h = hint ? hint[b] : 0;
-        int l = (h > 0 ? h : 0) + p;
+        int h = hint ? hint[b] : 0;
+        h = h < 0 ? 0 : (h > kMaxDim ? kMaxDim : h);  // a hint at or above min(m, n) already means full rank
+        int l = h + p;
         if (l < 1) l = 1;
         r.ell = l;
         r.mode = bad || r.k == 0 ? RS_DONE : ((l >= r.k || l > kLCap) ? RS_FULL : RS_RSVD);
