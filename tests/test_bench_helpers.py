@@ -1,0 +1,73 @@
+"""Host-side helpers of bench.py (CPU only): the nvidia-smi clock-sample parser that decides
+whether a timed run saw throttling, and the algorithmic flop count behind the roofline line."""
+import numpy as np
+import pytest
+
+import bench
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _clocks(lines):
+    c = bench.Clocks(0)
+    c.proc = _FakeProc()
+    c.lines = lines
+    return c
+
+
+def _row(sm, mx=2070, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return f"0, {sm}, {mx}, 812.4, 0x0000000000000000, {hw}, {hwt}, {swt}, {cap}"
+
+
+def test_clock_samples_inside_the_timed_window_only(monkeypatch):
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    lines = [(9.0, _row(1000, hw="Active")),          # before the window: ignored
+             (10.5, _row(2060)), (11.0, _row(2070)), (11.5, _row(2055, cap="Active")),
+             (13.0, _row(900, hwt="Active"))]         # after the window (+0.1 s): ignored
+    out = _clocks(lines).stop(10.0, 12.0)
+    assert out["samples"] == 3 and out["sm_mhz"] == 2060 and out["sm_max_mhz"] == 2070
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_throttle_reasons_are_reported(monkeypatch):
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    lines = [(1.0, _row(1500, hw="Active")), (1.1, _row(1400, hwt="Active")), (1.2, _row(1450, swt="Active")),
+             (1.3, "garbage line"), (1.4, "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active")]
+    out = _clocks(lines).stop(0.5, 2.0)
+    assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert out["samples"] == 3 and out["sm_mhz"] == 1450
+
+
+def test_clocks_without_samples_or_tool():
+    assert bench.Clocks(0).stop(0.0, 1.0) is None            # nvidia-smi never started
+    out = _clocks([]).stop(0.0, 1.0)
+    assert out["sm_mhz"] is None and out["samples"] == 0
+
+
+def test_jacobi_flops_counts_pairs_and_rotations():
+    # 4 x 4, 2 sweeps, 3 rotations: 2 sweeps x 6 pairs x 6 m + 3 x 6 (m + n)
+    assert bench.jacobi_flops(4, 4, [2], [3]) == 2 * 6 * 24 + 3 * 6 * 8
+    # a capped run reports NOT_CONVERGED + sweeps; the sweeps still count
+    assert bench.jacobi_flops(4, 4, [(1 << 20) + 2], [3]) == bench.jacobi_flops(4, 4, [2], [3])
+    # wide matrices pair the columns of A^T: k = min(m, n) columns of max(m, n) rows
+    assert bench.jacobi_flops(3, 5, [1], [0]) == 1 * 3 * 6 * 5
+    # preconditioning adds the factorisation (4 n^3 / 3) and the back-transformation (2 n^3) per matrix
+    pre = bench.jacobi_flops(4, 4, [2, 2], [3, 3], precond=True) - bench.jacobi_flops(4, 4, [2, 2], [3, 3])
+    assert pre == pytest.approx(2 * (4 * 64 / 3 + 2 * 64))
+
+
+def test_traffic_entries_name_current_kernel_digests():
+    for key, val in bench.TRAFFIC.items():
+        name, digest = key.split(":")
+        assert len(digest) == 16 and val > 0
+        assert bench.kernel_digest(f"{name}.cu") == digest, f"{key}: kernel changed since its ncu capture"
+
+
+def test_max_over_ranks_single_rank_is_identity():
+    assert bench.max_over_ranks(3.25, 1, None) == 3.25
