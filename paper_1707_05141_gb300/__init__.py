@@ -135,6 +135,34 @@ def _ptr(t):
     return ctypes.c_void_p(0 if t is None else int(t.data_ptr()))
 
 
+def _dptr(t, name: str, dtype=None, numel: int = 0):
+    """Device pointer of a caller's tensor (None: null), after the checks the kernels cannot make
+    themselves: a host tensor, another element type or too few elements would have them read or
+    write outside the tensor."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required (the library takes device pointers)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: {dtype} required, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: at least {numel} elements required, got {t.numel()}")
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+def _same(X, A, name: str):
+    """An output batch must hold A's element type and a pointer for every matrix of A."""
+    if X is None:
+        return
+    if X.dtype != A.dtype:
+        raise TypeError(f"{name}: {A.dtype} matrices required (the input's type), got {X.dtype}")
+    if X.batch < A.batch:
+        raise ValueError(f"{name}: {A.batch} matrices required, got {X.batch}")
+
+
 class Batch:
     """A batch of column-major matrices in device memory, in the pointer-array form of the C ABI.
 
@@ -143,6 +171,12 @@ class Batch:
     """
 
     def __init__(self, ptrs, m, n, ld, dtype, max_m, max_n, keep=()):
+        torch = _torch()
+        if dtype not in (torch.float32, torch.float64):
+            raise TypeError(f"matrices must be float32 or float64, got {dtype}")
+        for t in (ptrs, m, n, ld):
+            if not t.is_cuda:
+                raise ValueError("a batch lives in device memory: CUDA tensors are required")
         self.ptrs, self.m, self.n, self.ld = ptrs, m, n, ld
         self.dtype, self.max_m, self.max_n = dtype, int(max_m), int(max_n)
         self.keep = tuple(keep)
@@ -160,7 +194,8 @@ class Batch:
     def uniform(cls, t, m: int | None = None, n: int | None = None):
         """``t`` of shape (batch, cols, ld), contiguous on the GPU: matrix b is t[b].T[:m, :n]."""
         torch = _torch()
-        assert t.is_cuda and t.is_contiguous() and t.dim() == 3
+        if not (t.is_cuda and t.is_contiguous() and t.dim() == 3):
+            raise ValueError("Batch.uniform: a contiguous 3-D CUDA tensor (batch, cols, ld) is required")
         bsz, cols, ld = t.shape
         m = ld if m is None else m
         n = cols if n is None else n
@@ -176,6 +211,8 @@ class Batch:
         """Matrices at element ``offsets`` of a flat device tensor; ``m``, ``n``, ``ld`` per matrix
         (``ld`` defaults to max(1, m))."""
         torch = _torch()
+        if not flat.is_cuda:
+            raise ValueError("Batch.packed: the flat storage must be a CUDA tensor")
         dev = flat.device
         off = torch.as_tensor(offsets, dtype=torch.int64).to(dev)
         mt = torch.as_tensor(m, dtype=torch.int32).to(dev)
@@ -199,19 +236,27 @@ def _check(fn, rc):
 
 def batched_qr(A: Batch, Q: Batch | None, R: Batch | None, info, stream=None) -> None:
     """Reduced Householder QR of every matrix of ``A`` (Algorithm 1); see include/bsvd.h."""
+    torch = _torch()
+    _same(Q, A, "Q")
+    _same(R, A, "R")
     rc = lib().batched_qr(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
                           _ptr(Q.ptrs if Q else None), _ptr(Q.ld if Q else None),
-                          _ptr(R.ptrs if R else None), _ptr(R.ld if R else None), _ptr(info), _stream_ptr(stream))
+                          _ptr(R.ptrs if R else None), _ptr(R.ld if R else None),
+                          _dptr(info, "info", torch.int32, A.batch), _stream_ptr(stream))
     _check("batched_qr", rc)
 
 
 def batched_svd_jacobi(A: Batch, S: Batch, U: Batch | None, V: Batch | None, info, rotations=None,
                        tol: float = 0.0, max_sweeps: int = 0, tier: int = TIER_AUTO, stream=None) -> None:
     """Reduced SVD of every matrix of ``A`` by one-sided Jacobi (Algorithm 2); see include/bsvd.h."""
+    torch = _torch()
+    for X, name in ((S, "S"), (U, "U"), (V, "V")):
+        _same(X, A, name)
     rc = lib().batched_svd_jacobi(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
                                   _ptr(S.ptrs), _ptr(U.ptrs if U else None), _ptr(U.ld if U else None),
                                   _ptr(V.ptrs if V else None), _ptr(V.ld if V else None), float(tol),
-                                  int(max_sweeps), int(tier), _ptr(info), _ptr(rotations), _stream_ptr(stream))
+                                  int(max_sweeps), int(tier), _dptr(info, "info", torch.int32, A.batch),
+                                  _dptr(rotations, "rotations", torch.int64, A.batch), _stream_ptr(stream))
     _check("batched_svd_jacobi", rc)
 
 
@@ -224,10 +269,16 @@ def batched_svd_block_jacobi(A: Batch, S: Batch, U: Batch, V: Batch, info, works
                              tol: float = 0.0, max_sweeps: int = 0, block_width: int = 32,
                              method: int = BLOCK_GRAM, stream=None) -> None:
     """Reduced SVD by one-sided block Jacobi (Algorithm 3); ``workspace`` a device uint8 tensor."""
+    torch = _torch()
+    for X, name in ((S, "S"), (U, "U"), (V, "V")):
+        _same(X, A, name)
     rc = lib().batched_svd_block_jacobi(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n),
                                         _ptr(A.ld), _ptr(S.ptrs), _ptr(U.ptrs), _ptr(U.ld), _ptr(V.ptrs), _ptr(V.ld),
-                                        float(tol), int(max_sweeps), int(block_width), int(method), _ptr(info),
-                                        _ptr(rotations), _ptr(workspace), int(workspace.numel()), _stream_ptr(stream))
+                                        float(tol), int(max_sweeps), int(block_width), int(method),
+                                        _dptr(info, "info", torch.int32, A.batch),
+                                        _dptr(rotations, "rotations", torch.int64, A.batch),
+                                        _dptr(workspace, "workspace", torch.uint8), int(workspace.numel()),
+                                        _stream_ptr(stream))
     _check("batched_svd_block_jacobi", rc)
 
 
@@ -245,11 +296,17 @@ def batched_rsvd(A: Batch, U: Batch, S: Batch, V: Batch, kmax, rank, info, works
                  tol: float = 1e-5, oversample: int = 8, max_rounds: int = 4, seed: int = 0, err_est=None,
                  samples=None, stream=None) -> None:
     """Randomized truncated SVD (Algorithm 4 + one power step, adaptive); see include/bsvd.h."""
+    torch = _torch()
+    for X, name in ((S, "S"), (U, "U"), (V, "V")):
+        _same(X, A, name)
+    nb, i32 = A.batch, torch.int32
     rc = lib().batched_rsvd(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
-                            _ptr(rank_hint), float(tol), int(oversample), int(max_rounds), int(seed), _ptr(U.ptrs),
-                            _ptr(U.ld), _ptr(S.ptrs), _ptr(V.ptrs), _ptr(V.ld), _ptr(kmax), _ptr(rank),
-                            _ptr(err_est), _ptr(samples), _ptr(info), _ptr(workspace), int(workspace.numel()),
-                            _stream_ptr(stream))
+                            _dptr(rank_hint, "rank_hint", i32, nb), float(tol), int(oversample), int(max_rounds),
+                            int(seed), _ptr(U.ptrs), _ptr(U.ld), _ptr(S.ptrs), _ptr(V.ptrs), _ptr(V.ld),
+                            _dptr(kmax, "kmax", i32, nb), _dptr(rank, "rank", i32, nb),
+                            _dptr(err_est, "err_est", torch.float32, nb), _dptr(samples, "samples", i32, nb),
+                            _dptr(info, "info", i32, nb), _dptr(workspace, "workspace", torch.uint8),
+                            int(workspace.numel()), _stream_ptr(stream))
     _check("batched_rsvd", rc)
 
 
@@ -259,26 +316,43 @@ MLP_PARAMS = 5313
 
 def bsvd_sketch_features(A: Batch, features, seed: int = 0, stream=None) -> None:
     """16 sketch features per matrix into ``features`` (batch x 16 FP32 device tensor)."""
+    torch = _torch()
+    if A.dtype != torch.float32:
+        raise TypeError("bsvd_sketch_features: float32 matrices required")
+    feat = _dptr(features, "features", torch.float32, A.batch * SKETCH_FEATURES)
     _check("bsvd_sketch_features", lib().bsvd_sketch_features(A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m),
-                                                               _ptr(A.n), _ptr(A.ld), int(seed), _ptr(features),
+                                                               _ptr(A.n), _ptr(A.ld), int(seed), feat,
                                                                _stream_ptr(stream)))
 
 
 def bsvd_mlp_forward(features, params, out=None, hint=None, margin: float = 2.0, m=None, n=None, stream=None):
+    torch = _torch()
     batch = int(features.shape[0])
-    _check("bsvd_mlp_forward", lib().bsvd_mlp_forward(batch, _ptr(features), _ptr(params), _ptr(out), _ptr(hint),
-                                                       float(margin), _ptr(m), _ptr(n), _stream_ptr(stream)))
+    f32, i32 = torch.float32, torch.int32
+    _check("bsvd_mlp_forward", lib().bsvd_mlp_forward(batch, _dptr(features, "features", f32, batch * SKETCH_FEATURES),
+                                                       _dptr(params, "params", f32, MLP_PARAMS),
+                                                       _dptr(out, "out", f32, batch), _dptr(hint, "hint", i32, batch),
+                                                       float(margin), _dptr(m, "m", i32, batch),
+                                                       _dptr(n, "n", i32, batch), _stream_ptr(stream)))
 
 
 def bsvd_mlp_grad(features, target, params, grad, loss, stream=None):
+    torch = _torch()
     batch = int(features.shape[0])
-    _check("bsvd_mlp_grad", lib().bsvd_mlp_grad(batch, _ptr(features), _ptr(target), _ptr(params), _ptr(grad),
-                                                 _ptr(loss), _stream_ptr(stream)))
+    f32 = torch.float32
+    _check("bsvd_mlp_grad", lib().bsvd_mlp_grad(batch, _dptr(features, "features", f32, batch * SKETCH_FEATURES),
+                                                 _dptr(target, "target", f32, batch),
+                                                 _dptr(params, "params", f32, MLP_PARAMS),
+                                                 _dptr(grad, "grad", f32, MLP_PARAMS), _dptr(loss, "loss", f32, 1),
+                                                 _stream_ptr(stream)))
 
 
 def bsvd_mlp_adam(params, grad, mom, vel, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
                   eps: float = 1e-8, stream=None):
-    _check("bsvd_mlp_adam", lib().bsvd_mlp_adam(int(params.numel()), _ptr(params), _ptr(grad), _ptr(mom), _ptr(vel),
+    torch = _torch()
+    f32, npar = torch.float32, int(params.numel())
+    _check("bsvd_mlp_adam", lib().bsvd_mlp_adam(npar, _dptr(params, "params", f32), _dptr(grad, "grad", f32, npar),
+                                                 _dptr(mom, "mom", f32, npar), _dptr(vel, "vel", f32, npar),
                                                  int(step), float(lr), float(beta1), float(beta2), float(eps),
                                                  _stream_ptr(stream)))
 
@@ -340,10 +414,15 @@ def batched_svd_block_jacobi_noalloc(A: Batch, S: Batch, U: Batch, V: Batch, inf
                                      method: int = BLOCK_GRAM, stream=None) -> None:
     """Block-Jacobi SVD with the library's own fixed scratch (no workspace, no allocation);
     see include/bsvd.h for its limit and the rule against overlapping calls."""
+    torch = _torch()
+    for X, name in ((S, "S"), (U, "U"), (V, "V")):
+        _same(X, A, name)
     rc = lib().batched_svd_block_jacobi_noalloc(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m),
                                                 _ptr(A.n), _ptr(A.ld), _ptr(S.ptrs), _ptr(U.ptrs), _ptr(U.ld),
                                                 _ptr(V.ptrs), _ptr(V.ld), float(tol), int(max_sweeps),
-                                                int(block_width), int(method), _ptr(info), _ptr(rotations),
+                                                int(block_width), int(method),
+                                                _dptr(info, "info", torch.int32, A.batch),
+                                                _dptr(rotations, "rotations", torch.int64, A.batch),
                                                 _stream_ptr(stream))
     _check("batched_svd_block_jacobi_noalloc", rc)
 
