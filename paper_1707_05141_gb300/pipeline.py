@@ -9,6 +9,16 @@ has no counterpart)."""
 from __future__ import annotations
 
 
+def chunk_bounds(n: int, chunks: int):
+    """[(c0, c1), ...]: at most ``chunks`` consecutive, non-empty ranges covering 0 .. n - 1, all of
+    the same length but the last."""
+    if n <= 0:
+        return []
+    chunks = max(1, min(chunks, n))
+    step = (n + chunks - 1) // chunks
+    return [(c0, min(c0 + step, n)) for c0 in range(0, n, step)]
+
+
 class ChunkPipeline:
     """Device buffers and streams for repeated host -> device -> host runs of one batch shape.
 
@@ -24,10 +34,7 @@ class ChunkPipeline:
             if not h.is_pinned():
                 raise ValueError("host buffers must be pinned")
         self.compute = compute
-        n = self.h_in[0].shape[0]
-        chunks = max(1, min(chunks, n))
-        step = (n + chunks - 1) // chunks
-        self.bounds = [(c0, min(c0 + step, n)) for c0 in range(0, n, step)]
+        self.bounds = chunk_bounds(self.h_in[0].shape[0], chunks)
         dev = self.d_in[0].device
         self.s_in, self.s_comp, self.s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
         self.ev_in = [torch.cuda.Event() for _ in self.bounds]

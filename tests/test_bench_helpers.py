@@ -71,3 +71,14 @@ def test_traffic_entries_name_current_kernel_digests():
 
 def test_max_over_ranks_single_rank_is_identity():
     assert bench.max_over_ranks(3.25, 1, None) == 3.25
+
+
+@pytest.mark.parametrize("n,chunks", [(20000, 4), (1000, 3), (7, 4), (5, 8), (1, 4), (0, 4), (10, 1)])
+def test_chunk_bounds_cover_the_batch_once(n, chunks):
+    from paper_1707_05141_gb300.pipeline import chunk_bounds
+    b = chunk_bounds(n, chunks)
+    assert len(b) <= max(1, chunks)
+    covered = [i for c0, c1 in b for i in range(c0, c1)]
+    assert covered == list(range(n))
+    assert all(c1 > c0 for c0, c1 in b)
+    assert len({c1 - c0 for c0, c1 in b[:-1]}) <= 1
