@@ -106,7 +106,8 @@ def predict(feats, params, margin: float = 2.0, m=None, n=None):
 
 def save(path: str, params, meta: dict | None = None) -> None:
     p = params.detach().cpu().numpy().astype("<f4") if hasattr(params, "detach") else np.asarray(params, "<f4")
-    assert p.size == MLP_PARAMS
+    if p.size != MLP_PARAMS:
+        raise ValueError(f"{p.size} parameters, expected {MLP_PARAMS}")
     hdr = json.dumps(dict(meta or {}, nparams=int(p.size), features=F, hidden=H)).encode()
     with open(path, "wb") as f:
         f.write(MAGIC)
@@ -118,11 +119,17 @@ def save(path: str, params, meta: dict | None = None) -> None:
 def load(path: str):
     """(params as a float32 numpy array, header dict)."""
     with open(path, "rb") as f:
-        if f.read(8) != MAGIC:
-            raise ValueError(f"{path}: not a rank-predictor checkpoint")
-        (hl,) = struct.unpack("<I", f.read(4))
-        hdr = json.loads(f.read(hl).decode())
-        p = np.frombuffer(f.read(), dtype="<f4").copy()
-    if p.size != hdr.get("nparams", MLP_PARAMS) or p.size != MLP_PARAMS:
-        raise ValueError(f"{path}: {p.size} parameters, expected {MLP_PARAMS}")
-    return p, hdr
+        data = f.read()
+    if data[:8] != MAGIC or len(data) < 12:
+        raise ValueError(f"{path}: not a rank-predictor checkpoint")
+    (hl,) = struct.unpack("<I", data[8:12])
+    body = data[12 + hl:]
+    try:
+        hdr = json.loads(data[12:12 + hl].decode()) if 12 + hl <= len(data) else None
+    except (UnicodeDecodeError, ValueError):
+        hdr = None
+    if not isinstance(hdr, dict):
+        raise ValueError(f"{path}: damaged checkpoint header")
+    if len(body) != 4 * MLP_PARAMS or hdr.get("nparams", MLP_PARAMS) != MLP_PARAMS:
+        raise ValueError(f"{path}: {len(body) // 4} parameters, expected {MLP_PARAMS}")
+    return np.frombuffer(body, dtype="<f4").copy(), hdr
