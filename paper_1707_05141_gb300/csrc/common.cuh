@@ -41,8 +41,8 @@ __device__ __forceinline__ T group_sum(T v)
 
 // Round-robin ("circle") ordering of Section 5: np (even) column positions, np - 1 steps of
 // np / 2 disjoint pairs; position np - 1 stays fixed while the others rotate by one each step.
-// Returns the pair (p < q) handled by slot k in step `step`.
-__device__ __forceinline__ void round_robin_pair(int np, int step, int k, int& p, int& q)
+// Returns the pair (p < q) handled by slot k in step `step`.  (Host-callable for tests.)
+__host__ __device__ __forceinline__ void round_robin_pair(int np, int step, int k, int& p, int& q)
 {
     int a, b;
     if (k == 0) {
