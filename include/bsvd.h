@@ -212,8 +212,9 @@ size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const 
  *
  *   d_rank_hint[b] (nullable) first rank guess k0; the first round draws l = k0 + oversample
  *                  Gaussian columns (Philox4x32-10, counter (row/4, column, b, 0), key = seed).
- *                  NULL or 0 starts from l = oversample.  A guess with l >= min(m, n) (or > 128)
- *                  sends the matrix straight to the full Jacobi SVD.
+ *                  NULL or 0 starts from l = oversample (a negative guess counts as 0, one above
+ *                  256 as 256).  A guess with l >= min(m, n) (or > 128) sends the matrix straight
+ *                  to the full Jacobi SVD.
  *   tol            eps: the result satisfies ||A - U S V^T||_F <= eps ||A||_F up to the posterior
  *                  estimate's error.  After each round, 8 probe columns (stream 1) give
  *                  est = ||(A - U_l S_l V_l^T) W||_F / sqrt(8); est <= eps/2 ||A||_F accepts the
