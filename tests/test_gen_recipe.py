@@ -67,3 +67,33 @@ def test_kernel_blocks_3d_recipe():
         tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1])
         rank = int(np.argmax(tail <= 1e-5 * np.linalg.norm(a))) if np.any(tail <= 1e-5 * np.linalg.norm(a)) else len(s)
         assert 2 <= rank <= 40, (b, rank)                               # numerically low rank
+
+
+def test_admissibility_closed_form():
+    # unit cubes with a gap g along x: diameters sqrt(3), distance g -> admissible iff sqrt(3) <= eta g
+    lo, hi = np.zeros(3), np.ones(3)
+    for g, eta, want in [(2.0, 1.1, True), (1.5, 1.1, False), (1.6, 1.1, True), (1.55, 1.1, False),
+                         (1.7321, 1.0, True), (1.732, 1.0, False)]:
+        a = [0, 0, lo, hi, None]
+        b = [0, 0, lo + np.array([1.0 + g, 0, 0]), hi + np.array([1.0 + g, 0, 0]), None]
+        assert gen._admissible(a, b, eta) == want, (g, eta)
+    # touching boxes are never admissible; a box is never admissible with itself
+    a = [0, 0, lo, hi, None]
+    assert not gen._admissible(a, [0, 0, lo + np.array([1.0, 0, 0]), hi + np.array([1.0, 0, 0]), None], 10.0)
+    assert not gen._admissible(a, a, 10.0)
+
+
+def test_kd_tree_partitions_with_median_splits():
+    pts = gen.uniforms(4, 0, gen.TAG_MISC, 3 * 1000).reshape(1000, 3)
+    perm, nodes = gen._kd_tree(pts, 64)
+    assert sorted(perm.tolist()) == list(range(1000))
+    for s, e, lo, hi, ch in nodes:
+        p = pts[perm[s:e]]
+        assert np.all(p >= lo) and np.all(p <= hi)
+        if ch is None:
+            assert e - s <= 64
+        else:
+            a, b = nodes[ch[0]], nodes[ch[1]]
+            assert (a[0], a[1], b[0], b[1]) == (s, (s + e) // 2, (s + e) // 2, e)   # median: equal halves
+            d = int(np.argmax(hi - lo))                                               # split along the widest side
+            assert pts[perm[a[0]:a[1]], d].max() <= pts[perm[b[0]:b[1]], d].min()
