@@ -141,6 +141,31 @@ def jacobi_flops(m, n, info, rots, precond=False):
     return fl
 
 
+def block_jacobi_launches(n_cols, bw=32, sweeps=20):
+    """Kernels one batched_svd_block_jacobi call launches (GRAM): setup, then for every sweep up to
+    the cap -- launched whether or not matrices have converged, whose items the device lists then
+    skip -- (blocks - 1) steps of Gram, inner SVD, polish and update plus the sweep-end kernel,
+    then finalize."""
+    nblk = max(2, -(-n_cols // bw))
+    nblk += nblk & 1
+    return 1 + sweeps * ((nblk - 1) * 4 + 1) + 1
+
+
+def rsvd_launches(max_m, max_n, rounds):
+    """Kernels one batched_rsvd call launches: plan and scan; per round the arrays kernel, four
+    GEMM + QR pairs (sample, power step, projection), the small SVD (register tier, plus the shared
+    tier when samples may pass 64), two GEMMs for U and V and the estimate; then the fallback and
+    arrays kernels, the full-rank QR path (QR, SVD, GEMM, copy), the shared tier (min > 64), the
+    block tier (min > 128) and the finish kernel."""
+    kx = min(max_m, max_n)
+    lx = min(kx, 128)
+    per_round = 14 + (1 if lx > 64 else 0)
+    n = 2 + rounds * per_round + 2
+    if kx > 0:
+        n += 4 + (1 if kx > 64 else 0) + (block_jacobi_launches(kx) if kx > 128 else 0)
+    return n + 1
+
+
 def tier_precond(bs, code, m, n, tier):
     """True when the encoded register tier is a QR-preconditioned variant."""
     if (tier & 0xff) != bs.TIER_REGISTER:
@@ -359,7 +384,7 @@ class Block512:
     metric = "batched SVDs/s (512x512 FP32 block-Jacobi SVD)"
     unit = "SVDs/s"
     dtype = "f32"
-    launches_per_step = 0   # set after the first step (kernels launched inside the call)
+    launches_per_step = block_jacobi_launches(512, 32, 20)   # every sweep up to the cap of 20 is launched
 
     def __init__(self, args):
         self.args = args
@@ -413,7 +438,6 @@ class Block512:
         fl = float(np.sum(sweeps) * 120 * pair_fl)
         achieved = fl / (kernel_ms * 1e-3) / 1e12
         err = float(np.abs(self.S.cpu().numpy()[:, 0, :] - self.sigma).max())
-        self.launches_per_step = int(np.max(sweeps)) * 15 * 4 + 2
         return ({"kernel": "batched_svd_block_jacobi (all stages of one call)", "bound": "alu",
                  "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                  "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "ms_per_launch": kernel_ms,
@@ -598,7 +622,7 @@ class RsvdUneven(RsvdBase):
     def inner(self, stream):
         self._rsvd(stream, self.hint, 4)
 
-    launches_per_step = 4 * 15 + 6
+    launches_per_step = rsvd_launches(256, 256, 4)
 
     def cpu_sample(self, n):
         import gen
@@ -654,7 +678,7 @@ class HmatrixMlp(RsvdBase):
         bs.bsvd_mlp_forward(self.feats, self.params, self.pred, self.hint_d, 2.0, self.md, self.nd, stream)
         self._rsvd(stream, self.hint_d, 16)
 
-    launches_per_step = 2 + 15 + 6
+    launches_per_step = 2 + rsvd_launches(256, 256, 16)   # features, forward, then the randomized SVD
 
     def plain_ms(self, stream):
         """The plain adaptive method (no hints) on the same blocks: time, rounds, worst error."""

@@ -82,3 +82,15 @@ def test_chunk_bounds_cover_the_batch_once(n, chunks):
     assert covered == list(range(n))
     assert all(c1 > c0 for c0, c1 in b)
     assert len({c1 - c0 for c0, c1 in b[:-1]}) <= 1
+
+
+def test_launch_counts_follow_the_host_drivers():
+    # block tier, 512 columns of width 32: 16 blocks, 15 steps x (Gram, inner SVD, polish, update)
+    # and the sweep-end kernel for each of 20 sweeps, plus setup and finalize
+    assert bench.block_jacobi_launches(512, 32, 20) == 1 + 20 * (15 * 4 + 1) + 1
+    # randomized SVD of blocks up to 256 x 256, 4 rounds: plan + scan, 15 per round (the shared
+    # tier joins the register tier for the small SVD), fallback + arrays, the QR path (4), the
+    # shared tier, the block tier over 256 columns (8 blocks, 7 steps) and the finish kernel
+    assert bench.rsvd_launches(256, 256, 4) == 2 + 4 * 15 + 2 + 4 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1
+    # blocks up to 64 x 64: no shared or block tier
+    assert bench.rsvd_launches(64, 64, 4) == 2 + 4 * 14 + 2 + 4 + 1
