@@ -64,6 +64,14 @@ def lib():
             L.orc_rsvd.argtypes = [i, i, p, i, u64, u32, i, i, p, p, p]
             L.orc_trunc_rank.restype = i
             L.orc_trunc_rank.argtypes = [i, p, d, d]
+            L.orc_post_est2.restype = d
+            L.orc_post_est2.argtypes = [i, i, p, i, p, p, p, i, u64, u32, i]
+            L.orc_budget_rank.restype = i
+            L.orc_budget_rank.argtypes = [i, p, d, d, d]
+            L.orc_rsvd_adaptive.restype = i
+            L.orc_rsvd_adaptive.argtypes = [i, i, p, i, u64, u32, i, d, i, i, i, i, p, p, p, p, p]
+            L.orc_rsvd_rank.restype = i
+            L.orc_rsvd_rank.argtypes = [i, i, p, i, u64, u32, i, i, i, i, p, p, p]
             L.orc_qr_batch.argtypes = [i, p, p, p, p, p, p, p, p, p, i]
             L.orc_svd_batch.argtypes = [i, p, p, p, p, d, i, p, p, p, p, p, p, p, p, i]
             _lib = L
@@ -190,6 +198,64 @@ def rsvd(a, seed: int, index: int, l: int, q: int = 1):
 def trunc_rank(s, norm_a: float, eps: float) -> int:
     s = np.ascontiguousarray(s, dtype=np.float64)
     return lib().orc_trunc_rank(s.size, _p(s), norm_a, eps)
+
+
+PROBES = 8
+
+
+def post_est2(a, U, S, V, seed: int, index: int, r: int = PROBES) -> float:
+    """Posterior estimate (Halko et al. 4.3) of ||A - U diag(S) V^T||_F^2 from r probes of stream 1."""
+    a = _f64(a)
+    m, n = a.shape
+    U, V = _f64(U), _f64(V)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    l = S.size
+    return lib().orc_post_est2(m, n, _p(a), m, _p(U), _p(S), _p(V), l, seed, index, r)
+
+
+def budget_rank(s, norm2: float, eps: float, est2: float) -> int:
+    """Smallest k with sum_{i>=k} s_i^2 <= (0.95 eps)^2 norm2 - 4 est2."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    return lib().orc_budget_rank(s.size, _p(s), norm2, eps, est2)
+
+
+def rsvd_adaptive(a, seed: int, index: int, hint: int = 0, eps: float = 1e-5, p: int = 8, q: int = 1,
+                  max_rounds: int = 4, lcap: int = 128):
+    """Adaptive randomized SVD to a relative Frobenius tolerance (rounds of p samples, posterior
+    estimate, full-SVD fallback, budgeted truncation).  Returns a dict with U, S, V (first
+    `samples` columns), rank, samples, rounds, fallback, est2, norm2 and est2_round."""
+    a = _f64(a)
+    m, n = a.shape
+    k = min(m, n)
+    U = np.zeros((m, k), order="F")
+    V = np.zeros((n, k), order="F")
+    S = np.zeros(k)
+    res = np.zeros(6)
+    er = np.full(max_rounds, np.nan)
+    rc = lib().orc_rsvd_adaptive(m, n, _p(a), m, seed, index, int(hint), eps, p, q, max_rounds, lcap,
+                                 _p(U), _p(S), _p(V), _p(res), _p(er))
+    if rc:
+        raise ValueError("orc_rsvd_adaptive: bad arguments")
+    l = int(res[1])
+    return {"U": U[:, :l], "S": S[:l], "V": V[:, :l], "rank": int(res[0]), "samples": l, "rounds": int(res[2]),
+            "fallback": bool(res[3]), "est2": float(res[4]), "norm2": float(res[5]),
+            "est2_round": er[:int(res[2])]}
+
+
+def rsvd_rank(a, seed: int, index: int, k: int, p: int = 8, q: int = 1, lcap: int = 128):
+    """Fixed-rank randomized SVD (Algorithm 4: k + p samples, q power steps, first k columns kept;
+    the full SVD when k + p reaches min(m, n) or exceeds lcap): (U_k, S_k, V_k, samples)."""
+    a = _f64(a)
+    m, n = a.shape
+    kk = min(m, n)
+    U = np.zeros((m, kk), order="F")
+    V = np.zeros((n, kk), order="F")
+    S = np.zeros(kk)
+    l = lib().orc_rsvd_rank(m, n, _p(a), m, seed, index, int(k), p, q, lcap, _p(U), _p(S), _p(V))
+    if l < 0:
+        raise ValueError("orc_rsvd_rank: bad arguments")
+    k = min(int(k), kk)
+    return U[:, :k].copy(), S[:k].copy(), V[:, :k].copy(), l
 
 
 # ----------------------------------------------------------------------------------------------

@@ -23,6 +23,9 @@
  *  - convergence: a sweep that performs no rotation; at most max_sweeps sweeps.
  *  - singular values sorted descending (Section 1), ties kept in column order.
  *  - right singular vectors by accumulating the rotations on the identity (Section 2.2).
+ *  - randomized SVD to a tolerance: Algorithm 4 in rounds of p samples, judged by an 8-probe
+ *    posterior estimate (Halko, Martinsson & Tropp 2011, Sec. 4.3-4.4), with a full-SVD fallback
+ *    and a budgeted truncation; the constants are stated beside orc_rsvd_adaptive.
  */
 #include <math.h>
 #include <pthread.h>
@@ -410,6 +413,135 @@ int orc_trunc_rank(int len, const double* S, double normA, double eps)
         k = i;
     }
     return k;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Adaptive randomized SVD to a relative Frobenius tolerance.  Section 7 runs Algorithm 4 with a
+ * fixed sample count; the adaptive form follows Halko, Martinsson & Tropp (2011), Sec. 4.3-4.4,
+ * which the paper cites for the method: a posterior estimate of the range error decides whether
+ * more samples are drawn.  The constants are the library's reading of it:
+ *  - r = 8 probe columns w_j, Gaussian stream 1 of the matrix (stream 0 is Omega);
+ *  - est^2 = (1/r) sum_j ||(A - U S V^T) w_j||^2 (unbiased for ||A - U S V^T||_F^2);
+ *  - a round with l samples is accepted when est <= (eps / 2) ||A||_F;
+ *  - otherwise l grows by p; when l would reach min(m, n) or exceed lcap, or after max_rounds
+ *    rounds, the matrix takes the full Jacobi SVD (est = 0 then);
+ *  - the rank is the smallest k with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 - 4 est^2 (the
+ *    estimate trusted to a factor 2 in est, 5% of eps kept for the factorisation's own error).
+ * ------------------------------------------------------------------------------------------- */
+
+#define ORC_PROBES 8
+
+/* est^2 = (1/r) sum_j ||A w_j - U diag(S) V^T w_j||^2 for the first r columns w_j of stream 1 of
+   `index` (U m x l, S l, V n x l, column-major with ld m and n). */
+double orc_post_est2(int m, int n, const double* A, int lda, const double* U, const double* S,
+                     const double* V, int l, uint64_t seed, uint32_t index, int r)
+{
+    double* W = (double*)malloc(sizeof(double) * (size_t)n * (r > 0 ? r : 1));
+    double* AW = (double*)malloc(sizeof(double) * (size_t)m * (r > 0 ? r : 1));
+    double* VW = (double*)malloc(sizeof(double) * (size_t)(l > 0 ? l : 1) * (r > 0 ? r : 1));
+    orc_omega(seed, index, 1, n, 0, r, W);
+    orc_gemm(0, 0, m, r, n, A, lda, W, n, AW, m);     /* A W       */
+    if (l > 0) orc_gemm(1, 0, l, r, n, V, n, W, n, VW, l); /* V^T W     */
+    double sum = 0.0;
+    for (int j = 0; j < r; ++j)
+        for (int i = 0; i < m; ++i) {
+            double e = AT(AW, m, i, j);
+            for (int c = 0; c < l; ++c) e -= AT(U, m, i, c) * S[c] * AT(VW, l, c, j);
+            sum += e * e;
+        }
+    free(W);
+    free(AW);
+    free(VW);
+    return r > 0 ? sum / r : 0.0;
+}
+
+/* Truncation with the estimate's budget: the smallest k (<= len) with
+   sum_{i >= k} S_i^2 <= (0.95 eps)^2 normA2 - 4 est2 (a negative budget keeps all len values). */
+int orc_budget_rank(int len, const double* S, double normA2, double eps, double est2)
+{
+    double thr = 0.95 * 0.95 * eps * eps * normA2 - 4.0 * est2;
+    if (thr < 0.0) thr = 0.0;
+    double tail = 0.0;
+    int k = len;
+    for (int i = len - 1; i >= 0; --i) {
+        double t = tail + S[i] * S[i];
+        if (t > thr) break;
+        tail = t;
+        k = i;
+    }
+    return k;
+}
+
+/* Adaptive randomized SVD of one m x n matrix (1 <= m, n).  hint: first rank guess (clamped to
+   [0, 256]); the first round draws l = hint + p columns.  q power steps per round.
+   Outputs (caller-allocated, k = min(m, n)): U (m x k), S (k), V (n x k) -- the first `samples`
+   columns are filled -- and res[6] = {rank, samples, rounds, fallback (0/1), est2 (as double),
+   ||A||_F^2}; est2_round (max_rounds, nullable) receives each round's estimate.
+   Returns 0, or -1 for bad arguments. */
+int orc_rsvd_adaptive(int m, int n, const double* A, int lda, uint64_t seed, uint32_t index,
+                      int hint, double eps, int p, int q, int max_rounds, int lcap,
+                      double* U, double* S, double* V, double* res, double* est2_round)
+{
+    if (m < 1 || n < 1 || lda < m || p < 1 || max_rounds < 1) return -1;
+    int k = m < n ? m : n;
+    double norm2 = 0.0;
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < m; ++i) norm2 += AT(A, lda, i, j) * AT(A, lda, i, j);
+    if (hint < 0) hint = 0;
+    if (hint > 256) hint = 256;
+    int l = hint + p;
+    int full = (l >= k || l > lcap);
+    int rounds = 0, fallback = 0, accepted = 0;
+    double est2 = 0.0;
+    for (int r = 0; r < max_rounds && !full && !accepted; ++r) {
+        orc_rsvd(m, n, A, lda, seed, index, l, q, U, S, V);
+        est2 = orc_post_est2(m, n, A, lda, U, S, V, l, seed, index, ORC_PROBES);
+        if (est2_round) est2_round[r] = est2;
+        rounds += 1;
+        if (est2 <= 0.25 * eps * eps * norm2) {
+            accepted = 1;
+        } else if (l + p >= k || l + p > lcap) {
+            full = 1;
+            fallback = 1;
+        } else {
+            l += p;
+        }
+    }
+    if (!full && !accepted) { /* rounds exhausted */
+        full = 1;
+        fallback = 1;
+    }
+    int samples = l;
+    if (full) {
+        orc_jacobi_svd(m, n, A, lda, -1.0, 60, S, U, m, V, n, NULL);
+        est2 = 0.0;
+        samples = k;
+    }
+    res[0] = orc_budget_rank(samples, S, norm2, eps, est2);
+    res[1] = samples;
+    res[2] = rounds;
+    res[3] = fallback;
+    res[4] = est2;
+    res[5] = norm2;
+    return 0;
+}
+
+/* Fixed-rank randomized SVD (Algorithm 4 as stated: k + p samples, q power steps, the first k
+   columns kept).  When k + p reaches min(m, n) or exceeds lcap, the full Jacobi SVD replaces the
+   sampling.  U (m x min(m,n)), S, V (n x min(m,n)) caller-allocated; the first k columns are the
+   result.  Returns the number of samples used (k + p, or min(m, n)), or -1. */
+int orc_rsvd_rank(int m, int n, const double* A, int lda, uint64_t seed, uint32_t index, int k,
+                  int p, int q, int lcap, double* U, double* S, double* V)
+{
+    int kk = m < n ? m : n;
+    if (m < 1 || n < 1 || lda < m || k < 1 || p < 0) return -1;
+    int l = k + p;
+    if (l >= kk || l > lcap) {
+        orc_jacobi_svd(m, n, A, lda, -1.0, 60, S, U, m, V, n, NULL);
+        return kk;
+    }
+    orc_rsvd(m, n, A, lda, seed, index, l, q, U, S, V);
+    return l;
 }
 
 /* ---------------------------------------------------------------------------------------------

@@ -92,8 +92,28 @@ MUTANTS = [
      "orc_gemm(1, 0, l, n, m, Q, m, A, lda, B, l);", "orc_gemm(0, 0, l, n, m, Q, m, A, lda, B, l);"),
     ("gemm: op(B) transposed the wrong way", "oracle.c",
      "double b = tb ? AT(B, ldb, j, l) : AT(B, ldb, l, j);", "double b = tb ? AT(B, ldb, l, j) : AT(B, ldb, j, l);"),
+    ("adaptive: round accepted at eps instead of eps / 2", "oracle.c",
+     "if (est2 <= 0.25 * eps * eps * norm2) {", "if (est2 <= eps * eps * norm2) {"),
+    ("adaptive: probes drawn from the Omega stream", "oracle.c",
+     "orc_omega(seed, index, 1, n, 0, r, W);", "orc_omega(seed, index, 0, n, 0, r, W);"),
+    ("adaptive: probe residual without the singular values", "oracle.c",
+     "for (int c = 0; c < l; ++c) e -= AT(U, m, i, c) * S[c] * AT(VW, l, c, j);",
+     "for (int c = 0; c < l; ++c) e -= AT(U, m, i, c) * AT(VW, l, c, j);"),
+    ("adaptive: estimate not averaged over the probes", "oracle.c",
+     "return r > 0 ? sum / r : 0.0;", "return sum;"),
+    ("adaptive: sample grows by one column per round", "oracle.c", "            l += p;\n", "            l += 1;\n"),
+    ("adaptive: fallback only past min(m, n)", "oracle.c",
+     "} else if (l + p >= k || l + p > lcap) {", "} else if (l + p > k || l + p > lcap) {"),
+    ("budget: estimate added to the truncation budget", "oracle.c",
+     "double thr = 0.95 * 0.95 * eps * eps * normA2 - 4.0 * est2;",
+     "double thr = 0.95 * 0.95 * eps * eps * normA2 + 4.0 * est2;"),
+    ("fixed rank: full SVD only past min(m, n)", "oracle.c",
+     "    if (l >= kk || l > lcap) {", "    if (l > kk || l > lcap) {"),
     ("truncation: threshold not squared", "oracle.c", "double thr2 = thr * thr;", "double thr2 = thr;"),
-    ("truncation: rank one too high", "oracle.c", "        k = i;\n", "        k = i + 1;\n"),
+    ("truncation: rank one too high", "oracle.c", "if (t > thr2) break;\n        tail = t;\n        k = i;\n",
+     "if (t > thr2) break;\n        tail = t;\n        k = i + 1;\n"),
+    ("budget: rank one too high", "oracle.c", "if (t > thr) break;\n        tail = t;\n        k = i;\n",
+     "if (t > thr) break;\n        tail = t;\n        k = i + 1;\n"),
     # rank predictor (FP64 reference of the network and its features)
     ("MLP: loss without the factor 1/2", "mlp.py",
      "L = 0.5 * float(r @ r) / B", "L = float(r @ r) / B"),
