@@ -199,8 +199,10 @@ def block512_loguniform(batch: int = 500, first: int = 0, size: int = 512) -> Un
                          lambda i: sigma_loguniform(2, i, size), first=first, chunk=16)
 
 
-def rsvd_uneven_blocks(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: float = 1e-5) -> RaggedBatch:
-    """Uneven blocks: m, n iid uniform on ``sizes``; sigma_i = exp(-i/r0), r0 ~ U[2, 12].
+def rsvd_uneven_blocks(batch: int = 16384, first: int = 0, sizes=(64, 128, 256), eps: float = 1e-5,
+                       dtype=np.float32) -> RaggedBatch:
+    """Uneven blocks: m, n iid uniform on ``sizes``; sigma_i = exp(-i/r0), r0 ~ U[2, 12]; rounded to
+    ``dtype`` (FP32 for the workload; FP64 for the FP64 path's tests).
 
     ``extra['r0']`` holds r0 and ``extra['rank_hint']`` the rank at which sigma falls to
     ``eps`` relative, min(ceil(r0 ln(1/eps)), min(m, n)).
@@ -212,7 +214,7 @@ def rsvd_uneven_blocks(batch: int = 16384, first: int = 0, sizes=(64, 128, 256),
         ms.append(int(sizes[min(int(u[0] * len(sizes)), len(sizes) - 1)]))
         ns.append(int(sizes[min(int(u[1] * len(sizes)), len(sizes) - 1)]))
         r0s.append(2.0 + 10.0 * u[2])
-    off, flat = _pack(ms, ns, np.float32)
+    off, flat = _pack(ms, ns, dtype)
     sig = []
     for b, i in enumerate(range(first, first + batch)):
         m, n, r0 = ms[b], ns[b], r0s[b]
@@ -221,7 +223,7 @@ def rsvd_uneven_blocks(batch: int = 16384, first: int = 0, sizes=(64, 128, 256),
         v = _haar_stack(normals(3, i, TAG_V, n * k).reshape(n, k))
         s = sigma_decay(r0, k)
         a = (u * s) @ v.T
-        flat[off[b]:off[b] + m * n] = a.T.reshape(-1).astype(np.float32)
+        flat[off[b]:off[b] + m * n] = a.T.reshape(-1).astype(dtype)
         sig.append(s)
     hint = np.array([min(math.ceil(r0 * math.log(1.0 / eps)), min(m, n))
                      for m, n, r0 in zip(ms, ns, r0s)], dtype=np.int32)

@@ -50,6 +50,9 @@ extern "C" {
 #define BSVD_INFO_FALLBACK (1 << 22)      /* batched_rsvd: sampling did not pass, full SVD used */
 #define BSVD_INFO_DEVICE_TIMEOUT (-3)     /* a bounded on-device wait (tensor-core completion) gave up;
                                              the results of this call are not valid */
+#define BSVD_INFO_NONFINITE (-4)          /* the matrix holds a NaN or an infinity (seen in its column
+                                             norms, singular values or R's diagonal): its outputs are
+                                             not meaningful */
 
 /* Jacobi memory tiers (argument `tier` of batched_svd_jacobi).  `tier` may carry a variant in
    bits 8 and up: BSVD_TIER_REGISTER | (k << 8) forces the k-th register variant that fits the
@@ -123,11 +126,13 @@ int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier);
 
 /*
  * bsvd_jacobi_variant_desc -- describe the k-th (k >= 1) register-tier variant that fits a batch
- * bounded by max_m x max_n (the variant BSVD_TIER_REGISTER | (k << 8) launches).  desc (HOST, 7
+ * bounded by max_m x max_n (the variant BSVD_TIER_REGISTER | (k << 8) launches).  desc (HOST, 8
  * ints, caller-owned) receives {column-pair slots, row parts, rows of A per lane, rows of V per
- * lane, resident CTAs per SM, scaled rotations (0/1), QR preconditioning (0/1)}.  QR
- * preconditioning (square bounds only) factors A = Q R and runs the sweeps on R^T (the project's
- * addition; the paper runs them on A).  Returns 0, a negative argument code, or
+ * lane, resident CTAs per SM, scaled rotations (0/1), QR preconditioning (0/1), FP64 rotation
+ * parameters (0/1)}.  QR preconditioning (square bounds only) factors A = Q R and runs the sweeps
+ * on R^T (the project's addition; the paper runs them on A).  FP64 rotation parameters (FP32 data
+ * only) compute zeta, t, c, s and the rotation test in FP64 from the FP32 Gram sums; these
+ * variants are listed last.  Returns 0, a negative argument code, or
  * BSVD_ERR_UNSUPPORTED when there is no k-th variant.  Host only; launches nothing.
  */
 int bsvd_jacobi_variant_desc(int dtype, int max_m, int max_n, int k, int* desc);
@@ -150,6 +155,12 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
  * accumulation: FP32-level accuracy); this flag forms them with FP32 SIMT dot products instead
  * (the plain FP32 form).  The block updates run on the FP32 SIMT pipes either way. */
 #define BSVD_BLOCK_SIMT_PRODUCTS (1 << 16)
+/* Flag for `method`, for tests of the failure path only: in the tensor-core Gram (FP32, block
+ * width 32, without BSVD_BLOCK_SIMT_PRODUCTS) the first completion wait of each pair waits 1 ms on
+ * a barrier that nothing arrives at, as a tensor-core completion that never came would; the call
+ * then takes its timeout path (no further pairs, a bounded wait for the MMAs in flight before the
+ * tensor memory is freed) and every matrix gets BSVD_INFO_DEVICE_TIMEOUT.  No fault, no hang. */
+#define BSVD_BLOCK_TEST_TIMEOUT (1 << 17)
 
 /*
  * batched_svd_block_jacobi_workspace -- bytes of DEVICE workspace batched_svd_block_jacobi needs
@@ -172,6 +183,7 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *   block_width   bw = 16 or 32 columns per block (the paper uses 32, Section 6.3).
  *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
  *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
+ *                 | BSVD_BLOCK_TEST_TIMEOUT exercises the failure path (tests only; see the flag).
  *                 | BSVD_BLOCK_SIMT_PRODUCTS keeps the Gram products on the FP32 SIMT pipes (FP32
  *                 data with bw = 32 form them on the tensor cores otherwise).  | (s << 24) sets the sweep cap of
  *                 each pair visit's inner SVD: 1 <= s <= 126 sweeps, 127 = to convergence (as
@@ -179,7 +191,7 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *                 outer sweeps and errors; DIRECT: to convergence).  The outer sweeps continue
  *                 until no pair rotates either way.
  *                 DIRECT needs max(m, n) * 2 bw * sizeof(element) <= 200 KiB (the pair's QR runs on
- *                 chip); its default tol is 8 sqrt(max(m, n)) u, since its rotations are only as
+ *                 chip); its default tol is 4 sqrt(max(m, n)) u, since its rotations are only as
  *                 orthogonal as the pair's Householder Q.
  *   workspace     DEVICE buffer of at least batched_svd_block_jacobi_workspace(...) bytes, owned by
  *                 the caller, contents need not be initialised; not used after the stream work
@@ -202,41 +214,65 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n,
 /*
  * batched_rsvd_workspace -- bytes of DEVICE workspace for batched_rsvd.  h_m, h_n are optional
  * HOST arrays of the batch's sizes (exact size); NULL bounds every matrix by max_m x max_n.
+ * 0 for invalid arguments.
  */
 size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const int* h_m, const int* h_n);
 
 /*
- * batched_rsvd -- randomized truncated SVD of each matrix (Algorithm 4, Section 7) with one step
- * of randomized subspace iteration, truncated to a relative Frobenius tolerance (Section 8.2).
- * FP32 only (dtype BSVD_F32), m, n <= 256.
+ * batched_rsvd -- randomized SVD of each matrix (Algorithm 4, Section 7) with q steps of randomized
+ * subspace iteration (the robust variant Section 7 mentions), either at a fixed rank or truncated to
+ * a relative Frobenius tolerance (Section 8.2).  FP32 or FP64 (every stage in that precision,
+ * Gaussian samples included); m, n <= 256.
  *
- *   d_rank_hint[b] (nullable) first rank guess k0; the first round draws l = k0 + oversample
- *                  Gaussian columns (Philox4x32-10, counter (row/4, column, b, 0), key = seed).
- *                  NULL or 0 starts from l = oversample (a negative guess counts as 0, one above
- *                  256 as 256).  A guess with l >= min(m, n) (or > 128) sends the matrix straight
- *                  to the full Jacobi SVD.
- *   tol            eps: the result satisfies ||A - U S V^T||_F <= eps ||A||_F up to the posterior
- *                  estimate's error.  After each round, 8 probe columns (stream 1) give
+ *   d_rank[b]      (nullable) FIXED-RANK MODE when > 0: k = d_rank[b]; l = k + oversample Gaussian
+ *                  columns, `power_iters` power steps, one round, the first k columns of the rank-l
+ *                  factorisation are returned (Algorithm 4 as stated).  When k + oversample reaches
+ *                  min(m, n) or exceeds the sample cap (128 columns in FP32, 64 in FP64), the full
+ *                  Jacobi SVD replaces the sampling and its first k columns are returned.  NULL, 0
+ *                  or a negative value selects TOLERANCE MODE for that matrix.
+ *   d_rank_hint[b] (nullable, tolerance mode) first rank guess k0: the first round draws
+ *                  l = k0 + oversample columns (NULL or 0: l = oversample; negative counts as 0,
+ *                  above 256 as 256).  A guess with l >= min(m, n), or past the sample cap, sends
+ *                  the matrix straight to the full Jacobi SVD.
+ *   d_tol[b]       (nullable) per-matrix eps in [0, 1); NULL uses `tol` for every matrix.  A matrix
+ *                  whose eps is outside [0, 1) (or NaN) gets info BSVD_INFO_BAD_SHAPE.
+ *   tol            eps of every matrix when d_tol is NULL (must be in [0, 1)).  In tolerance mode the
+ *                  result satisfies ||A - U S V^T||_F <= eps ||A||_F up to the posterior estimate's
+ *                  error: after each round, 8 probe columns (Gaussian stream 1) give
  *                  est = ||(A - U_l S_l V_l^T) W||_F / sqrt(8); est <= eps/2 ||A||_F accepts the
  *                  round, otherwise the next round draws `oversample` more columns.  Past
- *                  max_rounds, or 128 columns, the matrix gets the full Jacobi SVD.
- *   The rank k is the smallest with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 - 4 est^2 (the
- *   estimate is trusted to a factor 2; 5% of eps is kept for the FP32 factorisation's residual).
- *   A matrix sent straight to the full SVD has est = 0 and 0 rounds.
+ *                  max_rounds, or the sample cap, the matrix gets the full Jacobi SVD (est = 0).
+ *                  The rank k is the smallest with sum_{i >= k} s_i^2 <= (0.95 eps)^2 ||A||_F^2 -
+ *                  4 est^2 (the estimate trusted to a factor 2; 5% of eps kept for the
+ *                  factorisation's own residual).
+ *   oversample     p in [1, 64];  power_iters q in [0, 8];  max_rounds in [1, 64].
+ *   seed           Omega(r, c) of matrix b is Philox4x32-10 at counter (r/4, c, b, 0), key = seed,
+ *                  through Box-Muller (the probes: counter (r/4, j, b, 1)).
+ *   flags          0, or BSVD_RSVD_SMALL_FP64 (FP32 runs; ignored in FP64): the small SVDs -- of the
+ *                  projected block's R_B^T and, for full-rank blocks with min(m, n) <= 64, of R^T
+ *                  -- run in FP64 when l <= 64 (operands widened, FP64 register tier, results
+ *                  narrowed to FP32), and with FP64 rotation parameters in the shared tier above
+ *                  (also for full-rank blocks with 64 < min(m, n) <= 128).  Other bits: argument
+ *                  error.
  *   dU[b] (m x kmax, ld d_ldu[b]), dS[b] (kmax), dV[b] (n x kmax, ld d_ldv[b]): the first k columns
  *                  and values are written; k > kmax writes kmax and flags BSVD_INFO_RANK_CAPPED.
- *   d_rank[b]      k;  d_err_est[b] (nullable) est / ||A||_F;  d_samples[b] (nullable) the number
- *                  of columns the result came from (l, or min(m, n) after a full SVD).
+ *   d_rank_out[b]  k;  d_err_est[b] (nullable) est / ||A||_F (also in fixed-rank mode; 0 after a
+ *                  full SVD);  d_samples[b] (nullable) the number of columns the result came from
+ *                  (l, or min(m, n) after a full SVD).
  *   d_info[b]      rounds run | BSVD_INFO_FALLBACK | BSVD_INFO_RANK_CAPPED, or BSVD_INFO_BAD_SHAPE
  *                  or BSVD_INFO_NO_SCRATCH (the matrix did not fit the workspace; nothing written).
- *   workspace      at least batched_rsvd_workspace(...) bytes (else BSVD_ERR_WORKSPACE).
+ *                  A matrix sent straight to the full SVD has 0 rounds.
+ *   workspace      at least batched_rsvd_workspace(...) bytes (else BSVD_ERR_WORKSPACE), caller-owned,
+ *                  contents need not be initialised.
  */
+#define BSVD_RSVD_SMALL_FP64 1 /* flags: FP32 runs take the small SVDs in FP64 (see batched_rsvd) */
+
 int batched_rsvd(int dtype, int batch, int max_m, int max_n,
                  void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
-                 const int* d_rank_hint, double tol, int oversample, int max_rounds,
-                 unsigned long long seed,
+                 const int* d_rank, const int* d_rank_hint, const double* d_tol, double tol,
+                 int oversample, int power_iters, int max_rounds, unsigned long long seed, int flags,
                  void* const* dU, const int* d_ldu, void* const* dS, void* const* dV, const int* d_ldv,
-                 const int* d_kmax, int* d_rank, float* d_err_est, int* d_samples, int* d_info,
+                 const int* d_kmax, int* d_rank_out, float* d_err_est, int* d_samples, int* d_info,
                  void* workspace, size_t workspace_bytes, void* stream);
 
 /*
@@ -291,7 +327,10 @@ int bsvd_mlp_param_count(void);
  *     rejected with BSVD_ERR_SCRATCH_LIMIT before anything is launched (for 512 x 512 FP32 with
  *     block width 32 that is about 250 matrices per call).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture.  Lookup failure
+ *     that device current; make that first call before any stream capture.  The address is kept
+ *     with the identifier of the context it was found in; a call in a new context of the device
+ *     (after cudaDeviceReset, or once the primary context was released and re-created) looks it up
+ *     again, so make the first call after such a reset before any capture too.  Lookup failure
  *     returns BSVD_ERR_CUDA.
  *   - Every call on a device uses the same array: calls whose GPU work overlaps (other streams,
  *     other host threads) race on it and must be serialised by the caller.  Each call writes every
@@ -304,6 +343,24 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
                                      void* const* dV, const int* d_ldv,
                                      double tol, int max_sweeps, int block_width, int method,
                                      int* d_info, long long* d_rotations, void* stream);
+
+/*
+ * Diagnostics (outside the method; for tests and the benchmark).
+ *
+ * bsvd_philox_gauss -- for each of `count` counters (d_ctr: 4 x count words, DEVICE) the
+ * Philox4x32-10 output words under key (seed low, seed high) to d_words (4 x count, nullable), and
+ * the four Gaussian samples the randomized SVD draws from that counter, read as (row / 4, column,
+ * matrix index, stream tag), in FP32 to d_gauss and in FP64 to d_gauss64 (4 x count each,
+ * nullable).  Returns 0 or a negative argument code; asynchronous on `stream`.
+ *
+ * bsvd_fma_probe -- launches `blocks` CTAs of 256 threads that each run `iters` x 16 independent
+ * fused multiply-adds in FP32 (dtype BSVD_F32) or FP64; d_out (DEVICE, blocks x 256 elements of
+ * dtype) receives the sums.  Returns the number of floating-point operations launched (2 per FMA),
+ * or a negative code.  Timing it with events on `stream` gives the pipe's peak throughput.
+ */
+int bsvd_philox_gauss(int count, const unsigned* d_ctr, unsigned long long seed, unsigned* d_words,
+                      float* d_gauss, double* d_gauss64, void* stream);
+long long bsvd_fma_probe(int dtype, int blocks, int iters, void* d_out, void* stream);
 
 /* Library version and build description (static strings). */
 const char* bsvd_version(void);

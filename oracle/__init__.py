@@ -151,6 +151,11 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return o
 
 
+def gauss(seed: int, index: int, tag: int, row: int, col: int) -> float:
+    """Entry (row, col) of Gaussian stream `tag` of matrix `index` under `seed`."""
+    return lib().orc_gauss(seed, index, tag, row, col)
+
+
 def omega(seed: int, index: int, tag: int, n: int, c0: int, cols: int) -> np.ndarray:
     """Columns c0 .. c0+cols-1 of the Gaussian sampling stream (n rows)."""
     o = np.zeros((n, cols), order="F")

@@ -28,7 +28,10 @@ INFO_NO_SCRATCH = -2
 INFO_RANK_CAPPED = 1 << 21
 INFO_FALLBACK = 1 << 22
 INFO_DEVICE_TIMEOUT = -3
+INFO_NONFINITE = -4
+RSVD_SMALL_FP64 = 1
 BLOCK_SIMT_PRODUCTS = 1 << 16
+BLOCK_TEST_TIMEOUT = 1 << 17
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -73,9 +76,13 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.c_size_t, p]
             L.batched_rsvd_workspace.restype = ctypes.c_size_t
             L.batched_rsvd_workspace.argtypes = [i, i, i, i, p, p]
+            L.bsvd_philox_gauss.restype = i
+            L.bsvd_philox_gauss.argtypes = [i, p, ctypes.c_ulonglong, p, p, p, p]
+            L.bsvd_fma_probe.restype = ctypes.c_longlong
+            L.bsvd_fma_probe.argtypes = [i, i, i, p, p]
             L.batched_rsvd.restype = i
-            L.batched_rsvd.argtypes = [i, i, i, i, p, p, p, p, p, d, i, i, ctypes.c_ulonglong, p, p, p, p, p, p, p,
-                                       p, p, p, p, ctypes.c_size_t, p]
+            L.batched_rsvd.argtypes = [i, i, i, i, p, p, p, p, p, p, p, d, i, i, i, ctypes.c_ulonglong, i, p, p, p,
+                                       p, p, p, p, p, p, p, p, ctypes.c_size_t, p]
             L.bsvd_sketch_features.restype = i
             L.bsvd_sketch_features.argtypes = [i, i, i, p, p, p, p, ctypes.c_ulonglong, p, p]
             L.bsvd_mlp_forward.restype = i
@@ -105,9 +112,10 @@ def jacobi_variants(dtype_code: int, max_m: int, max_n: int, tier: int) -> int:
 
 def jacobi_variant_desc(dtype_code: int, max_m: int, max_n: int, k: int) -> dict:
     """Shape parameters of the k-th (k >= 1) register-tier variant fitting max_m x max_n."""
-    d = (ctypes.c_int * 7)()
+    d = (ctypes.c_int * 8)()
     _check("bsvd_jacobi_variant_desc", lib().bsvd_jacobi_variant_desc(dtype_code, max_m, max_n, k, d))
-    return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond"), list(d)))
+    return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond", "fp64_params"),
+                    list(d)))
 
 
 def set_jacobi_choice(dtype_code: int, max_m: int, max_n: int, tier: int) -> None:
@@ -294,20 +302,49 @@ def batched_rsvd_workspace(A: Batch, h_m=None, h_n=None) -> int:
 
 def batched_rsvd(A: Batch, U: Batch, S: Batch, V: Batch, kmax, rank, info, workspace, rank_hint=None,
                  tol: float = 1e-5, oversample: int = 8, max_rounds: int = 4, seed: int = 0, err_est=None,
-                 samples=None, stream=None) -> None:
-    """Randomized truncated SVD (Algorithm 4 + one power step, adaptive); see include/bsvd.h."""
+                 samples=None, stream=None, fixed_rank=None, tol_per=None, power_iters: int = 1,
+                 flags: int = 0) -> None:
+    """Randomized SVD (Algorithm 4 + q power steps), fixed-rank (``fixed_rank`` > 0) or to a
+    tolerance (``tol``, or ``tol_per`` per matrix); see include/bsvd.h."""
     torch = _torch()
     for X, name in ((S, "S"), (U, "U"), (V, "V")):
         _same(X, A, name)
     nb, i32 = A.batch, torch.int32
     rc = lib().batched_rsvd(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n), _ptr(A.ld),
-                            _dptr(rank_hint, "rank_hint", i32, nb), float(tol), int(oversample), int(max_rounds),
-                            int(seed), _ptr(U.ptrs), _ptr(U.ld), _ptr(S.ptrs), _ptr(V.ptrs), _ptr(V.ld),
-                            _dptr(kmax, "kmax", i32, nb), _dptr(rank, "rank", i32, nb),
+                            _dptr(fixed_rank, "fixed_rank", i32, nb), _dptr(rank_hint, "rank_hint", i32, nb),
+                            _dptr(tol_per, "tol_per", torch.float64, nb), float(tol), int(oversample),
+                            int(power_iters), int(max_rounds), int(seed), int(flags), _ptr(U.ptrs), _ptr(U.ld),
+                            _ptr(S.ptrs),
+                            _ptr(V.ptrs), _ptr(V.ld), _dptr(kmax, "kmax", i32, nb), _dptr(rank, "rank", i32, nb),
                             _dptr(err_est, "err_est", torch.float32, nb), _dptr(samples, "samples", i32, nb),
                             _dptr(info, "info", i32, nb), _dptr(workspace, "workspace", torch.uint8),
                             int(workspace.numel()), _stream_ptr(stream))
     _check("batched_rsvd", rc)
+
+
+def philox_gauss(ctr, seed: int, stream=None):
+    """Generator access for tests: (words uint32 [count, 4], FP32 Gaussians [count, 4], FP64 Gaussians
+    [count, 4]) of the counters ``ctr`` (int64-compatible [count, 4]) under ``seed``."""
+    import numpy as np
+    torch = _torch()
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint64).reshape(-1, 4).astype(np.uint32).view(np.int32))
+    cnt = c.shape[0]
+    dev = torch.device("cuda")
+    cu = torch.from_numpy(c).to(dev).contiguous()
+    words = torch.zeros((cnt, 4), dtype=torch.int32, device=dev)
+    g = torch.zeros((cnt, 4), dtype=torch.float32, device=dev)
+    g64 = torch.zeros((cnt, 4), dtype=torch.float64, device=dev)
+    rc = lib().bsvd_philox_gauss(cnt, _ptr(cu), int(seed), _ptr(words), _ptr(g), _ptr(g64), _stream_ptr(stream))
+    _check("bsvd_philox_gauss", rc)
+    return words, g, g64
+
+
+def fma_probe(dtype_code: int, blocks: int, iters: int, out, stream=None) -> int:
+    """Launch the FMA throughput probe; returns the flops it performs."""
+    f = int(lib().bsvd_fma_probe(int(dtype_code), int(blocks), int(iters), _ptr(out), _stream_ptr(stream)))
+    if f < 0:
+        raise BsvdError("bsvd_fma_probe", f)
+    return f
 
 
 SKETCH_FEATURES = 16
@@ -365,10 +402,11 @@ class RsvdResult:
 
 
 def rsvd(flat, offsets, m, n, rank_hint=None, kmax=None, tol: float = 1e-5, oversample: int = 8,
-         max_rounds: int = 4, seed: int = 0, stream=None, workspace=None):
-    """Randomized SVD of matrices packed in ``flat`` (a device FP32 tensor) at element ``offsets``
-    with sizes ``m``, ``n`` (host sequences).  Allocates the outputs (kmax columns each, default
-    min(m, n)) and, unless given, the workspace."""
+         max_rounds: int = 4, seed: int = 0, stream=None, workspace=None, fixed_rank=None, tol_per=None,
+         power_iters: int = 1, flags: int = 0):
+    """Randomized SVD of matrices packed in ``flat`` (a device FP32 or FP64 tensor) at element
+    ``offsets`` with sizes ``m``, ``n`` (host sequences).  Allocates the outputs (kmax columns each,
+    default min(m, n)) and, unless given, the workspace."""
     import numpy as np
     torch = _torch()
     dev = flat.device
@@ -383,20 +421,25 @@ def rsvd(flat, offsets, m, n, rank_hint=None, kmax=None, tol: float = 1e-5, over
     ou = np.concatenate([[0], np.cumsum(su)[:-1]])
     ov = np.concatenate([[0], np.cumsum(sv)[:-1]])
     os_ = np.concatenate([[0], np.cumsum(ss)[:-1]])
-    fu = torch.zeros(int(su.sum()) + 4, device=dev)
-    fv = torch.zeros(int(sv.sum()) + 4, device=dev)
-    fs = torch.zeros(int(ss.sum()) + 4, device=dev)
+    fu = torch.zeros(int(su.sum()) + 4, device=dev, dtype=flat.dtype)
+    fv = torch.zeros(int(sv.sum()) + 4, device=dev, dtype=flat.dtype)
+    fs = torch.zeros(int(ss.sum()) + 4, device=dev, dtype=flat.dtype)
     A = Batch.packed(flat, offsets, m, n)
     U = Batch.packed(fu, ou, m, km)
     V = Batch.packed(fv, ov, n, km)
     S = Batch.packed(fs, os_, km, np.ones_like(km))
     kmax_d = torch.as_tensor(km, dtype=torch.int32).to(dev)
-    if rank_hint is None:
-        hint_d = None
-    elif isinstance(rank_hint, torch.Tensor):
-        hint_d = rank_hint.to(device=dev, dtype=torch.int32).contiguous()
-    else:
-        hint_d = torch.as_tensor(np.asarray(rank_hint, np.int32)).to(dev)
+
+    def dev_array(x, dtype):
+        if x is None:
+            return None
+        if isinstance(x, torch.Tensor):
+            return x.to(device=dev, dtype=dtype).contiguous()
+        return torch.as_tensor(np.asarray(x)).to(device=dev, dtype=dtype)
+
+    hint_d = dev_array(rank_hint, torch.int32)
+    fixed_d = dev_array(fixed_rank, torch.int32)
+    tol_d = dev_array(tol_per, torch.float64)
     rank = torch.zeros(bsz, dtype=torch.int32, device=dev)
     info = torch.zeros(bsz, dtype=torch.int32, device=dev)
     err = torch.zeros(bsz, dtype=torch.float32, device=dev)
@@ -404,7 +447,7 @@ def rsvd(flat, offsets, m, n, rank_hint=None, kmax=None, tol: float = 1e-5, over
     if workspace is None:
         workspace = torch.empty(batched_rsvd_workspace(A, m, n), dtype=torch.uint8, device=dev)
     batched_rsvd(A, U, S, V, kmax_d, rank, info, workspace, hint_d, tol, oversample, max_rounds, seed, err,
-                 samples, stream)
+                 samples, stream, fixed_rank=fixed_d, tol_per=tol_d, power_iters=power_iters, flags=flags)
     return RsvdResult(U=fu, V=fv, S=fs, off_u=ou, off_v=ov, off_s=os_, kmax=km, rank=rank, info=info, err_est=err,
                       samples=samples, workspace=workspace, m=m, n=n)
 

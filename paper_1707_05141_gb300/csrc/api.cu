@@ -186,8 +186,9 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
     if (!(tol == tol)) return -14;
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
-    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 24-30 inner sweep cap
-    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | (0x7f << 24))) return -17;
+    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
+    // 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | (0x7f << 24))) return -17;
     if (!d_info) return -18;
     if (!workspace) return -20;
     cudaStream_t st = (cudaStream_t)stream;
@@ -201,18 +202,21 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
 
 size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const int* h_m, const int* h_n)
 {
-    if (dtype != BSVD_F32 || batch < 0 || max_m < 0 || max_n < 0 || max_m > 256 || max_n > 256) return 0;
-    return rsvd_workspace(batch, max_m, max_n, h_m, h_n);
+    if ((dtype != BSVD_F32 && dtype != BSVD_F64) || batch < 0 || max_m < 0 || max_n < 0 || max_m > 256 ||
+        max_n > 256)
+        return 0;
+    return dtype == BSVD_F32 ? rsvd_workspace<float>(batch, max_m, max_n, h_m, h_n)
+                             : rsvd_workspace<double>(batch, max_m, max_n, h_m, h_n);
 }
 
 int batched_rsvd(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
-                 const int* d_lda, const int* d_rank_hint, double tol, int oversample, int max_rounds,
-                 unsigned long long seed, void* const* dU, const int* d_ldu, void* const* dS, void* const* dV,
-                 const int* d_ldv, const int* d_kmax, int* d_rank, float* d_err_est, int* d_samples, int* d_info,
-                 void* workspace, size_t workspace_bytes, void* stream)
+                 const int* d_lda, const int* d_rank, const int* d_rank_hint, const double* d_tol, double tol,
+                 int oversample, int power_iters, int max_rounds, unsigned long long seed, int flags, void* const* dU,
+                 const int* d_ldu, void* const* dS, void* const* dV, const int* d_ldv, const int* d_kmax,
+                 int* d_rank_out, float* d_err_est, int* d_samples, int* d_info, void* workspace,
+                 size_t workspace_bytes, void* stream)
 {
     if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
-    if (dtype != BSVD_F32) return BSVD_ERR_UNSUPPORTED;
     if (batch < 0) return -2;
     if (max_m < 0) return -3;
     if (max_n < 0) return -4;
@@ -222,21 +226,28 @@ int batched_rsvd(int dtype, int batch, int max_m, int max_n, void* const* dA, co
     if (!d_m) return -6;
     if (!d_n) return -7;
     if (!d_lda) return -8;
-    if (!(tol >= 0.0 && tol < 1.0)) return -10;
-    if (oversample < 1 || oversample > 64) return -11;
-    if (max_rounds < 1 || max_rounds > 64) return -12;
-    if (!dU) return -14;
-    if (!d_ldu) return -15;
-    if (!dS) return -16;
-    if (!dV) return -17;
-    if (!d_ldv) return -18;
-    if (!d_kmax) return -19;
-    if (!d_rank) return -20;
-    if (!d_info) return -23;
-    if (!workspace) return -24;
-    return launch_rsvd(batch, max_m, max_n, dA, d_m, d_n, d_lda, d_rank_hint, d_kmax, tol, oversample, max_rounds, seed,
-                       dU, d_ldu, dS, dV, d_ldv, d_rank, d_err_est, d_samples, d_info, workspace, workspace_bytes,
-                       (cudaStream_t)stream);
+    if (!(tol >= 0.0 && tol < 1.0)) return -12;
+    if (oversample < 1 || oversample > 64) return -13;
+    if (power_iters < 0 || power_iters > 8) return -14;
+    if (max_rounds < 1 || max_rounds > 64) return -15;
+    if (flags & ~(BSVD_RSVD_SMALL_FP64)) return -17;
+    if (!dU) return -18;
+    if (!d_ldu) return -19;
+    if (!dS) return -20;
+    if (!dV) return -21;
+    if (!d_ldv) return -22;
+    if (!d_kmax) return -23;
+    if (!d_rank_out) return -24;
+    if (!d_info) return -27;
+    if (!workspace) return -28;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32
+               ? launch_rsvd<float>(batch, max_m, max_n, dA, d_m, d_n, d_lda, d_rank, d_rank_hint, d_tol, tol, d_kmax,
+                                    oversample, power_iters, max_rounds, seed, flags, dU, d_ldu, dS, dV, d_ldv, d_rank_out,
+                                    d_err_est, d_samples, d_info, workspace, workspace_bytes, st)
+               : launch_rsvd<double>(batch, max_m, max_n, dA, d_m, d_n, d_lda, d_rank, d_rank_hint, d_tol, tol,
+                                     d_kmax, oversample, power_iters, max_rounds, seed, flags, dU, d_ldu, dS, dV, d_ldv,
+                                     d_rank_out, d_err_est, d_samples, d_info, workspace, workspace_bytes, st);
 }
 
 }  // extern "C"

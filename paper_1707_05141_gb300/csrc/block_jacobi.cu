@@ -349,14 +349,11 @@ __global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int
 // step ||X^T X - I|| is at the rounding level of one product.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int K2>
-__device__ __forceinline__ void bj_polish_item(int it, unsigned char* ws, const BjLayout& L, unsigned char* pol_sm)
+__device__ __forceinline__ void bj_polish_item(T* X, unsigned char* pol_sm)
 {
     constexpr int TPO = (K2 * K2) / 256;
     T(*xs)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm);                                  // X(r, c) at [c][r]
     T(*es)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm + sizeof(T) * K2 * (K2 + 1));      // X^T X - I
-    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
-    if (in[it] == 0) return;
-    T* X = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
     for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) xs[e / K2][e % K2] = X[e];
     __syncthreads();
     const int o0 = threadIdx.x * TPO;
@@ -384,17 +381,25 @@ __device__ __forceinline__ void bj_polish_item(int it, unsigned char* ws, const 
     for (int q = 0; q < TPO; ++q) acc[q] = xs[oc][or0 + q] - T(0.5) * acc[q];
 #pragma unroll
     for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = acc[q];
+    __syncthreads();  // the shared buffers are reused by the next item
 }
 
+// GRAM polishes the rotation X; DIRECT polishes both factors of R's SVD: V_R (the rotation of V)
+// and U_R (W <- Q U_R S_R), since W's columns are only as orthogonal as Q U_R
 template <typename T, int K2>
-__global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLayout L)
+__global__ void __launch_bounds__(256) bj_polish_kernel(unsigned char* ws, BjLayout L, int direct)
 {
     extern __shared__ __align__(16) unsigned char pol_sm[];
     BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
     const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
+    const int* in = reinterpret_cast<const int*>(ws + L.off_n);
     const long long items = C->pcount;
-    for (long long j = next_work(&C->claim[2]); j < items; j = next_work(&C->claim[2]))
-        bj_polish_item<T, K2>(plist[j], ws, L, pol_sm);
+    for (long long j = next_work(&C->claim[2]); j < items; j = next_work(&C->claim[2])) {
+        const int it = plist[j];
+        if (in[it] == 0) continue;
+        bj_polish_item<T, K2>(reinterpret_cast<T* const*>(ws + L.off_pX)[it], pol_sm);
+        if (direct) bj_polish_item<T, K2>(reinterpret_cast<T* const*>(ws + L.off_pUR)[it], pol_sm);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -606,7 +611,7 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
                                                 const int* LDU, float* const* V, const int* LDV, const int* M,
                                                 const int* N, unsigned char* ws, const BjLayout& L, double tol,
                                                 unsigned char* sm, uint32_t tmem, uint64_t* bars,
-                                                uint32_t& phase, uint32_t& used, BjCounters* C)
+                                                uint32_t& phase, uint32_t& used, BjCounters* C, uint64_t* never)
 {
     constexpr int K2 = 64;
     __shared__ float gd[K2];
@@ -668,7 +673,9 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
             for (int j = 0; j < kUnits; ++j) nxt[j] = load_unit(j, c + 1);
         }
         if (c >= kTcGramStages) {  // the MMAs of chunk c - 3 read this stage
-            if (ok) ok = tc::mbar_wait(&bars[s], (phase >> s) & 1u);  // after a failure: no more waits
+            // after a failure: no more waits.  `never` (failure-path test only) is a barrier nothing
+            // arrives at, waited for 1 ms: the wait runs out, and the call takes its timeout path
+            if (ok) ok = never ? tc::mbar_wait(never, 0u, 1000000ull) : tc::mbar_wait(&bars[s], (phase >> s) & 1u);
             phase ^= 1u << s;
         }
 #pragma unroll
@@ -796,10 +803,11 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
 __global__ void __launch_bounds__(128) bj_gram_tc_kernel(int npairs, int step, int bw, float* const* U,
                                                          const int* LDU, float* const* V, const int* LDV,
                                                          const int* M, const int* N, unsigned char* ws, BjLayout L,
-                                                         double tol)
+                                                         double tol, int test_timeout)
 {
     extern __shared__ __align__(16) unsigned char tc_raw[];
     __shared__ uint64_t bars[kTcGramStages];
+    __shared__ uint64_t never_bar;  // failure-path test: a barrier nothing arrives at
     __shared__ uint32_t tmem_slot;
     unsigned char* sm = align1k(tc_raw);
     BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
@@ -809,6 +817,7 @@ __global__ void __launch_bounds__(128) bj_gram_tc_kernel(int npairs, int step, i
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcGramStages; ++s) tc::mbar_init(&bars[s], 1);
+        tc::mbar_init(&never_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before_sync();
@@ -821,7 +830,7 @@ __global__ void __launch_bounds__(128) bj_gram_tc_kernel(int npairs, int step, i
     for (long long j = tc_next(C, 0); j < items; j = tc_next(C, 0)) {
         const int b = mlist[j / npairs], k = (int)(j % npairs);
         bj_gram_tc_item(b * npairs + k, npairs, step, bw, U, LDU, V, LDV, M, N, ws, L, tol, sm, tmem, bars, phase,
-                        used, C);
+                        used, C, test_timeout ? &never_bar : nullptr);
     }
     // after a wait that gave up (in any CTA of the call) this CTA's MMAs may still be in flight:
     // wait once more, again bounded, for the last commit of every stage it used before its tensor
@@ -897,6 +906,11 @@ __global__ void __launch_bounds__(256) bj_finalize_kernel(int batch, T* const* S
         if (lane == 0) sig[j] = dsqrt(s);
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        bool finite = true;
+        for (int j = 0; j < nn; ++j) finite = finite && isfinite(sig[j]);
+        if (!finite) info[b] = BSVD_INFO_NONFINITE;
+    }
     for (int j = threadIdx.x; j < nn; j += blockDim.x) {
         // rank in a total order (a NaN ranks last), so that dest is always a permutation
         const T sj = sig[j] == sig[j] ? sig[j] : T(-1);
@@ -963,6 +977,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     int inner_variant = (method >> 8) & 0xff;  // register-tier variant of the inner SVD (0: see below)
     const int cap_bits = (method >> 24) & 0x7f;
     const bool simt = (method & BSVD_BLOCK_SIMT_PRODUCTS) != 0;
+    const int test_timeout = (method & BSVD_BLOCK_TEST_TIMEOUT) != 0 ? 1 : 0;
     method &= 0xff;
     const bool direct = method != 0;
     // sweep cap of each inner SVD: 127 = to convergence (as Algorithm 3 states), 0 = default.
@@ -977,7 +992,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     // the SVD of R and keeps the first plain variant.
     bool inner_u = false;
     if (!direct && inner_variant == 0) {
-        int d[7];
+        int d[8];
         for (int k = 1; jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, k, d) == BSVD_SUCCESS; ++k)
             if (d[6]) {
                 inner_variant = k;
@@ -985,15 +1000,16 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                 break;
             }
     } else if (!direct) {
-        int d[7];
+        int d[8];
         inner_u = jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, inner_variant, d) == BSVD_SUCCESS && d[6];
     }
     const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
     const int npairs = L.npairs, nbp = 2 * npairs;
     // default pair threshold sqrt(m) u; DIRECT rotations are only as orthogonal as the pair's
-    // Householder Q (~ 2bw u), so its default sits 8x higher
-    const double tol_outer = tol > 0.0 ? tol : (direct ? 8.0 : 1.0) * sqrt((double)mm) * Unit<T>::value;
+    // Householder Q (~ 2bw u), so its default sits 4x higher (U's orthogonality at convergence is
+    // the threshold: 4 sqrt(512) u = 5.4e-6 in FP32)
+    const double tol_outer = tol > 0.0 ? tol : (direct ? 4.0 : 1.0) * sqrt((double)mm) * Unit<T>::value;
     BjCounters* ctr = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
     if (cudaMemsetAsync(ctr, 0, sizeof(BjCounters), st) != cudaSuccess) return BSVD_ERR_CUDA;
     bj_setup_kernel<T><<<batch, 256, 0, st>>>(batch, mm, nn, bw, npairs, (T* const*)A, M, N, LDA, (T* const*)U, LDU,
@@ -1054,7 +1070,8 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
             if (cudaMemsetAsync(ctr, 0, kStepCounterBytes, st) != cudaSuccess) return BSVD_ERR_CUDA;
             if (tc_gram)
                 bj_gram_tc_kernel<<<g_gram_tc, 128, kTcGramSmem, st>>>(npairs, step, bw, (float* const*)U, LDU,
-                                                                      (float* const*)V, LDV, M, N, ws, L, tol_outer);
+                                                                      (float* const*)V, LDV, M, N, ws, L, tol_outer,
+                                                                      test_timeout);
             else
                 bj_gram_kernel<T, K2><<<g_gram, 256, 0, st>>>(batch, npairs, step, bw, (T* const*)U, LDU,
                                                               (T* const*)V, LDV, M, N, ws, L, tol_outer);
@@ -1076,7 +1093,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                                           ItemList{pairs.idx, pairs.count, &ctr->claim[5]});
                 if (rc != BSVD_SUCCESS) return rc;
             }
-            bj_polish_kernel<T, K2><<<g_polish, 256, polish_smem, st>>>(ws, L);
+            bj_polish_kernel<T, K2><<<g_polish, 256, polish_smem, st>>>(ws, L, direct ? 1 : 0);
             bj_update_kernel<T, K2><<<g_update, 256, upd_smem, st>>>(tiles, npairs, step, bw, direct ? 1 : 0,
                                                                      (T* const*)U, LDU, (T* const*)V, LDV, M, N, ws, L);
             if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;

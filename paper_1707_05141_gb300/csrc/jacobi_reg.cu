@@ -34,6 +34,8 @@
 // about one sweep (the factorisation and the back-transformation).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "launch.cuh"
 
@@ -47,7 +49,7 @@ struct Red3 {
 // MINB is the number of matrices (CTAs) the launch bound asks to keep resident per SM; it caps
 // the register allocation at 65536 / (NS * PARTS * MINB), trading scheduling freedom against
 // occupancy.  Several values are instantiated and the autotuner picks one per size bin.
-template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE>
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64>
 __global__ void __launch_bounds__(NS * PARTS, MINB)
     jacobi_reg_kernel(int batch, T* const* A, const int* M, const int* N, const int* LDA, T* const* Sout, T* const* U,
                       const int* LDU, T* const* V, const int* LDV, double tol_in, int max_sweeps, int* info,
@@ -58,7 +60,9 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
     constexpr int NW = NT / 32;    // warps per matrix
     constexpr int NC = 2 * NS;     // column capacity
     static_assert(NT % 32 == 0, "whole warps only");
-    typedef T P;                   // rotation parameters in the working precision
+    // rotation parameters (zeta, t, c, s) and the rotation test in the working precision, or in
+    // FP64 for FP32 data (P64): the Gram entries are summed in T, then promoted
+    typedef typename std::conditional<P64, double, T>::type P;
 
     __shared__ Red3<T> red[2][NW > 1 ? NW : 1][32];
     __shared__ T sig_s[NC];
@@ -492,50 +496,57 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
             }
         }
         if (tid == 0) {
-            info[b] = converged ? sweep : BSVD_INFO_NOT_CONVERGED + sweep;
+            bool finite = true;
+            for (int i = 0; i < nn; ++i) finite = finite && isfinite(sig_s[i]);
+            info[b] = !finite ? BSVD_INFO_NONFINITE : (converged ? sweep : BSVD_INFO_NOT_CONVERGED + sweep);
             if (rot_out) rot_out[b] = total_rot;
         }
         __syncthreads();
     }
 }
 
-template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE>
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64>
 static int launch_reg(int batch, void* const* A, const int* M, const int* N, const int* LDA, void* const* S,
                       void* const* U, const int* LDU, void* const* V, const int* LDV, double tol, int max_sweeps,
                       int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
-    const int grid = item_grid(jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST, PRE>, NS * PARTS, 0, wl, batch, st);
+    auto kern = jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST, PRE, P64 && sizeof(T) == 4>;
+    const int grid = item_grid(kern, NS * PARTS, 0, wl, batch, st);
     if (grid == 0) return BSVD_ERR_CUDA;
-    jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST, PRE><<<grid, NS * PARTS, 0, st>>>(
+    kern<<<grid, NS * PARTS, 0, st>>>(
         batch, (T* const*)A, M, N, LDA, (T* const*)S, (T* const*)U, LDU, (T* const*)V, LDV, tol, max_sweeps, info, rot,
         wl);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 
 // Register-tier variants (slots, row parts, A rows per lane, V rows per lane, resident CTAs, scaled
-// rotations, QR preconditioning), in order of preference.  `variant` 0 launches the first that fits
-// the shape bound; k > 0 launches the k-th fitting one; a negative `variant` only counts the
-// fitting ones (returned).  The preconditioned ones need square bounds and are listed last, so
-// that variant 0 stays unpreconditioned.
+// rotations, QR preconditioning, FP64 rotation parameters), in order of preference.  `variant` 0
+// launches the first that fits the shape bound; k > 0 launches the k-th fitting one; a negative
+// `variant` only counts the fitting ones (returned).  The preconditioned ones need square bounds
+// and are listed after the plain ones, so that variant 0 stays unpreconditioned; the FP32 variants
+// with FP64 rotation parameters (zeta, t, c, s and the rotation test in FP64, the data and the Gram
+// sums in FP32) come last.
 #define BSVD_REG_VARIANTS_F32(X)                                                                        \
-    X(16, 2, 16, 16, 16, true, false) /* n <= 32, m <= 32: one warp per matrix */                       \
-    X(16, 2, 32, 16, 12, true, false) /* n <= 32, m <= 64 */                                            \
-    X(32, 2, 32, 32, 6, true, false)  /* n <= 64, m <= 64: two warps, 3 warps per SM sub-partition */   \
-    X(32, 2, 32, 32, 4, true, false)  /*   ... 2 warps per sub-partition, no register cap */            \
-    X(32, 2, 32, 32, 6, false, false) /*   ... rotations applied as written */                          \
-    X(32, 4, 16, 16, 4, true, false)  /*   ... four warps, 128-register cap */                          \
-    X(16, 4, 32, 8, 4, true, false)   /* n <= 32, m <= 128 */                                           \
-    X(32, 4, 32, 16, 2, true, false)  /* n <= 64, m <= 128 */                                           \
-    X(16, 2, 16, 16, 16, true, true)  /* 32 x 32, QR-preconditioned */                                  \
-    X(32, 2, 32, 32, 6, true, true)   /* 64 x 64, QR-preconditioned */
+    X(16, 2, 16, 16, 16, true, false, false) /* n <= 32, m <= 32: one warp per matrix */                \
+    X(16, 2, 32, 16, 12, true, false, false) /* n <= 32, m <= 64 */                                     \
+    X(32, 2, 32, 32, 6, true, false, false)  /* n <= 64, m <= 64: two warps, 3 warps per SMSP */        \
+    X(32, 2, 32, 32, 4, true, false, false)  /*   ... 2 warps per sub-partition, no register cap */     \
+    X(32, 2, 32, 32, 6, false, false, false) /*   ... rotations applied as written */                   \
+    X(32, 4, 16, 16, 4, true, false, false)  /*   ... four warps, 128-register cap */                   \
+    X(16, 4, 32, 8, 4, true, false, false)   /* n <= 32, m <= 128 */                                    \
+    X(32, 4, 32, 16, 2, true, false, false)  /* n <= 64, m <= 128 */                                    \
+    X(16, 2, 16, 16, 16, true, true, false)  /* 32 x 32, QR-preconditioned */                           \
+    X(32, 2, 32, 32, 6, true, true, false)   /* 64 x 64, QR-preconditioned */                           \
+    X(32, 2, 32, 32, 6, true, false, true)   /* n <= 64, m <= 64, FP64 rotation parameters */           \
+    X(32, 2, 32, 32, 6, true, true, true)    /* 64 x 64, QR-preconditioned, FP64 rotation parameters */
 #define BSVD_REG_VARIANTS_F64(X)                                                                        \
-    X(16, 2, 16, 16, 8, true, false)  /* n <= 32, m <= 32: one warp per matrix */                       \
-    X(16, 2, 16, 16, 8, false, false)                                                                   \
-    X(16, 2, 16, 16, 12, true, false)                                                                   \
-    X(16, 4, 16, 8, 5, true, false)   /* n <= 32, m <= 64 */                                            \
-    X(32, 4, 16, 16, 2, true, false)  /* n <= 64, m <= 64 */                                            \
-    X(16, 2, 16, 16, 8, true, true)   /* 32 x 32, QR-preconditioned */                                  \
-    X(32, 4, 16, 16, 2, true, true)   /* 64 x 64, QR-preconditioned */
+    X(16, 2, 16, 16, 8, true, false, false)  /* n <= 32, m <= 32: one warp per matrix */                \
+    X(16, 2, 16, 16, 8, false, false, false)                                                            \
+    X(16, 2, 16, 16, 12, true, false, false)                                                            \
+    X(16, 4, 16, 8, 5, true, false, false)   /* n <= 32, m <= 64 */                                     \
+    X(32, 4, 16, 16, 2, true, false, false)  /* n <= 64, m <= 64 */                                     \
+    X(16, 2, 16, 16, 8, true, true, false)   /* 32 x 32, QR-preconditioned */                           \
+    X(32, 4, 16, 16, 2, true, true, false)   /* 64 x 64, QR-preconditioned */
 
 #define BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_) \
     (nn <= 2 * (NS_) && mm <= (PARTS_) * (RA_) && nn <= (PARTS_) * (RV_) && (!(PRE_) || max_m == max_n))
@@ -548,12 +559,12 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
     const int mm = max_m > max_n ? max_m : max_n;
     const int nn = max_m > max_n ? max_n : max_m;
     int seen = 0;
-#define BSVD_TRY(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_)                                                      \
+#define BSVD_TRY(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_)                                               \
     if (BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_)) {                                                               \
         ++seen;                                                                                             \
         if (variant == 0 || variant == seen)                                                                \
-            return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_>(batch, A, M, N, LDA, S, U, LDU, V, LDV,   \
-                                                                     tol, max_sweeps, info, rot, st, wl);    \
+            return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_>(batch, A, M, N, LDA, S, U, LDU, V, \
+                                                                           LDV, tol, max_sweeps, info, rot, st, wl); \
     }
     if constexpr (sizeof(T) == 4) {
         BSVD_REG_VARIANTS_F32(BSVD_TRY)
@@ -565,18 +576,18 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
 }
 
 // The k-th (k >= 1) register-tier variant fitting the bounds: desc = {slots, parts, A rows per
-// lane, V rows per lane, resident CTAs, scaled rotations, QR preconditioning}; 0, or
-// BSVD_ERR_UNSUPPORTED when there is no k-th variant.
+// lane, V rows per lane, resident CTAs, scaled rotations, QR preconditioning, FP64 rotation
+// parameters}; 0, or BSVD_ERR_UNSUPPORTED when there is no k-th variant.
 int jacobi_reg_variant_desc(bool f64, int max_m, int max_n, int k, int* desc)
 {
     const int mm = max_m > max_n ? max_m : max_n;
     const int nn = max_m > max_n ? max_n : max_m;
     int seen = 0;
-#define BSVD_DESC(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_)                                   \
-    if (BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_) && ++seen == k) {                             \
-        const int d[7] = {NS_, PARTS_, RA_, RV_, MINB_, (FAST_) ? 1 : 0, (PRE_) ? 1 : 0};  \
-        for (int i = 0; i < 7; ++i) desc[i] = d[i];                                          \
-        return BSVD_SUCCESS;                                                                 \
+#define BSVD_DESC(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_)                                        \
+    if (BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_) && ++seen == k) {                                        \
+        const int d[8] = {NS_, PARTS_, RA_, RV_, MINB_, (FAST_) ? 1 : 0, (PRE_) ? 1 : 0, (P64_) ? 1 : 0}; \
+        for (int i = 0; i < 8; ++i) desc[i] = d[i];                                                     \
+        return BSVD_SUCCESS;                                                                            \
     }
     if (!f64) {
         BSVD_REG_VARIANTS_F32(BSVD_DESC)

@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(64 * G > 1024 ? 1024 : 64 * G) jacobi_smem_ker
             }
         }
         if (tid == 0) {
-            info[b] = converged ? sweep : BSVD_INFO_NOT_CONVERGED + sweep;
+            bool finite = true;
+            for (int i = 0; i < nn; ++i) finite = finite && isfinite(sig[i]);
+            info[b] = !finite ? BSVD_INFO_NONFINITE : (converged ? sweep : BSVD_INFO_NOT_CONVERGED + sweep);
             if (rot_out) rot_out[b] = total_rot;
         }
         __syncthreads();
@@ -226,7 +228,7 @@ static int launch_g(int batch, int max_mm, int max_np, void* const* A, const int
 template <typename T>
 int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
-                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl)
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl, bool p64)
 {
     const int max_mm = max_m > max_n ? max_m : max_n;
     const int max_nn = max_m > max_n ? max_n : max_m;
@@ -239,9 +241,12 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
     int g = 1;
     while (g * 16 < max_mm) g *= 2;
     if ((max_np / 2) * g > 1024) return BSVD_ERR_UNSUPPORTED;
-#define BSVD_LAUNCH_G(GG) \
-    return launch_g<T, T, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info, rot, st, \
-                              wl)
+#define BSVD_LAUNCH_G(GG)                                                                                          \
+    return p64 && sizeof(T) == 4                                                                                   \
+               ? launch_g<T, double, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, \
+                                             info, rot, st, wl)                                                   \
+               : launch_g<T, T, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info,  \
+                                        rot, st, wl)
     switch (g) {
         case 1: BSVD_LAUNCH_G(1);
         case 2: BSVD_LAUNCH_G(2);
@@ -254,9 +259,9 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
 
 template int launch_jacobi_smem<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
                                        void* const*, const int*, void* const*, const int*, double, int, int*,
-                                       long long*, cudaStream_t, ItemList);
+                                       long long*, cudaStream_t, ItemList, bool);
 template int launch_jacobi_smem<double>(int, int, int, void* const*, const int*, const int*, const int*,
                                         void* const*, void* const*, const int*, void* const*, const int*, double, int,
-                                        int*, long long*, cudaStream_t, ItemList);
+                                        int*, long long*, cudaStream_t, ItemList, bool);
 
 }  // namespace bsvd

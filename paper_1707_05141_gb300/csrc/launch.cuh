@@ -24,7 +24,8 @@ int jacobi_reg_variant_desc(bool f64, int max_m, int max_n, int k, int* desc);
 template <typename T>
 int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
-                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl = all_items());
+                       int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl = all_items(),
+                       bool p64 = false);  // p64: FP32 data, FP64 rotation parameters
 template <typename T>
 size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
 template <typename T>
@@ -32,10 +33,13 @@ int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, voi
                         const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
                         const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
                         cudaStream_t st);
+template <typename T>
 size_t rsvd_workspace(int batch, int max_m, int max_n, const int* h_m, const int* h_n);
+template <typename T>
 int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
-                const int* hint, const int* kmax, double eps, int p, int rounds, unsigned long long seed,
-                void* const* dU, const int* LDU, void* const* dS, void* const* dV, const int* LDV, int* rank_out,
-                float* err_est, int* samples, int* info, void* ws, size_t ws_bytes, cudaStream_t st);
+                const int* fixed, const int* hint, const double* tol_arr, double tol, const int* kmax, int p, int q,
+                int rounds, unsigned long long seed, int flags, void* const* dU, const int* LDU, void* const* dS,
+                void* const* dV, const int* LDV, int* rank_out, float* err_est, int* samples, int* info, void* ws,
+                size_t ws_bytes, cudaStream_t st);
 
 }  // namespace bsvd

@@ -9,7 +9,11 @@
 // The array is a file-scope __device__ object: every GPU that loads this library holds it until
 // the process exits.  In host code its name is only a stand-in, not a device address, so the
 // first call on each device, with that device current, looks the address up with
-// cudaGetSymbolAddress and remembers it for that device.
+// cudaGetSymbolAddress and remembers it for that device, together with the identifier of the
+// context it belongs to.  A later call in another context of that device (after cudaDeviceReset,
+// or a primary context released and created again) looks the address up again instead of using
+// a stale one.
+#include <cuda.h>  // context types only; the driver functions are reached through the runtime
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,18 +37,51 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_addr[kMaxDevices];  // device address of g_scratch on each device, once looked up
+void* g_addr[kMaxDevices];                 // device address of g_scratch on each device, once looked up
+unsigned long long g_ctx_id[kMaxDevices];  // identifier of the context that address belongs to
 
-// Device address of the scratch array on the current device (nullptr on failure).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Identifier of the calling thread's current context (unique for the life of the process), or 0
+// when there is none or it cannot be read.  Called with g_mu held.
+unsigned long long current_context_id()
+{
+    static bool resolved = false;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!resolved) {
+        resolved = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    return get_id(c, &id) == CUDA_SUCCESS ? id : 0;
+}
+
+// Device address of the scratch array on the current device (nullptr on failure).  Looked up once
+// per device and context; when the context identifier cannot be read, looked up on every call.
 void* scratch_address()
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return nullptr;
         g_addr[dev] = p;
+        g_ctx_id[dev] = current_context_id();  // the lookup makes the device's primary context current
     }
     return g_addr[dev];
 }
@@ -75,8 +112,9 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
     if (!(tol == tol)) return -14;
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
-    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 24-30 inner sweep cap
-    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | (0x7f << 24))) return -17;
+    // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
+    // 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | (0x7f << 24))) return -17;
     if (!d_info) return -18;
     const size_t need = dtype == BSVD_F32
                             ? bsvd::block_jacobi_workspace<float>(batch, max_m, max_n, block_width, method & 0xff)

@@ -44,6 +44,22 @@ __device__ __forceinline__ float4 gauss4(unsigned long long seed, uint32_t index
     return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
 }
 
+// the same four normals in FP64 (the FP64 randomized SVD): uniforms exact in double, double log
+// and sin / cos
+__device__ __forceinline__ double4 gauss4d(unsigned long long seed, uint32_t index, uint32_t tag, uint32_t g,
+                                           uint32_t c)
+{
+    const uint4 w = philox4x32_10(make_uint4(g, c, index, tag), (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double s32 = 2.3283064365386963e-10;  // 2^-32
+    const double ua = ((double)w.x + 0.5) * s32, ub = ((double)w.y + 0.5) * s32;
+    const double uc = ((double)w.z + 0.5) * s32, ud = ((double)w.w + 0.5) * s32;
+    const double r0 = sqrt(-2.0 * log(ua)), r1 = sqrt(-2.0 * log(uc));
+    double s0, c0, s1, c1;
+    sincospi(2.0 * ub, &s0, &c0);
+    sincospi(2.0 * ud, &s1, &c1);
+    return make_double4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
 __device__ __forceinline__ float gauss1(unsigned long long seed, uint32_t index, uint32_t tag, uint32_t r, uint32_t c)
 {
     const float4 z = gauss4(seed, index, tag, r >> 2, c);

@@ -56,6 +56,11 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
 
         // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
         house_factor_smem(S, ld, diag, m, n);
+        if (tid == 0) {  // a NaN or infinity anywhere in A reaches the norm of its column's reflector
+            bool finite = true;
+            for (int i = 0; i < n; ++i) finite = finite && isfinite(diag[i]);
+            if (!finite) info[b] = BSVD_INFO_NONFINITE;
+        }
 
         // ---- R: strict upper part from S, diagonal from diag, zeros below ----
         if (R) {

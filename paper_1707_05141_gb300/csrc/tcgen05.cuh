@@ -149,15 +149,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Wait until the phase of `parity` has completed; false if it did not within 2 s of global time
-// (or 2^26 polls), so that a wait that can never end returns instead of hanging the GPU.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Wait until the phase of `parity` has completed; false if it did not within limit_ns of global
+// time (2 s by default; or 2^26 polls), so that a wait that can never end returns instead of
+// hanging the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = 2000000000ull)
 {
     if (mbar_test_parity(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (int i = 0; i < (1 << 26); ++i) {
         if (mbar_test_parity(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > 2000000000ull) break;
+        if (globaltimer_ns() - t0 > limit_ns) break;
     }
     return false;
 }

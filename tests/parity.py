@@ -49,20 +49,22 @@ def svd_errors(a64, u, s, v, s_ref):
     return out
 
 
-def vector_errors(x, x_ref, s_ref, dtype, c: float = 64.0):
+def vector_errors(x, x_ref, s_ref, dtype, c: float = 64.0, s_all=None):
     """Columns of x vs x_ref after sign alignment, each within c * u * s_1 / gap_j.
 
     Returns the worst ratio (error / allowed); <= 1 passes.  Columns whose gap is zero (repeated
-    singular values) are skipped: only their span is unique.
+    singular values) are skipped: only their span is unique.  ``s_all`` (default s_ref) is the full
+    list the gaps are measured in, when x holds only the leading columns of a factorisation.
     """
     x = np.asarray(x, np.float64)
     x_ref = np.asarray(x_ref, np.float64)
     s_ref = np.asarray(s_ref, np.float64)
+    s_all = s_ref if s_all is None else np.asarray(s_all, np.float64)
     k = s_ref.size
     worst = 0.0
     u = unit(dtype)
     for j in range(k):
-        others = np.delete(s_ref, j)
+        others = np.delete(s_all, j)
         gap = np.abs(others - s_ref[j]).min() if others.size else s_ref[0]
         if gap <= 0 or s_ref[j] <= 0:
             continue

@@ -66,7 +66,7 @@ def test_host_argument_checks_without_gpu(lib):
     # block Jacobi: unknown `method` bits are refused before anything is launched (the pointers
     # are never dereferenced: the checks return first)
     p = 64
-    for bad in (1 << 17, 1 << 20, 2, -(1 << 30)):
+    for bad in (1 << 18, 1 << 20, 2, -(1 << 30)):
         assert L.batched_svd_block_jacobi(0, 1, 64, 64, p, p, p, p, p, p, p, p, p, 0.0, 0, 32, bad, p, z, p, 1 << 20,
                                           z) == -17, bad
 
@@ -88,13 +88,16 @@ def test_variant_counts_and_tuning_table(lib):
 
 def test_variant_descriptions(lib):
     """The k-th fitting register variant's shape; QR preconditioning only for square bounds, and
-    listed after every unpreconditioned variant (so variant 0 -- the first -- never has it)."""
+    listed after every unpreconditioned variant (so variant 0 -- the first -- never has it); the
+    FP64-rotation-parameter variants (FP32 only) come after all the others."""
     _, bs = lib
     L = bs.lib()
     for code, (m, n) in [(0, (64, 64)), (0, (32, 32)), (1, (32, 32)), (1, (64, 64)), (0, (128, 48)), (1, (64, 60))]:
         nv = L.bsvd_jacobi_variants(code, m, n, bs.TIER_REGISTER)
         descs = [bs.jacobi_variant_desc(code, m, n, k) for k in range(1, nv + 1)]
-        pre = [d["qr_precond"] for d in descs]
+        p64 = [d["fp64_params"] for d in descs]
+        assert p64 == sorted(p64) and (code == 0 or not any(p64)), (code, m, n, p64)
+        pre = [d["qr_precond"] for d in descs if not d["fp64_params"]]
         assert pre == sorted(pre), (code, m, n, pre)             # preconditioned ones last
         assert any(pre) == (m == n), (code, m, n, pre)
         for d in descs:                                          # every one fits the bounds
@@ -103,7 +106,7 @@ def test_variant_descriptions(lib):
         with pytest.raises(bs.BsvdError):
             bs.jacobi_variant_desc(code, m, n, nv + 1)
     import ctypes
-    d = (ctypes.c_int * 7)()
+    d = (ctypes.c_int * 8)()
     assert L.bsvd_jacobi_variant_desc(2, 64, 64, 1, d) == -1
     assert L.bsvd_jacobi_variant_desc(0, -1, 64, 1, d) == -2
     assert L.bsvd_jacobi_variant_desc(0, 64, 64, 0, d) == -4

@@ -45,14 +45,9 @@ def test_block_512_log_uniform_sigma(bs, w2, method, bw):
     for i in range(b.batch):
         assert 0 < info[i] < (1 << 20), (i, info[i])
         e = svd_errors(mats[i], u[i].T, s[i], v[i].T, So[i])
-        if method == 0:
-            # GRAM: every gate at 1e-5, U's orthogonality over all columns down to sigma = 1e-6
-            assert max(e.values()) <= 1e-5, (i, e)
-        else:
-            # DIRECT: a rotation is only as orthogonal as the pair's Householder Q (~ 2bw u), which
-            # bounds U's orthogonality a little above the gate; the other gates hold
-            assert e["sigma"] <= 1e-5 and e["orth_v"] <= 1e-5 and e["resid"] <= 1e-5, (i, e)
-            assert e["orth_u"] <= 4e-5, (i, e)
+        # every gate at 1e-5, U's orthogonality over all columns down to sigma = 1e-6 (DIRECT: its
+        # pair threshold 4 sqrt(512) u = 5.4e-6 bounds the cosines left between columns)
+        assert max(e.values()) <= 1e-5, (i, method, e)
 
 
 @pytest.mark.parametrize("bw", [16, 32])
@@ -77,7 +72,7 @@ def test_block_ragged_shapes(bs, dt, method, bw):
         ad = a64.astype(dt).astype(np.float64)
         _, so, _, _, _ = O.svd(ad)
         e = svd_errors(ad, u[0].T, s[0], v[0].T, so)
-        assert max(e.values()) <= 4 * g, ((m, n), e)
+        assert max(e.values()) <= g, ((m, n), e)
 
 
 @pytest.mark.parametrize("method", [0, 1 << 16])

@@ -12,7 +12,7 @@ import pytest
 
 import gen
 import oracle as O
-from parity import svd_errors
+from parity import svd_errors, vector_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -153,3 +153,130 @@ def test_rsvd_workspace_errors(bs):
     torch.cuda.synchronize()
     info = res.info.cpu().numpy()
     assert info[0] >= 0 and int(res.samples.cpu()[0]) > 0 and info[-1] == bs.INFO_NO_SCRATCH
+
+
+# ----------------------------------------------------------------------------------------------
+# fixed-rank mode (Algorithm 4 as stated), per-matrix tolerances, q power steps, FP64, and the
+# adaptive method's decisions against the oracle's adaptive range finder
+# ----------------------------------------------------------------------------------------------
+
+def _packed(rb, dtype):
+    flat = torch.from_numpy(rb.flat.astype(dtype)).cuda()
+    return flat
+
+
+def _run_mode(bs, rb, dtype, **kw):
+    res = bs.rsvd(_packed(rb, dtype), rb.offset, rb.m, rb.n, seed=SEED, **kw)
+    torch.cuda.synchronize()
+    res.U_h = res.U.cpu().numpy().astype(np.float64)
+    res.V_h = res.V.cpu().numpy().astype(np.float64)
+    res.S_h = res.S.cpu().numpy().astype(np.float64)
+    res.rank_h = res.rank.cpu().numpy()
+    res.info_h = res.info.cpu().numpy()
+    res.samples_h = res.samples.cpu().numpy()
+    return res
+
+
+def _fp64_blocks(batch, sizes):
+    """The uneven generator's blocks rounded to FP64 instead of FP32."""
+    return gen.rsvd_uneven_blocks(batch=batch, sizes=sizes, dtype=np.float64)
+
+
+@pytest.mark.parametrize("dtype,q", [(np.float32, 1), (np.float32, 0), (np.float32, 2), (np.float64, 1)])
+def test_rsvd_fixed_rank_matches_the_oracle(bs, dtype, q):
+    """rank[b] = k > 0: k + p samples, q power steps, the first k columns (paper Section 7,
+    Algorithm 4); sigma and U, V column by column against the oracle's fixed-rank RSVD with the same
+    Omega, after sign alignment."""
+    sizes = (64, 128, 256) if dtype == np.float32 else (64, 128)
+    rb = gen.rsvd_uneven_blocks(batch=24, sizes=sizes) if dtype == np.float32 else _fp64_blocks(16, sizes)
+    kk = np.minimum(rb.m, rb.n)
+    rng = np.random.default_rng(4)
+    k = np.maximum(1, (rb.extra["rank_hint"] * rng.uniform(0.3, 1.1, rb.batch)).astype(np.int32))
+    k[0] = kk[0]                         # k + p past min(m, n): the full SVD, k columns kept
+    k[1] = max(1, kk[1] - 8)             # k + p = min(m, n) exactly: the full SVD
+    lcap = 128 if dtype == np.float32 else 64
+    res = _run_mode(bs, rb, dtype, fixed_rank=k, power_iters=q)
+    g = 1e-5 if dtype == np.float32 else 1e-12
+    c = 256.0 if dtype == np.float32 else 64.0
+    for b in range(rb.batch):
+        a = rb.a64(b)
+        Uo, So, Vo, l = O.rsvd_rank(a, SEED, b, int(k[b]), 8, q, lcap)
+        kb = min(int(k[b]), int(kk[b]))
+        assert int(res.rank_h[b]) == kb and int(res.samples_h[b]) == l, (b, int(res.rank_h[b]), kb, l)
+        assert int(res.info_h[b]) == (0 if l == kk[b] else 1), (b, int(res.info_h[b]))
+        u, s, v = _unpack(res, b)
+        assert np.abs(s - So).max() <= g * So[0], (b, np.abs(s - So).max() / So[0])
+        s_all = O.rsvd(a, SEED, b, l, q)[1] if l < kk[b] else O.svd(a)[1]
+        assert vector_errors(u, Uo, So, dtype, c, s_all) <= 1.0, b
+        assert vector_errors(v, Vo, So, dtype, c, s_all) <= 1.0, b
+
+
+def _clear_rank(so, norm2, eps, est2, delta):
+    """The truncation rank of the oracle's values, or None when rounding of the singular values
+    (delta, absolute) or a factor 2 in the estimate could move it."""
+    lo = O.budget_rank(np.maximum(so - delta, 0.0), norm2, eps, est2 / 2)
+    hi = O.budget_rank(so + delta, norm2, eps, 2 * est2)
+    return lo if lo == hi else None
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_rsvd_adaptive_decisions_match_the_oracle(bs, dtype):
+    """Tolerance mode with per-matrix tolerances: rounds, samples and rank equal the oracle's adaptive
+    range finder (same Omega and probes) on every block whose round decisions are clear (the
+    estimate at least 2x from eps/2 ||A||_F) and whose truncation rank does not move under the
+    FP32/FP64 rounding of sigma and a factor 2 in the estimate."""
+    sizes = (64, 128, 256) if dtype == np.float32 else (64, 128)
+    rb = gen.rsvd_uneven_blocks(batch=48, sizes=sizes) if dtype == np.float32 else _fp64_blocks(24, sizes)
+    rng = np.random.default_rng(6)
+    tol = rng.choice([1e-3, 1e-4, 1e-5], rb.batch)
+    hint = (rb.extra["rank_hint"] // 2).astype(np.int32)
+    hint[::5] = 0
+    lcap = 128 if dtype == np.float32 else 64
+    res = _run_mode(bs, rb, dtype, rank_hint=hint, tol_per=tol, max_rounds=8)
+    delta = (2e-6 if dtype == np.float32 else 1e-13)
+    compared_rounds = compared_rank = 0
+    for b in range(rb.batch):
+        a = rb.a64(b)
+        r = O.rsvd_adaptive(a, SEED, b, int(hint[b]), float(tol[b]), 8, 1, 8, lcap)
+        thr = 0.25 * tol[b] ** 2 * r["norm2"]
+        clear = all(e >= 4 * thr or e <= thr / 4 for e in r["est2_round"])
+        u, s, v = _unpack(res, b)
+        na = math.sqrt(r["norm2"])
+        err = np.linalg.norm(a - (u * s) @ v.T) / na
+        assert err <= tol[b], (b, err, tol[b])
+        if not clear:
+            continue
+        compared_rounds += 1
+        got = (int(res.info_h[b]) & 0xff, int(res.samples_h[b]), bool(res.info_h[b] & (1 << 22)))
+        assert got == (r["rounds"], r["samples"], r["fallback"]), (b, got, r["rounds"], r["samples"], r["fallback"])
+        kr = _clear_rank(r["S"], r["norm2"], float(tol[b]), r["est2"], delta * r["S"][0])
+        if kr is not None:
+            compared_rank += 1
+            assert int(res.rank_h[b]) == kr == r["rank"], (b, int(res.rank_h[b]), kr, r["rank"])
+    assert compared_rounds >= rb.batch // 3 and compared_rank >= rb.batch // 4, (compared_rounds, compared_rank)
+
+
+def test_rsvd_fp64_tolerance_mode(bs):
+    """FP64 randomized SVD to 1e-10: error <= eps on every block, sigma against the oracle's FP64
+    fixed-width RSVD with the same samples within 1e-12 normwise."""
+    rb = _fp64_blocks(12, (64, 128, 256))
+    res = _run_mode(bs, rb, np.float64, rank_hint=rb.extra["rank_hint"], tol=1e-10, max_rounds=8)
+    assert np.all(res.info_h >= 0)
+    for b in range(rb.batch):
+        a = rb.a64(b)
+        u, s, v = _unpack(res, b)
+        na = np.linalg.norm(a)
+        assert np.linalg.norm(a - (u * s) @ v.T) / na <= 1e-10
+        if u.shape[1]:
+            assert np.abs(u.T @ u - np.eye(u.shape[1])).max() <= 1e-12
+            assert np.abs(v.T @ v - np.eye(v.shape[1])).max() <= 1e-12
+        l = int(res.samples_h[b])
+        so = O.rsvd(a, SEED, b, l, 1)[1] if l < min(a.shape) else O.svd(a)[1]
+        assert np.abs(s - so[:len(s)]).max() <= 1e-12 * so[0], b
+
+
+def test_rsvd_bad_tolerance_flags_the_matrix(bs):
+    rb = gen.rsvd_uneven_blocks(batch=4, sizes=(64,))
+    tol = np.array([1e-5, -1.0, float("nan"), 1.5])
+    res = _run_mode(bs, rb, np.float32, tol_per=tol)
+    assert res.info_h[0] >= 0 and list(res.info_h[1:]) == [-1, -1, -1]

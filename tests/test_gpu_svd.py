@@ -127,7 +127,7 @@ def test_svd_ragged_shapes(bs, dt, shapes):
         assert 0 < inf < (1 << 20), ((m, n), inf)
         uo, so, vo, _, _ = O.svd(a64)
         e = svd_errors(a64, u, s, v, so)
-        assert max(e.values()) <= g * max(1.0, np.sqrt(max(m, n) / 64)), ((m, n), e)
+        assert max(e.values()) <= g, ((m, n), e)
         assert vector_errors(u, uo, so, dt) <= 1.0 and vector_errors(v, vo, so, dt) <= 1.0, (m, n)
 
 

@@ -1,8 +1,8 @@
 """GPU parity at the benchmark's full sizes, in the launch configuration bench.py times (the slowest
-GPU tests; they sort last).
+GPU tests).
 
 The workloads are built by bench.py's own workload classes (same generators, sizes, seeds and
-calls; the randomized SVD replayed from its CUDA graph).  Every output is checked by properties
+calls; the randomized SVDs replayed from their CUDA graphs).  Every output is checked by properties
 that hold at any size; sampled matrices are compared with the FP64 oracle one by one.
   * block512: 500 FP32 512 x 512, GRAM, block width 32 -- every sigma against the generator's
     spectrum, two matrices against the oracle's SVD (sigma, orthogonality, residual);
@@ -41,8 +41,7 @@ def check_block512(W, picks):
     S = W.S.cpu().numpy()[:, 0, :].astype(np.float64)
     # the generator's spectrum: the FP32 rounding of A moves it by ~u ||A||_F (3e-7), far inside 1e-5
     assert np.abs(S - W.sigma).max() <= EPS
-    host = W.h_in[0].numpy()
-    mats = [host[b].T.astype(np.float64) for b in picks]
+    mats = [W.d[b].cpu().numpy().T.astype(np.float64) for b in picks]
     _, So, _, _, _ = O.svd_batch(mats)
     for i, b in enumerate(picks):
         u = W.U[b].cpu().numpy().T.astype(np.float64)
@@ -53,7 +52,7 @@ def check_block512(W, picks):
 
 def test_block512_full_workload(bs):
     import bench
-    W = bench.Block512(argparse.Namespace(block_batch=500))
+    W = bench.Block512(argparse.Namespace(block_batch=500, host_inputs=False))
     W.setup(0, torch.device("cuda"))
     W.step(torch.cuda.current_stream())
     torch.cuda.synchronize()
@@ -93,7 +92,7 @@ def check_rsvd(W, every, seed=BENCH_SEED):
 
 def test_rsvd_uneven_full_workload(bs):
     import bench
-    W = bench.RsvdUneven(argparse.Namespace(rsvd_batch=16384))
+    W = bench.RsvdUneven(argparse.Namespace(rsvd_batch=16384, host_inputs=False))
     W.setup(0, torch.device("cuda"))
     stream = torch.cuda.current_stream()
     for _ in range(3):      # the benchmark's warm-up calls, then the capture it replays
@@ -103,3 +102,33 @@ def test_rsvd_uneven_full_workload(bs):
     W.step(stream)          # one replay of the captured call, as the benchmark times it
     torch.cuda.synchronize()
     check_rsvd(W, W.rb.batch // 16)
+
+
+def test_hmatrix_mlp_full_workload(bs):
+    """Workload 4 at full size (32 768 points, about 52 000 kernel blocks): the rank predictor trained
+    as the benchmark trains it, its hints fed to the randomized SVD, one replay of the captured
+    step.  Every 1/48th block: the truncation error, Eckart-Young, orthogonality and sigma against
+    the oracle; the adaptive decisions (rounds, samples) equal the oracle's adaptive range finder
+    with the same hint wherever every round's estimate is at least 2x from eps/2."""
+    import bench
+    W = bench.HmatrixMlp(argparse.Namespace())
+    W.setup(0, torch.device("cuda"))
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        W.step(stream)
+    torch.cuda.synchronize()
+    W.capture(stream)
+    W.step(stream)
+    torch.cuda.synchronize()
+    check_rsvd(W, W.rb.batch // 48)
+    hint = W.hint_d.cpu().numpy()
+    info, samples = W.info.cpu().numpy(), W.samples.cpu().numpy()
+    compared = 0
+    for b in range(0, W.rb.batch, W.rb.batch // 48):
+        r = O.rsvd_adaptive(W.rb.a64(b), BENCH_SEED, b, int(hint[b]), EPS, 8, 1, 16, 128)
+        thr = 0.25 * EPS * EPS * r["norm2"]
+        if all(e >= 4 * thr or e <= thr / 4 for e in r["est2_round"]):
+            compared += 1
+            got = (int(info[b]) & 0xff, int(samples[b]))
+            assert got == (r["rounds"], r["samples"]), (b, got, r["rounds"], r["samples"])
+    assert compared >= 16, compared
