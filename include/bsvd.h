@@ -126,13 +126,16 @@ int bsvd_jacobi_variants(int dtype, int max_m, int max_n, int tier);
 
 /*
  * bsvd_jacobi_variant_desc -- describe the k-th (k >= 1) register-tier variant that fits a batch
- * bounded by max_m x max_n (the variant BSVD_TIER_REGISTER | (k << 8) launches).  desc (HOST, 8
+ * bounded by max_m x max_n (the variant BSVD_TIER_REGISTER | (k << 8) launches).  desc (HOST, 9
  * ints, caller-owned) receives {column-pair slots, row parts, rows of A per lane, rows of V per
  * lane, resident CTAs per SM, scaled rotations (0/1), QR preconditioning (0/1), FP64 rotation
- * parameters (0/1)}.  QR preconditioning (square bounds only) factors A = Q R and runs the sweeps
+ * parameters (0/1), carried column norms (0/1)}.  QR preconditioning (square bounds only) factors A = Q R and runs the sweeps
  * on R^T (the project's addition; the paper runs them on A).  FP64 rotation parameters (FP32 data
- * only) compute zeta, t, c, s and the rotation test in FP64 from the FP32 Gram sums; these
- * variants are listed last.  Returns 0, a negative argument code, or
+ * only) compute zeta, t, c, s and the rotation test in FP64 from the FP32 Gram sums; carried
+ * column norms keep each column's squared norm across the steps of a sweep (one dot product per
+ * pair instead of three; alpha' = alpha - t gamma, beta' = beta + t gamma after a rotation, summed
+ * afresh at every sweep's start and after a cancelling update).  These variants are listed last,
+ * the carried-norm ones after the FP64-parameter ones.  Returns 0, a negative argument code, or
  * BSVD_ERR_UNSUPPORTED when there is no k-th variant.  Host only; launches nothing.
  */
 int bsvd_jacobi_variant_desc(int dtype, int max_m, int max_n, int k, int* desc);
@@ -161,10 +164,19 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
  * then takes its timeout path (no further pairs, a bounded wait for the MMAs in flight before the
  * tensor memory is freed) and every matrix gets BSVD_INFO_DEVICE_TIMEOUT.  No fault, no hang. */
 #define BSVD_BLOCK_TEST_TIMEOUT (1 << 17)
+/* Flag for `method`: precondition by a blocked Householder QR (the preconditioning Section 6.3
+ * names as future work).  The working matrix X (A, or A^T when m < n) is factored X = Q R in
+ * 32-column panels (each panel on chip, the trailing columns updated through the compact WY form
+ * I - V T V^T), the block Jacobi runs on the lower-triangular R^T, whose rows are graded like the
+ * singular values (about half the outer sweeps), and X's left vectors are formed as Q times R^T's
+ * right vectors.  Needs max(m, n) * 32 * sizeof(element) <= 200 KiB (a panel on chip); the workspace
+ * holds X, R^T and the panels' T factors besides the block tier's own. */
+#define BSVD_BLOCK_QR_PRECONDITION (1 << 18)
 
 /*
  * batched_svd_block_jacobi_workspace -- bytes of DEVICE workspace batched_svd_block_jacobi needs
- * for these bounds, block width and method (0 for invalid arguments).  Host only.
+ * for these bounds, block width and method (its BSVD_BLOCK_QR_PRECONDITION bit included; 0 for
+ * invalid arguments).  Host only.
  */
 size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int max_n, int block_width,
                                           int method);
@@ -184,6 +196,8 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
  *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
  *                 | BSVD_BLOCK_TEST_TIMEOUT exercises the failure path (tests only; see the flag).
+ *                 | BSVD_BLOCK_QR_PRECONDITION runs the block Jacobi on R^T of a blocked QR (see the
+ *                 flag); info and rotations then count the sweeps on R^T.
  *                 | BSVD_BLOCK_SIMT_PRODUCTS keeps the Gram products on the FP32 SIMT pipes (FP32
  *                 data with bw = 32 form them on the tensor cores otherwise).  | (s << 24) sets the sweep cap of
  *                 each pair visit's inner SVD: 1 <= s <= 126 sweeps, 127 = to convergence (as
@@ -252,8 +266,13 @@ size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const 
  *                  projected block's R_B^T and, for full-rank blocks with min(m, n) <= 64, of R^T
  *                  -- run in FP64 when l <= 64 (operands widened, FP64 register tier, results
  *                  narrowed to FP32), and with FP64 rotation parameters in the shared tier above
- *                  (also for full-rank blocks with 64 < min(m, n) <= 128).  Other bits: argument
- *                  error.
+ *                  (also for full-rank blocks with 64 < min(m, n) <= 128).
+ *                  | BSVD_RSVD_TC_SAMPLING (FP32 runs; ignored in FP64): the sample A Omega is a
+ *                  tcgen05 product of kind::tf32 (the FP32 operands read with a 10-bit mantissa, FP32
+ *                  accumulation), the 8 probe columns stay FP32 products; the power step and the
+ *                  projection that follow are FP32.  Other bits: argument error.  A tensor-core
+ *                  completion wait that gives up (bounded; no valid input makes one) gives every
+ *                  matrix of the call BSVD_INFO_DEVICE_TIMEOUT.
  *   dU[b] (m x kmax, ld d_ldu[b]), dS[b] (kmax), dV[b] (n x kmax, ld d_ldv[b]): the first k columns
  *                  and values are written; k > kmax writes kmax and flags BSVD_INFO_RANK_CAPPED.
  *   d_rank_out[b]  k;  d_err_est[b] (nullable) est / ||A||_F (also in fixed-rank mode; 0 after a
@@ -265,7 +284,8 @@ size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const 
  *   workspace      at least batched_rsvd_workspace(...) bytes (else BSVD_ERR_WORKSPACE), caller-owned,
  *                  contents need not be initialised.
  */
-#define BSVD_RSVD_SMALL_FP64 1 /* flags: FP32 runs take the small SVDs in FP64 (see batched_rsvd) */
+#define BSVD_RSVD_SMALL_FP64 1  /* flags: FP32 runs take the small SVDs in FP64 (see batched_rsvd) */
+#define BSVD_RSVD_TC_SAMPLING 2 /* flags: FP32 runs form the sample A Omega on the tensor cores */
 
 int batched_rsvd(int dtype, int batch, int max_m, int max_n,
                  void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
@@ -343,6 +363,39 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
                                      void* const* dV, const int* d_ldv,
                                      double tol, int max_sweeps, int block_width, int method,
                                      int* d_info, long long* d_rotations, void* stream);
+
+/*
+ * bsvd_h2_truncate_workspace -- bytes of DEVICE workspace bsvd_h2_truncate needs (0 for invalid
+ * arguments).  Host only.
+ *
+ * bsvd_h2_truncate -- the truncation phase of H^2-matrix compression (Section 8.2): a nested row
+ * basis over a binary tree of depth `depth` is replaced by a truncated orthonormal one, level by
+ * level from the leaves, with the projections T = U~^T U of every node.
+ *
+ * Nodes are numbered in heap order: node i of level l is g = 2^l - 1 + i (root 0, children of g are
+ * 2g + 1 and 2g + 2); the 2^depth leaves are g = 2^depth - 1 + i.  All pointers are DEVICE arrays.
+ *   d_leaf[i]      leaf basis U_i, m_i x k (d_leaf_m[i] = m_i <= max_leaf_m <= 256, ld d_leaf_ld[i]).
+ *   d_transfer[g]  (g >= 1) transfer matrix E_g, k x k, ld k: U_parent = diag(U_c1, U_c2) [E_c1; E_c2].
+ *   k              the basis rank of every node (1..64; q^2 for a q x q Chebyshev grid).
+ *   eps            relative threshold: every node keeps the smallest rank r whose discarded tail
+ *                  sqrt(sum_{j >= r} s_j^2) is within eps times the Frobenius norm of the matrix it
+ *                  truncates (the leaf basis, or TE_p = [T_c1 E_c1; T_c2 E_c2]).
+ *   d_new_leaf[i]  (out) U~_i: the first rank[leaf] columns are written (ld d_new_leaf_ld[i] >= m_i).
+ *   d_new_transfer[g] (out, g >= 1) E~_g: rank[g] x rank[parent] written, ld k (k x k buffers).
+ *   d_T[g]         (out) T_g = U~_g^T U_g: rank[g] x k written, ld k (k x k buffers), every node.
+ *   d_rank[g], d_info[g] (out) per node: the kept rank; the sweeps of the node's SVD, or
+ *                  BSVD_INFO_BAD_SHAPE (a leaf with m_i > max_leaf_m or a short ld; rank 0) or
+ *                  BSVD_INFO_NONFINITE.
+ *   d_rotations[g] (out, nullable) plane rotations of the node's SVD.
+ *   workspace      at least bsvd_h2_truncate_workspace(...) bytes (else BSVD_ERR_WORKSPACE).
+ * Every SVD is the one-sided Jacobi of this library (register tier; shared tier where the
+ * register tier does not hold the bounds), all nodes of a level in one batched call.
+ */
+size_t bsvd_h2_truncate_workspace(int dtype, int depth, int k, int max_leaf_m);
+int bsvd_h2_truncate(int dtype, int depth, int k, int max_leaf_m, void* const* d_leaf, const int* d_leaf_m,
+                     const int* d_leaf_ld, void* const* d_transfer, double eps, void* const* d_new_leaf,
+                     const int* d_new_leaf_ld, void* const* d_new_transfer, void* const* d_T, int* d_rank,
+                     int* d_info, long long* d_rotations, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Diagnostics (outside the method; for tests and the benchmark).

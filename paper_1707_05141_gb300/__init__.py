@@ -30,8 +30,10 @@ INFO_FALLBACK = 1 << 22
 INFO_DEVICE_TIMEOUT = -3
 INFO_NONFINITE = -4
 RSVD_SMALL_FP64 = 1
+RSVD_TC_SAMPLING = 2
 BLOCK_SIMT_PRODUCTS = 1 << 16
 BLOCK_TEST_TIMEOUT = 1 << 17
+BLOCK_QR_PRECONDITION = 1 << 18
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -76,6 +78,10 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.c_size_t, p]
             L.batched_rsvd_workspace.restype = ctypes.c_size_t
             L.batched_rsvd_workspace.argtypes = [i, i, i, i, p, p]
+            L.bsvd_h2_truncate_workspace.restype = ctypes.c_size_t
+            L.bsvd_h2_truncate_workspace.argtypes = [i, i, i, i]
+            L.bsvd_h2_truncate.restype = i
+            L.bsvd_h2_truncate.argtypes = [i, i, i, i, p, p, p, p, d, p, p, p, p, p, p, p, p, ctypes.c_size_t, p]
             L.bsvd_philox_gauss.restype = i
             L.bsvd_philox_gauss.argtypes = [i, p, ctypes.c_ulonglong, p, p, p, p]
             L.bsvd_fma_probe.restype = ctypes.c_longlong
@@ -112,10 +118,10 @@ def jacobi_variants(dtype_code: int, max_m: int, max_n: int, tier: int) -> int:
 
 def jacobi_variant_desc(dtype_code: int, max_m: int, max_n: int, k: int) -> dict:
     """Shape parameters of the k-th (k >= 1) register-tier variant fitting max_m x max_n."""
-    d = (ctypes.c_int * 8)()
+    d = (ctypes.c_int * 9)()
     _check("bsvd_jacobi_variant_desc", lib().bsvd_jacobi_variant_desc(dtype_code, max_m, max_n, k, d))
-    return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond", "fp64_params"),
-                    list(d)))
+    return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond", "fp64_params",
+                     "carried_norms"), list(d)))
 
 
 def set_jacobi_choice(dtype_code: int, max_m: int, max_n: int, tier: int) -> None:
@@ -320,6 +326,76 @@ def batched_rsvd(A: Batch, U: Batch, S: Batch, V: Batch, kmax, rank, info, works
                             _dptr(info, "info", i32, nb), _dptr(workspace, "workspace", torch.uint8),
                             int(workspace.numel()), _stream_ptr(stream))
     _check("batched_rsvd", rc)
+
+
+class H2Plan:
+    """A basis tree staged on the GPU for ``bsvd_h2_truncate`` (Section 8.2): leaves packed in one
+    flat device tensor (column-major at ``offsets``), transfers and the outputs as (nodes, k, k)
+    tensors (node g's matrix column-major: tensor[g].T), heap order (node i of level l is
+    2^l - 1 + i), the workspace allocated once.  ``run`` truncates to ``eps``."""
+
+    def __init__(self, leaves, transfers, k: int, dtype=None):
+        import numpy as np
+        torch = _torch()
+        dt = torch.float32 if dtype in (None, np.float32, torch.float32) else torch.float64
+        npdt = np.float32 if dt == torch.float32 else np.float64
+        dev = torch.device("cuda")
+        d = len(transfers) - 1
+        nl = len(leaves)
+        if nl != 2 ** d:
+            raise ValueError("a tree of depth d has 2^d leaves")
+        nodes = 2 * nl - 1
+        ms = np.array([np.asarray(u).shape[0] for u in leaves], dtype=np.int32)
+        lds = np.maximum(ms, 1).astype(np.int32)
+        sizes = (lds.astype(np.int64) * k + 3) // 4 * 4
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        flat = np.zeros(int(sizes.sum()) + 4, dtype=npdt)
+        for u, o, m in zip(leaves, offs, ms):
+            flat[o:o + m * k] = np.asarray(u, dtype=np.float64).T.reshape(-1).astype(npdt)
+        E = np.zeros((nodes, k, k), dtype=npdt)
+        for l in range(1, d + 1):
+            for i, e in enumerate(transfers[l]):
+                E[2 ** l - 1 + i] = np.asarray(e, dtype=np.float64).T.astype(npdt)   # column-major
+        self.leaf = torch.from_numpy(flat).to(dev)
+        self.new_leaf = torch.zeros_like(self.leaf)
+        self.E = torch.from_numpy(E).to(dev)
+        self.new_transfer = torch.zeros_like(self.E)
+        self.T = torch.zeros_like(self.E)
+        self.rank = torch.zeros(nodes, dtype=torch.int32, device=dev)
+        self.info = torch.zeros(nodes, dtype=torch.int32, device=dev)
+        self.rotations = torch.zeros(nodes, dtype=torch.int64, device=dev)
+        es = self.leaf.element_size()
+        self.leaf_p = torch.as_tensor(offs * es + int(self.leaf.data_ptr()), dtype=torch.int64).to(dev)
+        self.new_leaf_p = torch.as_tensor(offs * es + int(self.new_leaf.data_ptr()), dtype=torch.int64).to(dev)
+        node_off = torch.arange(nodes, dtype=torch.int64, device=dev) * (k * k * es)
+        self.E_p = node_off + int(self.E.data_ptr())
+        self.newE_p = node_off + int(self.new_transfer.data_ptr())
+        self.T_p = node_off + int(self.T.data_ptr())
+        self.m_d = torch.as_tensor(ms).to(dev)
+        self.ld_d = torch.as_tensor(lds).to(dev)
+        self.code = F32 if dt == torch.float32 else F64
+        self.max_m = int(ms.max()) if nl else 0
+        self.depth, self.k, self.m, self.offsets, self.nodes = d, k, ms, offs, nodes
+        self.workspace = torch.empty(int(lib().bsvd_h2_truncate_workspace(self.code, d, k, self.max_m)),
+                                     dtype=torch.uint8, device=dev)
+
+    def run(self, eps: float, stream=None) -> None:
+        torch = _torch()
+        rc = lib().bsvd_h2_truncate(self.code, self.depth, self.k, self.max_m, _ptr(self.leaf_p), _ptr(self.m_d),
+                                    _ptr(self.ld_d), _ptr(self.E_p), float(eps), _ptr(self.new_leaf_p),
+                                    _ptr(self.ld_d), _ptr(self.newE_p), _ptr(self.T_p), _ptr(self.rank),
+                                    _ptr(self.info), _ptr(self.rotations),
+                                    _dptr(self.workspace, "workspace", torch.uint8), int(self.workspace.numel()),
+                                    _stream_ptr(stream))
+        _check("bsvd_h2_truncate", rc)
+
+
+def h2_truncate(leaves, transfers, k: int, eps: float, dtype=None, stream=None):
+    """Truncation phase of H^2 compression (Section 8.2) on the GPU; returns the H2Plan holding the
+    outputs (``new_leaf``, ``new_transfer``, ``T``, ``rank``, ``info``, ``rotations``)."""
+    plan = H2Plan(leaves, transfers, k, dtype)
+    plan.run(eps, stream)
+    return plan
 
 
 def philox_gauss(ctr, seed: int, stream=None):

@@ -54,8 +54,9 @@ extern "C" {
 
 const char* bsvd_version(void)
 {
-    return "bsvd-gb300 0.5 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD with QR "
-           "preconditioning and a tcgen05 block Gram, randomized SVD, learned rank predictor)";
+    return "bsvd-gb300 0.6 (sm_103a; batched Householder QR, register/shared/block one-sided Jacobi SVD with QR "
+           "preconditioning (register and block level) and a tcgen05 block Gram, fixed-rank and adaptive "
+           "randomized SVD, H2 basis truncation, learned rank predictor)";
 }
 
 int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
@@ -159,8 +160,9 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
     if ((dtype != BSVD_F32 && dtype != BSVD_F64) || batch < 0 || max_m < 0 || max_n < 0) return 0;
     const int base = method & 0xff;
     if ((block_width != 16 && block_width != 32) || (base != BSVD_BLOCK_GRAM && base != BSVD_BLOCK_DIRECT)) return 0;
-    return dtype == BSVD_F32 ? block_jacobi_workspace<float>(batch, max_m, max_n, block_width, base)
-                             : block_jacobi_workspace<double>(batch, max_m, max_n, block_width, base);
+    const int m2 = base | (method & BSVD_BLOCK_QR_PRECONDITION);
+    return dtype == BSVD_F32 ? block_jacobi_workspace<float>(batch, max_m, max_n, block_width, m2)
+                             : block_jacobi_workspace<double>(batch, max_m, max_n, block_width, m2);
 }
 
 int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m,
@@ -187,8 +189,10 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
     // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
-    // 24-30 inner sweep cap
-    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | (0x7f << 24))) return -17;
+    // 18 QR preconditioning, 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | BSVD_BLOCK_QR_PRECONDITION |
+                   (0x7f << 24)))
+        return -17;
     if (!d_info) return -18;
     if (!workspace) return -20;
     cudaStream_t st = (cudaStream_t)stream;
@@ -230,7 +234,7 @@ int batched_rsvd(int dtype, int batch, int max_m, int max_n, void* const* dA, co
     if (oversample < 1 || oversample > 64) return -13;
     if (power_iters < 0 || power_iters > 8) return -14;
     if (max_rounds < 1 || max_rounds > 64) return -15;
-    if (flags & ~(BSVD_RSVD_SMALL_FP64)) return -17;
+    if (flags & ~(BSVD_RSVD_SMALL_FP64 | BSVD_RSVD_TC_SAMPLING)) return -17;
     if (!dU) return -18;
     if (!d_ldu) return -19;
     if (!dS) return -20;
@@ -248,6 +252,46 @@ int batched_rsvd(int dtype, int batch, int max_m, int max_n, void* const* dA, co
                : launch_rsvd<double>(batch, max_m, max_n, dA, d_m, d_n, d_lda, d_rank, d_rank_hint, d_tol, tol,
                                      d_kmax, oversample, power_iters, max_rounds, seed, flags, dU, d_ldu, dS, dV, d_ldv,
                                      d_rank_out, d_err_est, d_samples, d_info, workspace, workspace_bytes, st);
+}
+
+size_t bsvd_h2_truncate_workspace(int dtype, int depth, int k, int max_leaf_m)
+{
+    if ((dtype != BSVD_F32 && dtype != BSVD_F64) || depth < 0 || depth > 20 || k < 1 || k > 64 || max_leaf_m < 0 ||
+        max_leaf_m > 256)
+        return 0;
+    return dtype == BSVD_F32 ? h2_truncate_workspace<float>(depth, k, max_leaf_m)
+                             : h2_truncate_workspace<double>(depth, k, max_leaf_m);
+}
+
+int bsvd_h2_truncate(int dtype, int depth, int k, int max_leaf_m, void* const* d_leaf, const int* d_leaf_m,
+                     const int* d_leaf_ld, void* const* d_transfer, double eps, void* const* d_new_leaf,
+                     const int* d_new_leaf_ld, void* const* d_new_transfer, void* const* d_T, int* d_rank,
+                     int* d_info, long long* d_rotations, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (depth < 0 || depth > 20) return -2;
+    if (k < 1 || k > 64) return -3;
+    if (max_leaf_m < 0 || max_leaf_m > 256 || (dtype == BSVD_F64 && max_leaf_m > 256)) return -4;
+    if (!d_leaf) return -5;
+    if (!d_leaf_m) return -6;
+    if (!d_leaf_ld) return -7;
+    if (depth > 0 && !d_transfer) return -8;
+    if (!(eps >= 0.0 && eps < 1.0)) return -9;
+    if (!d_new_leaf) return -10;
+    if (!d_new_leaf_ld) return -11;
+    if (depth > 0 && !d_new_transfer) return -12;
+    if (!d_T) return -13;
+    if (!d_rank) return -14;
+    if (!d_info) return -15;
+    if (!workspace) return -17;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32
+               ? launch_h2_truncate<float>(depth, k, max_leaf_m, d_leaf, d_leaf_m, d_leaf_ld, d_transfer, eps,
+                                           d_new_leaf, d_new_leaf_ld, d_new_transfer, d_T, d_rank, d_info, d_rotations,
+                                           workspace, workspace_bytes, st)
+               : launch_h2_truncate<double>(depth, k, max_leaf_m, d_leaf, d_leaf_m, d_leaf_ld, d_transfer, eps,
+                                            d_new_leaf, d_new_leaf_ld, d_new_transfer, d_T, d_rank, d_info, d_rotations,
+                                            workspace, workspace_bytes, st);
 }
 
 }  // extern "C"

@@ -965,7 +965,8 @@ __global__ void __launch_bounds__(256) bj_finalize_kernel(int batch, T* const* S
 template <typename T>
 size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method)
 {
-    return bj_layout<T>(batch, max_m, max_n, bw, method != 0).total;
+    if (method & BSVD_BLOCK_QR_PRECONDITION) return block_jacobi_qr_workspace<T>(batch, max_m, max_n, bw, method);
+    return bj_layout<T>(batch, max_m, max_n, bw, (method & 0xff) != 0).total;
 }
 
 template <typename T, int K2>
@@ -992,7 +993,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     // the SVD of R and keeps the first plain variant.
     bool inner_u = false;
     if (!direct && inner_variant == 0) {
-        int d[8];
+        int d[9];
         for (int k = 1; jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, k, d) == BSVD_SUCCESS; ++k)
             if (d[6]) {
                 inner_variant = k;
@@ -1000,7 +1001,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                 break;
             }
     } else if (!direct) {
-        int d[8];
+        int d[9];
         inner_u = jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, inner_variant, d) == BSVD_SUCCESS && d[6];
     }
     const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
@@ -1116,6 +1117,9 @@ int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, voi
                         const int* LDV, double tol, int max_sweeps, int* info, long long* rot, void* ws, size_t ws_bytes,
                         cudaStream_t st)
 {
+    if (method & BSVD_BLOCK_QR_PRECONDITION)
+        return launch_block_jacobi_qr<T>(batch, max_m, max_n, bw, method, A, M, N, LDA, S, U, LDU, V, LDV, tol,
+                                         max_sweeps, info, rot, ws, ws_bytes, st);
     if (bw != 16 && bw != 32) return BSVD_ERR_UNSUPPORTED;
     const int mm = max_m > max_n ? max_m : max_n;
     if ((method & 0xff) != 0 && (size_t)(mm > 2 * bw ? mm : 2 * bw) * 2 * bw * sizeof(T) > 200 * 1024) return BSVD_ERR_UNSUPPORTED;

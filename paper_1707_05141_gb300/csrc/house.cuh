@@ -6,42 +6,55 @@
 
 namespace bsvd {
 
+// The reflector of column i, formed by one warp: v = house(S(i:m, i)) (norm by a warp shuffle
+// reduction), stored normalised so that the reflector is I - 2 v v^T in S(i:m, i), and
+// R(i, i) = -sign(x_0) ||x|| in diag[i].  A zero column gives v = 0 (identity reflector), R(i, i) = 0.
+template <typename T>
+__device__ __forceinline__ void house_reflector(T* col, int i, int m, T* diag, int lane)
+{
+    const T x0 = col[i];  // read by every lane before the shuffles below
+    T ss = T(0);
+    for (int r = i + lane; r < m; r += 32) ss += col[r] * col[r];
+    ss = warp_sum(ss);
+    const T alpha = dsqrt(ss);
+    if (alpha > T(0)) {
+        const T sg = x0 >= T(0) ? T(1) : T(-1);
+        // ||x + sign(x0) alpha e1||^2 = 2 alpha (alpha + |x0|)
+        const T inv = drsqrt(T(2) * alpha * (alpha + dabs(x0)));
+        for (int r = i + lane; r < m; r += 32) col[r] = (r == i ? x0 + sg * alpha : col[r]) * inv;
+        if (lane == 0) diag[i] = -sg * alpha;
+    } else if (lane == 0) {
+        diag[i] = T(0);  // zero column: v = 0 (already zero), identity reflector
+    }
+}
+
 // Factor the m x n (m >= n) column-major matrix S (leading dimension ld) in place with all
-// blockDim.x threads (whole warps): for each column i a single warp forms the reflector
-// v = house(S(i:m, i)) (norm by a warp shuffle reduction), stores it, normalised so that the
-// reflector is I - 2 v v^T, in S(i:m, i) and R(i, i) = -sign(x_0) ||x|| in diag[i]; then every warp
-// applies it to the trailing columns, one column per warp (M^T v as a warp reduction, then the
-// rank-1 update).  On return the strict upper triangle of S holds R above its diagonal.  A zero
-// column gives v = 0 (identity reflector) and R(i, i) = 0.  Callers synchronise before and after.
+// blockDim.x threads (whole warps): reflector i (house_reflector) is applied to the trailing
+// columns, one column per warp (M^T v as a warp reduction, then the rank-1 update).  Look-ahead:
+// the warp that owns column i + 1 updates it first and forms reflector i + 1 at once, while the
+// other warps are still applying reflector i to their columns, so each column costs one barrier.
+// On return the strict upper triangle of S holds R above its diagonal.  Callers synchronise
+// before and after.
 template <typename T>
 __device__ __forceinline__ void house_factor_smem(T* S, int ld, T* diag, int m, int n)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (n > 0 && warp == 0) house_reflector(S, 0, m, diag, lane);
+    __syncthreads();
     for (int i = 0; i < n; ++i) {
-        T* col = S + (size_t)i * ld;
-        if (warp == 0) {
-            const T x0 = col[i];  // read by every lane before the shuffles below
-            T ss = T(0);
-            for (int r = i + lane; r < m; r += 32) ss += col[r] * col[r];
-            ss = warp_sum(ss);
-            const T alpha = dsqrt(ss);
-            if (alpha > T(0)) {
-                const T sg = x0 >= T(0) ? T(1) : T(-1);
-                // ||x + sign(x0) alpha e1||^2 = 2 alpha (alpha + |x0|)
-                const T inv = drsqrt(T(2) * alpha * (alpha + dabs(x0)));
-                for (int r = i + lane; r < m; r += 32) col[r] = (r == i ? x0 + sg * alpha : col[r]) * inv;
-                if (lane == 0) diag[i] = -sg * alpha;
-            } else if (lane == 0) {
-                diag[i] = T(0);  // zero column: v = 0 (already zero), identity reflector
-            }
-        }
-        __syncthreads();
-        for (int j = i + 1 + warp; j < n; j += nwarps) {
+        const T* col = S + (size_t)i * ld;
+        // this warp's first column right of i: columns j with j % nwarps == warp
+        const int first = i + 1 + ((warp - (i + 1) % nwarps) + nwarps) % nwarps;
+        for (int j = first; j < n; j += nwarps) {
             T* cj = S + (size_t)j * ld;
             T w = T(0);
             for (int r = i + lane; r < m; r += 32) w += col[r] * cj[r];
             w = T(2) * warp_sum(w);
             for (int r = i + lane; r < m; r += 32) cj[r] -= w * col[r];
+            if (j == i + 1) {
+                __syncwarp();
+                house_reflector(cj, j, m, diag, lane);
+            }
         }
         __syncthreads();
     }

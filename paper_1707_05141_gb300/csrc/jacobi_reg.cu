@@ -25,6 +25,16 @@
 // the columns at the end of every sweep (c >= 1/sqrt 2, so d stays above 2^-33 within a sweep).
 // FAST = false applies the rotation as written.
 //
+// Carried column norms (CARRY = true).  Each lane keeps the squared norms of its two columns (true,
+// unscaled frame) and moves them with the columns; a step then needs one dot product (gamma)
+// instead of three, and after a rotation the norms follow from the Jacobi angle's identities
+// alpha' = alpha - t gamma, beta' = beta + t gamma (the one-sided Jacobi norm update LAPACK's xGESVJ
+// uses).  The norms are recomputed from the columns at the start of every sweep; an update that
+// cancels below a quarter of the old value marks the norm stale (negative), and the next step of
+// that column sums it afresh (the warp, or the CTA, takes the three-product step when any of its
+// lanes holds a stale norm).  A rotation-free sweep changes no norm, so the convergence decision is
+// taken on norms summed at that sweep's start.
+//
 // QR preconditioning (PRE = true, square matrices).  A = Q R by Householder QR in the register
 // layout (reflectors kept in shared memory), then the sweeps run on W = R^T: R^T V_w = U_w S gives A = (Q V_w) S U_w^T, so
 // U = Q V_w (the reflectors applied to the accumulated rotations) and V = U_w = W / sigma.  The
@@ -49,7 +59,7 @@ struct Red3 {
 // MINB is the number of matrices (CTAs) the launch bound asks to keep resident per SM; it caps
 // the register allocation at 65536 / (NS * PARTS * MINB), trading scheduling freedom against
 // occupancy.  Several values are instantiated and the autotuner picks one per size bin.
-template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64>
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64, bool CARRY>
 __global__ void __launch_bounds__(NS * PARTS, MINB)
     jacobi_reg_kernel(int batch, T* const* A, const int* M, const int* N, const int* LDA, T* const* Sout, T* const* U,
                       const int* LDU, T* const* V, const int* LDV, double tol_in, int max_sweeps, int* info,
@@ -229,6 +239,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
             vR[k] = (r == colR) ? T(1) : T(0);
         }
         T dL = T(1), dR = T(1);  // column scales
+        T nL = T(0), nR = T(0);  // CARRY: true squared norms of the two columns (negative: stale)
 
         const P tol = tol_in > 0.0 ? P(tol_in) : P(dsqrt(double(mm)) * Unit<T>::value);
         const int sweeps_cap = max_sweeps > 0 ? max_sweeps : 30;
@@ -238,26 +249,42 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
 
         while (sweep < sweeps_cap) {
             int rot_sweep = 0;
+            if (CARRY) nL = nR = T(-1);  // every sweep starts from norms summed afresh
 #pragma unroll 1
             for (int st = 0; st < 2 * NS; ++st) {
                 const bool odd = st & 1;
-                // Gram partials over this lane's rows (two accumulators per entry)
+                // Gram partials over this lane's rows (two accumulators per entry); with carried
+                // norms only gamma, unless a norm of the warp (of the CTA, NW > 1) is stale.  The
+                // flag is exchanged with the partial sums: a stale lane sends its squared norms
+                // (non-negative) in slots a and b, the others send -1
+                const bool mine = !CARRY || nL < T(0) || nR < T(0);
+                const bool full = !CARRY || (NW > 1 ? true : __any_sync(0xffffffffu, mine));
                 T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0), c0 = T(0), c1 = T(0);
+                if (mine) {
 #pragma unroll
-                for (int k = 0; k < RA; k += 2) {
-                    a0 = fma(aL[k], aL[k], a0);
-                    b0 = fma(aR[k], aR[k], b0);
-                    c0 = fma(aL[k], aR[k], c0);
-                    if (k + 1 < RA) {
-                        a1 = fma(aL[k + 1], aL[k + 1], a1);
-                        b1 = fma(aR[k + 1], aR[k + 1], b1);
-                        c1 = fma(aL[k + 1], aR[k + 1], c1);
+                    for (int k = 0; k < RA; k += 2) {
+                        a0 = fma(aL[k], aL[k], a0);
+                        b0 = fma(aR[k], aR[k], b0);
+                        c0 = fma(aL[k], aR[k], c0);
+                        if (k + 1 < RA) {
+                            a1 = fma(aL[k + 1], aL[k + 1], a1);
+                            b1 = fma(aR[k + 1], aR[k + 1], b1);
+                            c1 = fma(aL[k + 1], aR[k + 1], c1);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RA; k += 2) {
+                        c0 = fma(aL[k], aR[k], c0);
+                        if (k + 1 < RA) c1 = fma(aL[k + 1], aR[k + 1], c1);
                     }
                 }
                 T sa = a0 + a1, sb = b0 + b1, sc = c0 + c1;
                 if (PPW == 2) {
-                    sa += __shfl_xor_sync(0xffffffffu, sa, 16);
-                    sb += __shfl_xor_sync(0xffffffffu, sb, 16);
+                    if (full) {
+                        sa += __shfl_xor_sync(0xffffffffu, sa, 16);
+                        sb += __shfl_xor_sync(0xffffffffu, sb, 16);
+                    }
                     sc += __shfl_xor_sync(0xffffffffu, sc, 16);
                 }
                 if (NW > 1) {
@@ -273,9 +300,16 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                     }
                     step_parity ^= 1;
                 }
+                // column norms in the unscaled frame: carried, or just summed (all parts of a pair
+                // hold the same carried values and the same stale flag, so they agree)
+                T tnL = nL, tnR = nR;
+                if (CARRY && mine) {
+                    tnL = dL * dL * sa;
+                    tnR = dR * dR * sb;
+                }
                 // rotation of the pair, in the unscaled frame; the wrap slot idles on odd steps
-                const P alpha = FAST ? P(dL) * P(dL) * P(sa) : P(sa);
-                const P beta = FAST ? P(dR) * P(dR) * P(sb) : P(sb);
+                const P alpha = CARRY ? P(tnL) : (FAST ? P(dL) * P(dL) * P(sa) : P(sa));
+                const P beta = CARRY ? P(tnR) : (FAST ? P(dR) * P(dR) * P(sb) : P(sb));
                 const P gamma = FAST ? P(dL) * P(dR) * P(sc) : P(sc);
                 const bool rot = !(odd && s == NS - 1) && alpha > P(0) && beta > P(0) &&
                                  off_diagonal_large(alpha, beta, gamma, tol);
@@ -328,6 +362,17 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                     }
                 }
                 rot_sweep += __popc(__ballot_sync(0xffffffffu, rot) & part_mask);
+                if (CARRY) {
+                    // alpha' = alpha - t gamma, beta' = beta + t gamma; a cancelling update is stale
+                    nL = tnL;
+                    nR = tnR;
+                    if (rot) {
+                        const T tg = T(tth * gamma);
+                        const T aN = tnL - tg, bN = tnR + tg;
+                        nL = aN < T(0.25) * tnL ? T(-1) : aN;
+                        nR = bN < T(0.25) * tnR ? T(-1) : bN;
+                    }
+                }
                 // exchange: after the swap the pair's lower position holds the right column
                 if (!odd) {
                     // even -> odd: the right column moves one slot down (slot s receives s + 1's)
@@ -339,6 +384,7 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                         for (int k = 0; k < RV; ++k) vR[k] = __shfl_sync(0xffffffffu, vR[k], src, NS);
                     }
                     if (FAST) dR = __shfl_sync(0xffffffffu, dR, src, NS);
+                    if (CARRY) nR = __shfl_sync(0xffffffffu, nR, src, NS);
                     colR = __shfl_sync(0xffffffffu, colR, src, NS);
                 } else {
                     // odd -> even: the left column moves one slot up; the wrap slot, which did not
@@ -363,6 +409,11 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                         const T r = __shfl_sync(0xffffffffu, wrap ? dR : dL, src, NS);
                         dR = wrap ? dL : dR;
                         dL = r;
+                    }
+                    if (CARRY) {
+                        const T r = __shfl_sync(0xffffffffu, wrap ? nR : nL, src, NS);
+                        nR = wrap ? nL : nR;
+                        nL = r;
                     }
                     const int rc = __shfl_sync(0xffffffffu, wrap ? colR : colL, src, NS);
                     colR = wrap ? colL : colR;
@@ -505,12 +556,12 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
     }
 }
 
-template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64>
+template <typename T, int NS, int PARTS, int RA, int RV, int MINB, bool FAST, bool PRE, bool P64, bool CARRY>
 static int launch_reg(int batch, void* const* A, const int* M, const int* N, const int* LDA, void* const* S,
                       void* const* U, const int* LDU, void* const* V, const int* LDV, double tol, int max_sweeps,
                       int* info, long long* rot, cudaStream_t st, ItemList wl)
 {
-    auto kern = jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST, PRE, P64 && sizeof(T) == 4>;
+    auto kern = jacobi_reg_kernel<T, NS, PARTS, RA, RV, MINB, FAST, PRE, P64 && sizeof(T) == 4, CARRY>;
     const int grid = item_grid(kern, NS * PARTS, 0, wl, batch, st);
     if (grid == 0) return BSVD_ERR_CUDA;
     kern<<<grid, NS * PARTS, 0, st>>>(
@@ -520,33 +571,39 @@ static int launch_reg(int batch, void* const* A, const int* M, const int* N, con
 }
 
 // Register-tier variants (slots, row parts, A rows per lane, V rows per lane, resident CTAs, scaled
-// rotations, QR preconditioning, FP64 rotation parameters), in order of preference.  `variant` 0
+// rotations, QR preconditioning, FP64 rotation parameters, carried column norms), in order of
+// preference.  `variant` 0
 // launches the first that fits the shape bound; k > 0 launches the k-th fitting one; a negative
 // `variant` only counts the fitting ones (returned).  The preconditioned ones need square bounds
 // and are listed after the plain ones, so that variant 0 stays unpreconditioned; the FP32 variants
 // with FP64 rotation parameters (zeta, t, c, s and the rotation test in FP64, the data and the Gram
-// sums in FP32) come last.
+// sums in FP32) come next, the carried-norm ones last.
 #define BSVD_REG_VARIANTS_F32(X)                                                                        \
-    X(16, 2, 16, 16, 16, true, false, false) /* n <= 32, m <= 32: one warp per matrix */                \
-    X(16, 2, 32, 16, 12, true, false, false) /* n <= 32, m <= 64 */                                     \
-    X(32, 2, 32, 32, 6, true, false, false)  /* n <= 64, m <= 64: two warps, 3 warps per SMSP */        \
-    X(32, 2, 32, 32, 4, true, false, false)  /*   ... 2 warps per sub-partition, no register cap */     \
-    X(32, 2, 32, 32, 6, false, false, false) /*   ... rotations applied as written */                   \
-    X(32, 4, 16, 16, 4, true, false, false)  /*   ... four warps, 128-register cap */                   \
-    X(16, 4, 32, 8, 4, true, false, false)   /* n <= 32, m <= 128 */                                    \
-    X(32, 4, 32, 16, 2, true, false, false)  /* n <= 64, m <= 128 */                                    \
-    X(16, 2, 16, 16, 16, true, true, false)  /* 32 x 32, QR-preconditioned */                           \
-    X(32, 2, 32, 32, 6, true, true, false)   /* 64 x 64, QR-preconditioned */                           \
-    X(32, 2, 32, 32, 6, true, false, true)   /* n <= 64, m <= 64, FP64 rotation parameters */           \
-    X(32, 2, 32, 32, 6, true, true, true)    /* 64 x 64, QR-preconditioned, FP64 rotation parameters */
+    X(16, 2, 16, 16, 16, true, false, false, false) /* n <= 32, m <= 32: one warp per matrix */                \
+    X(16, 2, 32, 16, 12, true, false, false, false) /* n <= 32, m <= 64 */                                     \
+    X(32, 2, 32, 32, 6, true, false, false, false)  /* n <= 64, m <= 64: two warps, 3 warps per SMSP */        \
+    X(32, 2, 32, 32, 4, true, false, false, false)  /*   ... 2 warps per sub-partition, no register cap */     \
+    X(32, 2, 32, 32, 6, false, false, false, false) /*   ... rotations applied as written */                   \
+    X(32, 4, 16, 16, 4, true, false, false, false)  /*   ... four warps, 128-register cap */                   \
+    X(16, 4, 32, 8, 4, true, false, false, false)   /* n <= 32, m <= 128 */                                    \
+    X(32, 4, 32, 16, 2, true, false, false, false)  /* n <= 64, m <= 128 */                                    \
+    X(16, 2, 16, 16, 16, true, true, false, false)  /* 32 x 32, QR-preconditioned */                           \
+    X(32, 2, 32, 32, 6, true, true, false, false)   /* 64 x 64, QR-preconditioned */                           \
+    X(32, 2, 32, 32, 6, true, false, true, false)   /* n <= 64, m <= 64, FP64 rotation parameters */           \
+    X(32, 2, 32, 32, 6, true, true, true, false)    /* 64 x 64, QR-preconditioned, FP64 rotation parameters */ \
+    X(16, 2, 16, 16, 16, true, true, false, true)   /* 32 x 32, QR-preconditioned, carried column norms */  \
+    X(32, 2, 32, 32, 6, true, false, false, true)   /* n <= 64, m <= 64, carried column norms */            \
+    X(32, 2, 32, 32, 6, true, true, false, true)    /* 64 x 64, QR-preconditioned, carried column norms */
 #define BSVD_REG_VARIANTS_F64(X)                                                                        \
-    X(16, 2, 16, 16, 8, true, false, false)  /* n <= 32, m <= 32: one warp per matrix */                \
-    X(16, 2, 16, 16, 8, false, false, false)                                                            \
-    X(16, 2, 16, 16, 12, true, false, false)                                                            \
-    X(16, 4, 16, 8, 5, true, false, false)   /* n <= 32, m <= 64 */                                     \
-    X(32, 4, 16, 16, 2, true, false, false)  /* n <= 64, m <= 64 */                                     \
-    X(16, 2, 16, 16, 8, true, true, false)   /* 32 x 32, QR-preconditioned */                           \
-    X(32, 4, 16, 16, 2, true, true, false)   /* 64 x 64, QR-preconditioned */
+    X(16, 2, 16, 16, 8, true, false, false, false)  /* n <= 32, m <= 32: one warp per matrix */                \
+    X(16, 2, 16, 16, 8, false, false, false, false)                                                            \
+    X(16, 2, 16, 16, 12, true, false, false, false)                                                            \
+    X(16, 4, 16, 8, 5, true, false, false, false)   /* n <= 32, m <= 64 */                                     \
+    X(32, 4, 16, 16, 2, true, false, false, false)  /* n <= 64, m <= 64 */                                     \
+    X(16, 2, 16, 16, 8, true, true, false, false)   /* 32 x 32, QR-preconditioned */                           \
+    X(32, 4, 16, 16, 2, true, true, false, false)   /* 64 x 64, QR-preconditioned */                       \
+    X(16, 2, 16, 16, 8, true, true, false, true)    /* 32 x 32, QR-preconditioned, carried column norms */  \
+    X(32, 4, 16, 16, 2, true, true, false, true)    /* 64 x 64, QR-preconditioned, carried column norms */
 
 #define BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_) \
     (nn <= 2 * (NS_) && mm <= (PARTS_) * (RA_) && nn <= (PARTS_) * (RV_) && (!(PRE_) || max_m == max_n))
@@ -559,12 +616,12 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
     const int mm = max_m > max_n ? max_m : max_n;
     const int nn = max_m > max_n ? max_n : max_m;
     int seen = 0;
-#define BSVD_TRY(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_)                                               \
+#define BSVD_TRY(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_, CARRY_)                                       \
     if (BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_)) {                                                               \
         ++seen;                                                                                             \
         if (variant == 0 || variant == seen)                                                                \
-            return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_>(batch, A, M, N, LDA, S, U, LDU, V, \
-                                                                           LDV, tol, max_sweeps, info, rot, st, wl); \
+            return launch_reg<T, NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_, CARRY_>(                        \
+                batch, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info, rot, st, wl);                      \
     }
     if constexpr (sizeof(T) == 4) {
         BSVD_REG_VARIANTS_F32(BSVD_TRY)
@@ -577,16 +634,17 @@ int launch_jacobi_reg(int batch, int max_m, int max_n, int variant, void* const*
 
 // The k-th (k >= 1) register-tier variant fitting the bounds: desc = {slots, parts, A rows per
 // lane, V rows per lane, resident CTAs, scaled rotations, QR preconditioning, FP64 rotation
-// parameters}; 0, or BSVD_ERR_UNSUPPORTED when there is no k-th variant.
+// parameters, carried column norms}; 0, or BSVD_ERR_UNSUPPORTED when there is no k-th variant.
 int jacobi_reg_variant_desc(bool f64, int max_m, int max_n, int k, int* desc)
 {
     const int mm = max_m > max_n ? max_m : max_n;
     const int nn = max_m > max_n ? max_n : max_m;
     int seen = 0;
-#define BSVD_DESC(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_)                                        \
+#define BSVD_DESC(NS_, PARTS_, RA_, RV_, MINB_, FAST_, PRE_, P64_, CARRY_)                                \
     if (BSVD_FITS(NS_, PARTS_, RA_, RV_, PRE_) && ++seen == k) {                                        \
-        const int d[8] = {NS_, PARTS_, RA_, RV_, MINB_, (FAST_) ? 1 : 0, (PRE_) ? 1 : 0, (P64_) ? 1 : 0}; \
-        for (int i = 0; i < 8; ++i) desc[i] = d[i];                                                     \
+        const int d[9] = {NS_, PARTS_, RA_, RV_, MINB_, (FAST_) ? 1 : 0, (PRE_) ? 1 : 0, (P64_) ? 1 : 0,  \
+                          (CARRY_) ? 1 : 0};                                                            \
+        for (int i = 0; i < 9; ++i) desc[i] = d[i];                                                     \
         return BSVD_SUCCESS;                                                                            \
     }
     if (!f64) {

@@ -27,7 +27,14 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
                        int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl = all_items(),
                        bool p64 = false);  // p64: FP32 data, FP64 rotation parameters
 template <typename T>
-size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);
+size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);  // method: base | QR flag
+template <typename T>
+size_t block_jacobi_qr_workspace(int batch, int max_m, int max_n, int bw, int method);
+template <typename T>
+int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
+                           const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU,
+                           void* const* V, const int* LDV, double tol, int max_sweeps, int* info, long long* rot,
+                           void* ws, size_t ws_bytes, cudaStream_t st);
 template <typename T>
 int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
                         const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,
@@ -41,5 +48,18 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
                 int rounds, unsigned long long seed, int flags, void* const* dU, const int* LDU, void* const* dS,
                 void* const* dV, const int* LDV, int* rank_out, float* err_est, int* samples, int* info, void* ws,
                 size_t ws_bytes, cudaStream_t st);
+
+template <typename T>
+size_t h2_truncate_workspace(int depth, int k, int max_leaf_m);
+template <typename T>
+int launch_h2_truncate(int depth, int k, int max_leaf_m, void* const* leaf, const int* leaf_m, const int* leaf_ld,
+                       void* const* transfer, double eps, void* const* new_leaf, const int* new_leaf_ld,
+                       void* const* new_transfer, void* const* Tout, int* rank, int* info, long long* rot, void* ws,
+                       size_t ws_bytes, cudaStream_t st);
+
+// Y(:, 0:l) = A Omega on the tensor cores (TF32, FP32 accumulation), Y(:, l:l+8) = A W in FP32
+// (randomized SVD sampling, FP32 data, m, n <= 256, l <= 128, Y with leading dimension m)
+int launch_rs_sample_tc(int batch, ItemList wl, float* const* A, const int* LDA, float* const* Y, const int* M,
+                        const int* N, const int* L, unsigned long long seed, int* timeouts, cudaStream_t st);
 
 }  // namespace bsvd

@@ -113,12 +113,16 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
     // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
-    // 24-30 inner sweep cap
-    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | (0x7f << 24))) return -17;
+    // 18 QR preconditioning, 24-30 inner sweep cap
+    if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | BSVD_BLOCK_QR_PRECONDITION |
+                   (0x7f << 24)))
+        return -17;
     if (!d_info) return -18;
     const size_t need = dtype == BSVD_F32
-                            ? bsvd::block_jacobi_workspace<float>(batch, max_m, max_n, block_width, method & 0xff)
-                            : bsvd::block_jacobi_workspace<double>(batch, max_m, max_n, block_width, method & 0xff);
+                            ? bsvd::block_jacobi_workspace<float>(batch, max_m, max_n, block_width,
+                                                                  method & (0xff | BSVD_BLOCK_QR_PRECONDITION))
+                            : bsvd::block_jacobi_workspace<double>(batch, max_m, max_n, block_width,
+                                                                   method & (0xff | BSVD_BLOCK_QR_PRECONDITION));
     if (need > kScratchBytes) return BSVD_ERR_SCRATCH_LIMIT;
     void* ws = scratch_address();
     if (!ws) return BSVD_ERR_CUDA;

@@ -16,7 +16,9 @@
 
 namespace bsvd {
 
-template <typename T>
+// QROWS: rows per lane of the register-resident Q formation (m <= 32 QROWS; taller matrices
+// accumulate Q backwards in shared memory)
+template <typename T, int QROWS>
 __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const int* M, const int* N,
                           const int* LDA, T* const* Q, const int* LDQ, T* const* R, const int* LDR,
                           int* info, ItemList wl, int r_trans, const int* a_trans)
@@ -44,23 +46,27 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         if (tid == 0) info[b] = 0;
         if (n == 0) continue;
         const T* a = A[b];
+        int nonfinite = 0;  // a NaN or an infinity in A (the factorisation would take a NaN norm for 0)
         if (!at) {
             for (int j = warp; j < n; j += nwarps)
-                for (int i = lane; i < m; i += 32) S[j * ld + i] = a[(size_t)j * lda + i];
+                for (int i = lane; i < m; i += 32) {
+                    const T x = a[(size_t)j * lda + i];
+                    nonfinite |= !isfinite(x);
+                    S[j * ld + i] = x;
+                }
         } else {
             // S(i, j) = A(j, i): row i of S is column i of the stored matrix (coalesced reads)
             for (int i = warp; i < m; i += nwarps)
-                for (int j = lane; j < n; j += 32) S[j * ld + i] = a[(size_t)i * lda + j];
+                for (int j = lane; j < n; j += 32) {
+                    const T x = a[(size_t)i * lda + j];
+                    nonfinite |= !isfinite(x);
+                    S[j * ld + i] = x;
+                }
         }
-        __syncthreads();
+        if (__syncthreads_or(nonfinite) && tid == 0) info[b] = BSVD_INFO_NONFINITE;
 
         // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
         house_factor_smem(S, ld, diag, m, n);
-        if (tid == 0) {  // a NaN or infinity anywhere in A reaches the norm of its column's reflector
-            bool finite = true;
-            for (int i = 0; i < n; ++i) finite = finite && isfinite(diag[i]);
-            if (!finite) info[b] = BSVD_INFO_NONFINITE;
-        }
 
         // ---- R: strict upper part from S, diagonal from diag, zeros below ----
         if (R) {
@@ -72,8 +78,38 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         }
         __syncthreads();
 
-        // ---- Q = H_0 ... H_{n-1} [I; 0], backward, in place ----
-        if (Q) {
+        // ---- Q = H_0 ... H_{n-1} [I; 0] ----
+        if (Q && m <= 32 * QROWS) {
+            // column j of Q is H_0 H_1 ... H_j e_j (H_i e_j = e_j for i > j): every column on its own,
+            // one warp per column, in registers (rows lane + 32 t), with no barrier
+            T* q_out = Q[b];
+            for (int j = warp; j < n; j += nwarps) {
+                T q[QROWS];
+#pragma unroll
+                for (int t = 0; t < QROWS; ++t) q[t] = (lane + 32 * t == j) ? T(1) : T(0);
+                for (int i = j; i >= 0; --i) {
+                    const T* v = S + (size_t)i * ld;
+                    T w = T(0);
+#pragma unroll
+                    for (int t = 0; t < QROWS; ++t) {
+                        const int r = lane + 32 * t;
+                        if (r >= i && r < m) w = fma(v[r], q[t], w);
+                    }
+                    w = T(2) * warp_sum(w);
+#pragma unroll
+                    for (int t = 0; t < QROWS; ++t) {
+                        const int r = lane + 32 * t;
+                        if (r >= i && r < m) q[t] = fma(-w, v[r], q[t]);
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < QROWS; ++t) {
+                    const int r = lane + 32 * t;
+                    if (r < m) q_out[(size_t)j * ldq + r] = q[t];
+                }
+            }
+        } else if (Q) {
+            // taller matrices: backward accumulation in place
             for (int i = n - 1; i >= 0; --i) {
                 const T* col = S + i * ld;
                 for (int j = i + 1 + warp; j < n; j += nwarps) {
@@ -107,14 +143,17 @@ int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, con
 {
     const size_t smem = ((size_t)(max_m | 1) * max_n + max_n) * sizeof(T);
     const int threads = max_n <= 32 ? 128 : 256;
+    // rows per lane of the register Q formation from the batch's row bound
+    auto kern = max_m <= 32 ? qr_kernel<T, 1> : (max_m <= 64 ? qr_kernel<T, 2> : (max_m <= 128 ? qr_kernel<T, 4>
+                                                                                             : qr_kernel<T, 8>));
     if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BSVD_ERR_CUDA;
     }
-    const int grid = item_grid(qr_kernel<T>, threads, smem, wl, batch, st);
+    const int grid = item_grid(kern, threads, smem, wl, batch, st);
     if (grid == 0) return BSVD_ERR_CUDA;
-    qr_kernel<T><<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ,
-                                              (T* const*)R, LDR, info, wl, r_transposed ? 1 : 0, a_trans);
+    kern<<<grid, threads, smem, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ, (T* const*)R,
+                                      LDR, info, wl, r_transposed ? 1 : 0, a_trans);
     return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
 }
 

@@ -26,7 +26,7 @@
 //            first k columns of U, V and k values of S to the caller.
 // Full-rank blocks: min(m, n) <= 64 by A = Q R (A^T when m < n), the register-tier SVD of R^T and
 // a batched GEMM for the Q side; up to 128 (FP32) by the shared tier; above by the block-Jacobi
-// tier.  FP64 runs every stage in FP64 (the Gaussian samples too).
+// tier on R^T of a blocked Householder QR.  FP64 runs every stage in FP64 (the Gaussian samples too).
 // Every stage runs over a device list of the blocks it concerns.
 #include <cuda_runtime.h>
 
@@ -47,6 +47,10 @@ template <> struct RsCap<float> { static constexpr int l = 128, smem = 128; };
 template <> struct RsCap<double> { static constexpr int l = 64, smem = 64; };
 
 enum { RS_RSVD = 0, RS_FULL = 1, RS_DONE = 2 };
+
+// full-rank blocks above the shared tier: GRAM block Jacobi on R^T of a blocked Householder QR
+// (about half the outer sweeps of the block tier on A)
+constexpr int kBlockMethod = BSVD_BLOCK_GRAM | BSVD_BLOCK_QR_PRECONDITION;
 enum { RSF_FALLBACK = 1, RSF_FROM_FULL = 2, RSF_NO_SCRATCH = 4 };
 
 struct RsState {
@@ -564,6 +568,10 @@ __global__ void __launch_bounds__(256) rs_finish_kernel(RsArrays<T> ar, T* const
     const int b = blockIdx.x;
     RsState* s = ar.st + b;
     if (info[b] == BSVD_INFO_BAD_SHAPE) return;
+    if (ar.cnt[7] != 0) {  // a tensor-core completion wait gave up: the call's results are not valid
+        if (threadIdx.x == 0) info[b] = BSVD_INFO_DEVICE_TIMEOUT;
+        return;
+    }
     if (info[b] == BSVD_INFO_NONFINITE) {
         if (threadIdx.x == 0) rank_out[b] = 0;
         return;
@@ -644,7 +652,7 @@ static RsFixed rs_fixed(int batch, int max_m, int max_n)
     o = al256(o + sizeof(unsigned long long) * 8 + sizeof(int) * 8);  // claim counters, list lengths
     F.off_bjws = o;
     const int kmx = max_m < max_n ? max_m : max_n;
-    F.bj_bytes = kmx > RsCap<T>::smem ? block_jacobi_workspace<T>(batch, max_m, max_n, 32, 0) : 0;
+    F.bj_bytes = kmx > RsCap<T>::smem ? block_jacobi_workspace<T>(batch, max_m, max_n, 32, kBlockMethod) : 0;
     o = al256(o + F.bj_bytes);
     F.off_scratch = o;
     return F;
@@ -709,6 +717,8 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     ar.pS64 = dp + 3 * (size_t)batch;
     // the small SVDs (of R_B^T, and of R^T on the full-rank QR path) in FP64: FP32 runs only
     const bool small64 = sizeof(T) == 4 && (flags & BSVD_RSVD_SMALL_FP64) != 0;
+    // the sampling product on the tensor cores: FP32 runs only
+    const bool tc_sample = sizeof(T) == 4 && (flags & BSVD_RSVD_TC_SAMPLING) != 0;
     int* ip = reinterpret_cast<int*>(w + F.off_int);
     int** islots[kIntArrays] = {&ar.m_act, &ar.n_act, &ar.l_act, &ar.lp_act, &ar.l_reg, &ar.l_smem,
                                 &ar.ld_m, &ar.ld_n, &ar.ld_l, &ar.m_reg, &ar.n_reg, &ar.m_smem,
@@ -722,6 +732,8 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     auto listed = [&](const int* idx, int which) { return ItemList{idx, ar.cnt + which, claim}; };
     const long long capacity = (long long)((ws_bytes - F.off_scratch) / sizeof(T));
 
+    // tensor-core waits that gave up (cnt[7]; the round memsets clear only the list lengths)
+    if (cudaMemsetAsync(ar.cnt + 7, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
     rs_plan_kernel<T><<<batch, 256, 0, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, fixed, hint, tol_arr, tol,
                                              p, ar.st, info);
     rs_scan_kernel<<<1, 1024, 0, st>>>(batch, ar.st, capacity, info);
@@ -737,8 +749,14 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
         if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RL_COUNT, st) != cudaSuccess) return BSVD_ERR_CUDA;
         rs_arrays_kernel<T><<<tb, 128, 0, st>>>(batch, scratch, ar, 0);
         // sample: Y = A [Omega | probes]
-        rc = gemm<false, true, T>(batch, act, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act, ar.n_act,
-                                  ar.l_act, seed, st);
+        if constexpr (sizeof(T) == 4) {
+            if (tc_sample)
+                rc = launch_rs_sample_tc(batch, act, fA, LDA, ar.pY, ar.m_act, ar.n_act, ar.l_act, seed, ar.cnt + 7,
+                                         st);
+        }
+        if (!tc_sample)
+            rc = gemm<false, true, T>(batch, act, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act,
+                                      ar.n_act, ar.l_act, seed, st);
         if (rc) break;
         rc = launch_qr<T>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY, ar.ld_m,
                           (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
@@ -832,7 +850,7 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
         }
         if (kx > RsCap<T>::smem) {
             // the block tier keeps its own list of live matrices: blocks not routed to it are 0 x 0
-            rc = launch_block_jacobi<T>(batch, mx, nx, 32, 0, A, ar.m_blk, ar.n_blk, LDA, (void* const*)ar.pS,
+            rc = launch_block_jacobi<T>(batch, mx, nx, 32, kBlockMethod, A, ar.m_blk, ar.n_blk, LDA, (void* const*)ar.pS,
                                         (void* const*)ar.pUw, ar.ld_m, (void* const*)ar.pVw, ar.ld_n, 0.0, 0, ar.info,
                                         nullptr, w + F.off_bjws, F.bj_bytes, st);
             if (rc) return rc;

@@ -66,7 +66,7 @@ def test_host_argument_checks_without_gpu(lib):
     # block Jacobi: unknown `method` bits are refused before anything is launched (the pointers
     # are never dereferenced: the checks return first)
     p = 64
-    for bad in (1 << 18, 1 << 20, 2, -(1 << 30)):
+    for bad in (1 << 19, 1 << 20, 2, -(1 << 30)):
         assert L.batched_svd_block_jacobi(0, 1, 64, 64, p, p, p, p, p, p, p, p, p, 0.0, 0, 32, bad, p, z, p, 1 << 20,
                                           z) == -17, bad
 
@@ -95,9 +95,11 @@ def test_variant_descriptions(lib):
     for code, (m, n) in [(0, (64, 64)), (0, (32, 32)), (1, (32, 32)), (1, (64, 64)), (0, (128, 48)), (1, (64, 60))]:
         nv = L.bsvd_jacobi_variants(code, m, n, bs.TIER_REGISTER)
         descs = [bs.jacobi_variant_desc(code, m, n, k) for k in range(1, nv + 1)]
-        p64 = [d["fp64_params"] for d in descs]
+        car = [d["carried_norms"] for d in descs]
+        assert car == sorted(car), (code, m, n, car)             # carried-norm variants last
+        p64 = [d["fp64_params"] for d in descs if not d["carried_norms"]]
         assert p64 == sorted(p64) and (code == 0 or not any(p64)), (code, m, n, p64)
-        pre = [d["qr_precond"] for d in descs if not d["fp64_params"]]
+        pre = [d["qr_precond"] for d in descs if not d["fp64_params"] and not d["carried_norms"]]
         assert pre == sorted(pre), (code, m, n, pre)             # preconditioned ones last
         assert any(pre) == (m == n), (code, m, n, pre)
         for d in descs:                                          # every one fits the bounds
@@ -106,7 +108,7 @@ def test_variant_descriptions(lib):
         with pytest.raises(bs.BsvdError):
             bs.jacobi_variant_desc(code, m, n, nv + 1)
     import ctypes
-    d = (ctypes.c_int * 8)()
+    d = (ctypes.c_int * 9)()
     assert L.bsvd_jacobi_variant_desc(2, 64, 64, 1, d) == -1
     assert L.bsvd_jacobi_variant_desc(0, -1, 64, 1, d) == -2
     assert L.bsvd_jacobi_variant_desc(0, 64, 64, 0, d) == -4

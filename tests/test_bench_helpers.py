@@ -91,6 +91,8 @@ def test_launch_counts_follow_the_host_drivers():
     # randomized SVD of blocks up to 256 x 256, 4 rounds: plan + scan, 15 per round (the shared
     # tier joins the register tier for the small SVD), fallback + arrays, the QR path (4), the
     # shared tier, the block tier over 256 columns (8 blocks, 7 steps) and the finish kernel
-    assert bench.rsvd_launches(256, 256, 4) == 2 + 4 * 15 + 2 + 4 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1
+    # the block tier on R^T of a blocked QR: setup, 8 panels, 7 trailing updates, R^T, the block
+    # Jacobi, the zero fill, 8 block-reflector applications
+    assert bench.rsvd_launches(256, 256, 4) == 2 + 4 * 15 + 2 + 4 + 1 + (1 + 8 + 7 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1 + 8) + 1
     # blocks up to 64 x 64: no shared or block tier
     assert bench.rsvd_launches(64, 64, 4) == 2 + 4 * 14 + 2 + 4 + 1

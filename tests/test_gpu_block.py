@@ -31,15 +31,22 @@ def w2():
     return b, mats, So
 
 
-@pytest.mark.parametrize("method,bw", [(0, 32), (1, 32), (0, 16), (1, 16), (0 | (1 << 16), 32)])
+QR = 1 << 18   # BSVD_BLOCK_QR_PRECONDITION
+
+
+@pytest.mark.parametrize("method,bw", [(0, 32), (1, 32), (0, 16), (1, 16), (0 | (1 << 16), 32), (0 | QR, 32),
+                                       (1 | QR, 32), (0 | QR, 16)])
 def test_block_512_log_uniform_sigma(bs, w2, method, bw):
     """FP32 with bw = 32 forms the pair Gram matrices on the tensor cores; the BLOCK_SIMT_PRODUCTS
-    flag keeps them on the SIMT pipes."""
+    flag keeps them on the SIMT pipes; BLOCK_QR_PRECONDITION runs the block Jacobi on R^T of a
+    blocked Householder QR and forms U = Q V~ (about half the outer sweeps)."""
     b, mats, So = w2
     a = torch.from_numpy(b.a).cuda()
     u, s, v, info, rots = bs.svd_block(a, block_width=bw, method=method, max_sweeps=30)
-    method &= 0xff
     torch.cuda.synchronize()
+    if method & QR:      # fewer outer sweeps than on A itself (14-15 on these matrices)
+        assert int(info.cpu().numpy().max()) <= 11, info.cpu().numpy()
+    method &= 0xff
     u, s, v = _host(u, s, v)
     info = info.cpu().numpy()
     for i in range(b.batch):
@@ -52,7 +59,7 @@ def test_block_512_log_uniform_sigma(bs, w2, method, bw):
 
 @pytest.mark.parametrize("bw", [16, 32])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("method", [0, 1, 0 | QR, 1 | QR])
 def test_block_ragged_shapes(bs, dt, method, bw):
     """Partial last block, a virtual empty block, wide input, tiny block counts."""
     shapes = [(96, 80), (70, 130), (64, 64), (200, 33), (33, 33), (5, 3)]

@@ -280,3 +280,39 @@ def test_rsvd_bad_tolerance_flags_the_matrix(bs):
     tol = np.array([1e-5, -1.0, float("nan"), 1.5])
     res = _run_mode(bs, rb, np.float32, tol_per=tol)
     assert res.info_h[0] >= 0 and list(res.info_h[1:]) == [-1, -1, -1]
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_rsvd_precision_options_match_the_oracle(bs, flags):
+    """BSVD_RSVD_SMALL_FP64 (1: the small SVDs in FP64) and BSVD_RSVD_TC_SAMPLING (2: the sample A Omega
+    on the tensor cores, TF32 operands, FP32 accumulation, the probes in FP32): fixed-rank sigma against
+    the oracle's fixed-rank RSVD at the same l, and in tolerance mode the error gate, Eckart-Young and
+    orthogonality on every block, sigma against the oracle at the sample count used.
+
+    The tensor-core sample is A Omega read with 10-bit mantissas: a sample of a slightly different
+    Gaussian matrix, so its rank-l approximation A~ differs from the oracle's A^ (exact Omega) by up to
+    the two approximations' errors.  By Weyl's inequality |sigma_i(A~) - sigma_i(A^)| <= ||A - A~||_2 +
+    ||A - A^||_2: with the TC sample sigma is compared within 1e-5 sigma_1 plus those two errors (each
+    measured in FP64), and the TC approximation's error must stay within twice the oracle's (plus
+    1e-5 ||A||_2: the same quality of sample)."""
+    rb = gen.rsvd_uneven_blocks(batch=32, sizes=(64, 128, 256))
+    kk = np.minimum(rb.m, rb.n)
+    k = np.maximum(1, (rb.extra["rank_hint"] * 0.7).astype(np.int32))
+    res = _run_mode(bs, rb, np.float32, fixed_rank=k, flags=flags)
+    assert np.all(res.info_h >= 0)
+    for b in range(rb.batch):
+        a = rb.a64(b)
+        Uo, So, Vo, l = O.rsvd_rank(a, SEED, b, int(k[b]), 8, 1, 128)
+        assert int(res.samples_h[b]) == l and int(res.rank_h[b]) == min(int(k[b]), int(kk[b]))
+        u, s, v = _unpack(res, b)
+        tol = 1e-5 * So[0]
+        if flags & 2 and l < kk[b]:
+            e_o = np.linalg.norm(a - (Uo * So) @ Vo.T, 2)
+            e_g = np.linalg.norm(a - (u * s) @ v.T, 2)
+            assert e_g <= 2 * e_o + 1e-5 * So[0], (b, e_g, e_o)
+            tol += e_o + e_g
+        assert np.abs(s - So).max() <= tol, (b, np.abs(s - So).max() / So[0])
+    res = _run_mode(bs, rb, np.float32, rank_hint=rb.extra["rank_hint"] // 2, max_rounds=8, flags=flags)
+    assert np.all(res.info_h >= 0)
+    for b in range(rb.batch):
+        _check_block(rb, res, b)
