@@ -35,10 +35,42 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.070 GHz maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# FP64 peak of the part (GB300 data sheet figure)
-FP64_PEAK_TFLOPS = 1.25
+# ALU peaks the FP32 / FP64 rooflines divide by.  Measured at start-up by the library's FMA probe
+# (bsvd_fma_probe: 16 independent FMA chains per thread, 8 CTAs of 256 threads per SM, timed with
+# CUDA events, best of five); the nominal figures below are used only when the probe cannot run.
+PEAKS = {
+    "fp32": {"tflops": 152 * 128 * 2 * 2.070e9 / 1e12,
+             "note": "nominal FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (probe not run)"},
+    "fp64": {"tflops": 1.25, "note": "nominal FP64: GB300 data sheet (probe not run)"},
+}
+
+
+def measure_alu_peaks(bs, dev, local_rank=0):
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s), with the SM clock sampled meanwhile."""
+    import torch
+    stream = torch.cuda.current_stream()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = nsm * 8
+    for key, code, iters, dt in (("fp32", bs.F32, 20000, torch.float32), ("fp64", bs.F64, 400, torch.float64)):
+        out = torch.empty(blocks * 256, device=dev, dtype=dt)
+        flops = bs.fma_probe(code, blocks, iters, out, stream)        # warm-up
+        torch.cuda.synchronize()
+        clocks = Clocks(local_rank)
+        clocks.start()
+        best = float("inf")
+        w0 = time.time()
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bs.fma_probe(code, blocks, iters, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        ck = clocks.stop(w0, time.time())
+        PEAKS[key] = {"tflops": flops / (best * 1e-3) / 1e12,
+                      "note": f"measured: bsvd_fma_probe ({blocks} CTAs x 256 threads x {iters} x 16 FMAs, "
+                              f"best of 5 = {best:.3f} ms)", "clocks": ck}
+    return PEAKS
 
 
 def measured_hbm_gbs() -> float:
@@ -53,10 +85,6 @@ def measured_hbm_gbs() -> float:
 # digest of the kernel's sources at capture time: a changed kernel has no entry and reports null
 # traffic, not stale counters.  profiles/ holds the capture summaries.
 TRAFFIC = {
-    # jacobi_reg_kernel, 64x64 FP32, QR-preconditioned variant (tier 0x601): 440.9 MB for 10 000
-    # matrices, scaled to 20 000.  Captured at digest 324d9b169c8f96bf; rekeyed after common.cuh
-    # made round_robin_pair host-callable (a qualifier on a function this kernel does not call)
-    "jacobi_reg:d9fd4d969fabfce6": 881.8e6,
 }
 
 
@@ -151,6 +179,14 @@ def block_jacobi_launches(n_cols, bw=32, sweeps=20):
     return 1 + sweeps * ((nblk - 1) * 4 + 1) + 1
 
 
+def block_qr_launches(n_cols, bw=32, sweeps=20):
+    """Kernels of a QR-preconditioned block-Jacobi call: setup, per 32-column panel the panel kernel
+    and (but the last) the trailing update, R^T, the block Jacobi on R^T, the left vectors' zero
+    fill and one block-reflector application per panel."""
+    p = -(-n_cols // 32)
+    return 1 + p + (p - 1) + 1 + block_jacobi_launches(n_cols, bw, sweeps) + 1 + p
+
+
 def rsvd_launches(max_m, max_n, rounds):
     """Kernels one batched_rsvd call launches: plan and scan; per round the arrays kernel, four
     GEMM + QR pairs (sample, power step, projection), the small SVD (register tier, plus the shared
@@ -162,7 +198,7 @@ def rsvd_launches(max_m, max_n, rounds):
     per_round = 14 + (1 if lx > 64 else 0)
     n = 2 + rounds * per_round + 2
     if kx > 0:
-        n += 4 + (1 if kx > 64 else 0) + (block_jacobi_launches(kx) if kx > 128 else 0)
+        n += 4 + (1 if kx > 64 else 0) + (block_qr_launches(kx) if kx > 128 else 0)
     return n + 1
 
 
@@ -230,7 +266,13 @@ class SvdQr64:
         self.R = torch.empty((self.nq, 32, 32), device=dev)
         self.Qb, self.Rb = bs.Batch.uniform(self.Q, 128, 32), bs.Batch.uniform(self.R, 32, 32)
         self.qinfo = torch.empty(self.nq, dtype=torch.int32, device=dev)
-        self.tuned = autotune.tune_jacobi(self.d_svd, m, n)
+        if getattr(self.args, "jacobi_tier", None):
+            # a given register variant instead of the autotuner's choice (profiling runs)
+            t = int(self.args.jacobi_tier, 0)
+            bs.set_jacobi_choice(bs.F32, m, n, t)
+            self.tuned = {"tier": t, "ms": None, "sample": 0, "all_ms": {}, "forced": True}
+        else:
+            self.tuned = autotune.tune_jacobi(self.d_svd, m, n)
         self.outs = [self.S, self.U, self.V, self.Q, self.R]
         self.d_in = [self.d_svd, self.d_qr]
 
@@ -274,12 +316,51 @@ class SvdQr64:
         traffic = TRAFFIC.get("jacobi_reg:" + kernel_digest("jacobi_reg.cu")) if reg else None
         if traffic is not None:
             traffic *= self.nb / 20000  # per launch: scales with the matrix count
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "ms_per_launch": kernel_ms,
-                "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (max SM clock)"}
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": PEAKS["fp32"]["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / PEAKS["fp32"]["tflops"], "traffic": traffic, "ms_per_launch": kernel_ms,
+                "peak_note": PEAKS["fp32"]["note"]}
         detail = {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
                   "jacobi_gflop_per_launch": fl / 1e9, "autotune": self.tuned}
         return roof, detail
+
+    def extra_arms(self, stream, steps, warmup, time_fn):
+        """The register variant of the tuned one's shape (carried norms off) with its rotation
+        parameters (zeta, t, c, s) and rotation test in FP32, and the same with them in FP64 from the
+        FP32 Gram sums: the cost of the FP64 parameters, measured side by side."""
+        import torch
+        bs = self.bs
+        tier = int(self.tuned["tier"])
+        if (tier & 0xff) != bs.TIER_REGISTER:
+            return {}
+        base = dict(bs.jacobi_variant_desc(bs.F32, 64, 64, tier >> 8 or 1), carried_norms=0)
+        nv = bs.jacobi_variants(bs.F32, 64, 64, bs.TIER_REGISTER)
+        descs = {k: bs.jacobi_variant_desc(bs.F32, 64, 64, k) for k in range(1, nv + 1)}
+        k32 = next((k for k, d in descs.items() if d == dict(base, fp64_params=0)), None)
+        k64 = next((k for k, d in descs.items() if d == dict(base, fp64_params=1)), None)
+        if k32 is None or k64 is None:
+            return {}
+        out = {}
+        for name, k in (("fp32", k32), ("fp64", k64)):
+            t_k = bs.TIER_REGISTER | (k << 8)
+
+            def step(st, kev=None, t_k=t_k):
+                if kev is not None:
+                    kev[0].record(st)
+                bs.batched_svd_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.rots, tier=t_k, stream=st)
+                if kev is not None:
+                    kev[1].record(st)
+            for _ in range(warmup):
+                step(stream)
+            torch.cuda.synchronize()
+            t = time_fn(step)
+            info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
+            fl = jacobi_flops(64, 64, info_h, rots_h, bool(base["qr_precond"]))
+            achieved = fl / (t["kernel_ms"] * 1e-3) / 1e12
+            out[name] = {"tier": hex(t_k), "ms_per_launch": t["kernel_ms"], "clocks": t["clocks"],
+                         "achieved_tflops": achieved, "frac": achieved / PEAKS["fp32"]["tflops"],
+                         "svd_sweeps_mean": float(np.mean(info_h))}
+        out["slowdown"] = out["fp64"]["ms_per_launch"] / out["fp32"]["ms_per_launch"]
+        return {"rotation_parameter_precision": out}
 
     def cpu_sample(self, n):
         import gen
@@ -358,9 +439,9 @@ class Fp64_32:
         fl = jacobi_flops(32, 32, info_h, rots_h, pre)
         achieved = fl / (kernel_ms * 1e-3) / 1e12
         return ({"kernel": f"jacobi_reg_kernel<double> (tier {int(self.tuned['tier']):#x})", "bound": "alu",
-                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "ms_per_launch": kernel_ms,
-                 "peak_note": "FP64: GB300 data-sheet 1.25 TFLOP/s"},
+                 "achieved": achieved, "peak": PEAKS["fp64"]["tflops"], "unit": "TFLOP/s",
+                 "frac": achieved / PEAKS["fp64"]["tflops"], "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": PEAKS["fp64"]["note"]},
                 {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
                  "autotune": self.tuned})
 
@@ -384,16 +465,17 @@ class Block512:
     metric = "batched SVDs/s (512x512 FP32 block-Jacobi SVD)"
     unit = "SVDs/s"
     dtype = "f32"
-    launches_per_step = block_jacobi_launches(512, 32, 20)   # every sweep up to the cap of 20 is launched
+    launches_per_step = block_qr_launches(512, 32, 20)   # every sweep up to the cap of 20 is launched
 
     def __init__(self, args):
         self.args = args
         self.nb = args.block_batch
 
     def config(self, world):
-        return {"workload": f"block512: block-Jacobi SVD (U,S,V) of {self.nb} FP32 512x512 per GPU per step, GRAM "
-                            "method, block width 32, pair Gram products on the tensor cores (TF32 hi/lo split, "
-                            "FP32 accumulation), updates on FP32 SIMT; sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
+        return {"workload": f"block512: block-Jacobi SVD (U,S,V) of {self.nb} FP32 512x512 per GPU per step, blocked "
+                            "Householder QR then GRAM block Jacobi on R^T (block width 32, pair Gram products on the "
+                            "tensor cores: TF32 hi/lo split, FP32 accumulation; updates on FP32 SIMT), U = Q V~; "
+                            "sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
                 "l2": f"inputs ({self.nb * 512 * 512 * 4 / 1e6:.0f} MB per GPU) "
                       f"{'larger' if self.nb * 512 * 512 * 4 > 129e6 else 'smaller'} than L2",
                 "parallelism": f"independent batches per GPU x{world}"}
@@ -403,9 +485,15 @@ class Block512:
         import gen
         import paper_1707_05141_gb300 as bs
         self.bs = bs
-        b = gen.block512_loguniform(batch=self.nb, first=rank * self.nb)
-        self.h_in = [torch.from_numpy(b.a).pin_memory()]
-        self.d = self.h_in[0].to(dev)
+        if self.args.host_inputs:
+            b = gen.block512_loguniform(batch=self.nb, first=rank * self.nb)
+            self.h_in = [torch.from_numpy(b.a).pin_memory()]
+            self.d = self.h_in[0].to(dev)
+            self.sigma = b.sigma
+        else:  # the same recipe generated on the device (minutes of host LAPACK time otherwise)
+            from gen import device as gdev
+            self.d, self.sigma = gdev.block512_loguniform(batch=self.nb, first=rank * self.nb, dev=dev)
+            self.h_in = None
         self.d_in = [self.d]
         k = 512
         self.A = bs.Batch.uniform(self.d, 512, 512)
@@ -416,74 +504,109 @@ class Block512:
                                      bs.Batch.uniform(self.V, 512, k))
         self.info = torch.empty(self.nb, dtype=torch.int32, device=dev)
         self.rots = torch.empty(self.nb, dtype=torch.int64, device=dev)
-        self.ws = torch.empty(bs.batched_svd_block_jacobi_workspace(self.A, 32, 0), dtype=torch.uint8, device=dev)
+        self.ws = torch.empty(max(bs.batched_svd_block_jacobi_workspace(self.A, 32, m)
+                                  for m in (0, bs.BLOCK_QR_PRECONDITION)), dtype=torch.uint8, device=dev)
         self.outs = [self.S, self.U, self.V]
-        self.sigma = b.sigma
 
     def step(self, stream, kev=None):
         if kev is not None:
             kev[0].record(stream)
         self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
-                                         max_sweeps=20, block_width=32, method=0, stream=stream)
+                                         max_sweeps=20, block_width=32, method=self.bs.BLOCK_QR_PRECONDITION,
+                                         stream=stream)
         if kev is not None:
             kev[1].record(stream)
+
+    mixed_form = ("blocked Householder QR, GRAM block Jacobi on R^T with the pair Gram products on the tensor cores "
+                  "(tcgen05 TF32 hi/lo split, FP32 accumulation), U = Q V~")
+    plain_form = "pair Gram products on the FP32 SIMT pipes (BSVD_BLOCK_SIMT_PRODUCTS)"
+
+    def quality(self):
+        info_h = self.info.cpu().numpy()
+        sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
+        s = self.S.cpu().numpy()[:, 0, :].astype(np.float64)
+        err = float(np.max(np.abs(s - self.sigma).max(axis=1) / self.sigma[:, 0]))
+        return {"sweeps_mean": float(np.mean(sweeps)), "max_sigma_err_vs_generator_normwise": err,
+                "within_1e-5": bool(err <= 1e-5)}
+
+    def _step_fn(self, method):
+        def step(st, kev=None):
+            if kev is not None:
+                kev[0].record(st)
+            self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
+                                             max_sweeps=20, block_width=32, method=method, stream=st)
+            if kev is not None:
+                kev[1].record(st)
+        return step
+
+    def plain_arm(self, stream):
+        return self._step_fn(self.bs.BLOCK_SIMT_PRODUCTS), self.quality
+
+    def extra_arms(self, stream, steps, warmup, time_fn):
+        """GRAM on A itself (no QR preconditioning), tensor-core Gram."""
+        import torch
+        step = self._step_fn(0)
+        for _ in range(warmup):
+            step(stream)
+        torch.cuda.synchronize()
+        t = time_fn(step)
+        return {"no_qr_preconditioning": {"form": "GRAM block Jacobi on A (tensor-core Gram), no QR preconditioning",
+                                          "ms_per_step": t["ms_step"], "clocks": t["clocks"],
+                                          "value": self.units / (t["ms_step"] * 1e-3), **self.quality()}}
 
     units = property(lambda self: self.nb)
 
     def roofline(self, kernel_ms):
         info_h = self.info.cpu().numpy()
         sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
-        # per pair: Gram 2 m (2bw)^2, update 2 (m + n) (2bw)^2 flops; 120 pairs per sweep
+        # per pair: Gram 2 m (2bw)^2, update 2 (m + n) (2bw)^2 flops; 120 pairs per sweep; per matrix
+        # the blocked QR (4 n^3 / 3) and U = Q V~ (2 n^3)
         pair_fl = 2 * 512 * 64 * 64 + 2 * 1024 * 64 * 64
-        fl = float(np.sum(sweeps) * 120 * pair_fl)
+        fl = float(np.sum(sweeps) * 120 * pair_fl) + self.nb * (4.0 / 3.0 + 2.0) * 512 ** 3
         achieved = fl / (kernel_ms * 1e-3) / 1e12
-        err = float(np.abs(self.S.cpu().numpy()[:, 0, :] - self.sigma).max())
         return ({"kernel": "batched_svd_block_jacobi (all stages of one call)", "bound": "alu",
-                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "ms_per_launch": kernel_ms,
-                 "peak_note": "FP32 SIMT; achieved counts Gram + update flops of the pairs of every sweep run"},
-                {"sweeps_mean": float(np.mean(sweeps)), "sweeps_max": int(np.max(sweeps)),
-                 "max_sigma_err_vs_generator": err})
-
-    def plain_ms(self, stream):
-        """The same call with the Gram products on the FP32 SIMT pipes (the plain FP32 form), timed
-        once after a warm-up run, for the mixed-vs-plain comparison."""
-        import torch
-
-        def run():
-            self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
-                                             max_sweeps=20, block_width=32, method=self.bs.BLOCK_SIMT_PRODUCTS,
-                                             stream=stream)
-        run()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        run()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        info_h = self.info.cpu().numpy()
-        sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
-        err = float(np.abs(self.S.cpu().numpy()[:, 0, :] - self.sigma).max())
-        return {"plain_simt_ms": e0.elapsed_time(e1), "plain_sweeps_mean": float(np.mean(sweeps)),
-                "plain_max_sigma_err_vs_generator": err}
+                 "achieved": achieved, "peak": PEAKS["fp32"]["tflops"], "unit": "TFLOP/s",
+                 "frac": achieved / PEAKS["fp32"]["tflops"], "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": PEAKS["fp32"]["note"] + "; achieved counts Gram + update flops of the pairs of "
+                              "every sweep run, the blocked QR and U = Q V~"},
+                {"sweeps_max": int(np.max(sweeps)), **self.quality()})
 
     def cpu_sample(self, n):
-        import gen
         import oracle
-        n = max(1, min(n, 16))
-        b = gen.block512_loguniform(batch=n)
-        mats = [b.a64(i) for i in range(n)]
+        n = max(1, min(n, 16, self.nb))
+        a = self.d[:n].cpu().numpy()
+        mats = [a[i].T.astype(np.float64) for i in range(n)]
         cores = oracle.default_threads()
         t0 = time.time()
         oracle.svd_batch(mats, nthreads=cores)
         dt = time.time() - t0
         return {"value": n / dt, "count": n, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
-                "sample": f"{n} SVDs of 512x512 FP64 (same generator), {dt:.2f} s wall"}
+                "sample": f"{n} SVDs of 512x512 FP64 (the first matrices of the timed batch), {dt:.2f} s wall"}
+
+
+class DeviceBlocks:
+    """Uneven blocks generated on the device, with a pinned host copy for the end-to-end run, the
+    error checks and the oracle's sample."""
+
+    def __init__(self, flat_d, offset, m, n, extra):
+        self.flat_d = flat_d
+        self.h = flat_d.cpu().pin_memory()
+        self.flat = self.h.numpy()
+        self.offset, self.m, self.n, self.extra = offset, m, n, extra
+
+    @property
+    def batch(self):
+        return len(self.m)
+
+    def a64(self, b):
+        mb, nb, o = int(self.m[b]), int(self.n[b]), int(self.offset[b])
+        return self.flat[o:o + mb * nb].reshape(nb, mb).T.astype(np.float64)
 
 
 class RsvdBase:
     unit = "SVDs/s"
     dtype = "f32"
+    flags = 0   # the timed form samples in FP32 (the tensor-core sample is an arm: measured slower)
 
     def _alloc(self, rb, dev, hint_host):
         import torch
@@ -491,8 +614,12 @@ class RsvdBase:
         self.rb = rb
         m, n = rb.m, rb.n
         k = np.minimum(m, n)
-        self.h_in = [torch.from_numpy(rb.flat).pin_memory()]
-        self.flat = self.h_in[0].to(dev)
+        if getattr(rb, "flat_d", None) is not None:   # generated on the device
+            self.h_in = [rb.h]
+            self.flat = rb.flat_d
+        else:
+            self.h_in = [torch.from_numpy(rb.flat).pin_memory()]
+            self.flat = self.h_in[0].to(dev)
         self.d_in = [self.flat]
         su, sv, ss = (m.astype(np.int64) * k + 3) // 4 * 4, (n.astype(np.int64) * k + 3) // 4 * 4, (k + 3) // 4 * 4
         off = lambda x: np.concatenate([[0], np.cumsum(x)[:-1]])
@@ -513,10 +640,61 @@ class RsvdBase:
         self.outs = [self.fu, self.fv, self.fs]
         self.graph = None
 
-    def _rsvd(self, stream, hint, rounds):
+    def _rsvd(self, stream, hint, rounds, fixed=None, flags=0):
         self.bs.batched_rsvd(self.A, self.U, self.S, self.V, self.kmax, self.rank, self.info, self.ws, hint,
                              tol=1e-5, oversample=8, max_rounds=rounds, seed=1707, err_est=self.err,
-                             samples=self.samples, stream=stream)
+                             samples=self.samples, stream=stream, fixed_rank=fixed, flags=flags)
+
+    def _timed_arm(self, fn, stream, warmup, time_fn, form):
+        import torch
+        step = self._graph_arm(fn)
+        for _ in range(warmup):
+            step(stream)
+        torch.cuda.synchronize()
+        t = time_fn(step)
+        return {"form": form, "ms_per_step": t["ms_step"], "clocks": t["clocks"],
+                "value": self.units / (t["ms_step"] * 1e-3), **self.quality()}
+
+    def extra_arms(self, stream, steps, warmup, time_fn):
+        """The timed form with the small SVDs in FP64 as well (BSVD_RSVD_SMALL_FP64: the precision
+        split of the method -- low-precision sample, FP64 small SVD), and with FP32 sampling."""
+        bs = self.bs
+        return {"small_svd_fp64": self._timed_arm(
+                    lambda st: self.inner(st, self.flags | bs.RSVD_SMALL_FP64), stream, warmup, time_fn,
+                    self.mixed_form + "; small SVDs in FP64"),
+                "tc_sampling": self._timed_arm(
+                    lambda st: self.inner(st, self.flags | bs.RSVD_TC_SAMPLING), stream, warmup, time_fn,
+                    self.mixed_form + "; sample A Omega on the tensor cores (tcgen05 kind::tf32, FP32 "
+                                      "accumulation; probes in FP32)")}
+
+    def _graph_arm(self, fn):
+        """A step function replaying a CUDA graph of fn(stream) (captured now)."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn(torch.cuda.current_stream())
+
+        def step(stream, kev=None):
+            if kev is not None:
+                kev[0].record(stream)
+            g.replay()
+            if kev is not None:
+                kev[1].record(stream)
+        step.graph = g
+        return step
+
+    plain_form = "FP32 SIMT sampling and projection, adaptive range finder from 8 samples (no rank hints)"
+
+    def plain_arm(self, stream):
+        return self._graph_arm(lambda st: self._rsvd(st, None, 16)), self.quality
+
+    def quality(self):
+        info = self.info.cpu().numpy()
+        samp = self.samples.cpu().numpy()
+        err = self.error_sample()
+        return {"rounds_mean": float((info & 0xff).mean()), "samples_mean": float(samp.mean()),
+                "fallback_frac": float(np.mean((info >> 22) & 1)), "rank_mean": float(self.rank.float().mean()),
+                "max_rel_error_sampled": err, "within_1e-5": bool(err <= 1e-5)}
 
     def capture(self, stream):
         import torch
@@ -557,21 +735,24 @@ class RsvdBase:
         rounds = info & 0xff
         samp = self.samples.cpu().numpy()
         rb = self.rb
-        # algorithmic bytes: every sampling round reads A four times (sample, power step x2,
-        # projection), a full SVD reads it once; outputs U, S, V of the rank k
-        abytes = float(np.sum((rb.m.astype(np.float64) * rb.n) * 4 * (4 * rounds + (samp == np.minimum(rb.m, rb.n)))))
+        # algorithmic bytes: one read of A plus the writes of U, S, V of rank k (the method's
+        # minimum when a block is factored on chip); the secondary count takes every pass over A
+        # the method makes (sample, two power-step products, projection per round; one per full SVD)
         rk = self.rank.cpu().numpy().astype(np.float64)
-        abytes += float(np.sum((rb.m + rb.n + 1) * rk * 4))
+        outb = float(np.sum((rb.m + rb.n + 1) * rk * 4))
+        abytes = float(np.sum(rb.m.astype(np.float64) * rb.n * 4)) + outb
+        pbytes = float(np.sum((rb.m.astype(np.float64) * rb.n) * 4 * (4 * rounds + (samp == np.minimum(rb.m, rb.n))))) + outb
         achieved = abytes / (kernel_ms * 1e-3) / 1e9
+        passes_gbs = pbytes / (kernel_ms * 1e-3) / 1e9
         peak = measured_hbm_gbs()
         k = np.minimum(rb.m, rb.n)
         return ({"kernel": self.kernel_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                  "frac": achieved / peak, "traffic": None, "ms_per_launch": kernel_ms,
-                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json); achieved = algorithmic bytes of "
-                              "the whole call / its time"},
-                {"rounds_mean": float(rounds.mean()), "fallback_frac": float(np.mean((info >> 22) & 1)),
-                 "full_rank_frac": float(np.mean(samp == k)), "samples_mean": float(samp.mean()),
-                 "rank_mean": float(rk.mean()), "max_rel_error_sampled": self.error_sample()})
+                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json); achieved = algorithmic bytes "
+                              "(one read of A + the writes of U, S, V of rank k) of the whole call / its time",
+                 "achieved_passes": passes_gbs, "passes_note": "the same time against the bytes of every pass "
+                 "the method makes over A (four per sampling round, one per full SVD) plus the outputs"},
+                {"full_rank_frac": float(np.mean(samp == k)), **self.quality()})
 
     def cpu_sample_blocks(self, rb, n, hint):
         import oracle
@@ -580,13 +761,7 @@ class RsvdBase:
         from concurrent.futures import ThreadPoolExecutor
 
         def one(b):
-            a = rb.a64(b)
-            k = min(a.shape)
-            l = int(hint[b]) + 8 if hint is not None else 8
-            if l >= k or l > 128:
-                oracle.svd(a)
-            else:
-                oracle.rsvd(a, 1707, b, l, 1)
+            oracle.rsvd_adaptive(rb.a64(b), 1707, b, int(hint[b]) if hint is not None else 0, 1e-5, 8, 1, 16, 128)
 
         t0 = time.time()
         with ThreadPoolExecutor(max_workers=cores) as ex:
@@ -616,21 +791,40 @@ class RsvdUneven(RsvdBase):
         import gen
         import paper_1707_05141_gb300 as bs
         self.bs = bs
-        rb = gen.rsvd_uneven_blocks(batch=self.nb, first=rank * self.nb)
+        if self.args.host_inputs:
+            rb = gen.rsvd_uneven_blocks(batch=self.nb, first=rank * self.nb)
+        else:  # the same recipe generated on the device (minutes of host LAPACK time otherwise)
+            from gen import device as gdev
+            flat, off, m, n, r0, hint = gdev.rsvd_uneven_blocks(batch=self.nb, first=rank * self.nb, dev=dev)
+            rb = DeviceBlocks(flat, off, m, n, {"r0": r0, "rank_hint": hint})
         self._alloc(rb, dev, rb.extra["rank_hint"])
+        self.kstar = self.hint
 
-    def inner(self, stream):
-        self._rsvd(stream, self.hint, 4)
+    def inner(self, stream, flags=None):
+        self._rsvd(stream, self.hint, 4, flags=self.flags if flags is None else flags)
+
+    mixed_form = ("tolerance mode with the rank where sigma falls to 1e-5 as the first guess, FP32 sampling, "
+                  "one CUDA graph per step")
+
+    def extra_arms(self, stream, steps, warmup, time_fn):
+        """Plus fixed-rank mode (Algorithm 4 as stated) at k* = the rank where sigma falls to 1e-5."""
+        out = super().extra_arms(stream, steps, warmup, time_fn)
+        out["fixed_rank_kstar"] = self._timed_arm(lambda st: self._rsvd(st, None, 1, fixed=self.kstar), stream,
+                                                  warmup, time_fn,
+                                                  "fixed rank k* + 8 samples, one power step (Algorithm 4)")
+        return out
 
     launches_per_step = rsvd_launches(256, 256, 4)
 
     def cpu_sample(self, n):
-        import gen
-        rb = gen.rsvd_uneven_blocks(batch=max(n, 1))
+        rb = getattr(self, "rb", None)
+        if rb is None:   # the reference arm: no device, the host generator
+            import gen
+            rb = gen.rsvd_uneven_blocks(batch=max(n, 1))
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, rb.extra["rank_hint"])
         return {"value": cnt / dt, "count": cnt, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
-                "sample": f"{cnt} blocks of the same generator, fixed-width FP64 RSVD (hint + 8 columns, one "
-                          f"power step) or full Jacobi SVD, {dt:.2f} s wall"}
+                "sample": f"{cnt} blocks spread over the batch, FP64 adaptive RSVD (the oracle's range finder "
+                          f"from hint + 8 columns, one power step, full Jacobi SVD fallback), {dt:.2f} s wall"}
 
 
 class HmatrixMlp(RsvdBase):
@@ -672,32 +866,15 @@ class HmatrixMlp(RsvdBase):
         self.md = torch.as_tensor(rb.m).to(dev)
         self.nd = torch.as_tensor(rb.n).to(dev)
 
-    def inner(self, stream):
+    def inner(self, stream, flags=None):
         bs = self.bs
         bs.bsvd_sketch_features(self.A, self.feats, 6, stream)
         bs.bsvd_mlp_forward(self.feats, self.params, self.pred, self.hint_d, 2.0, self.md, self.nd, stream)
-        self._rsvd(stream, self.hint_d, 16)
+        self._rsvd(stream, self.hint_d, 16, flags=self.flags if flags is None else flags)
 
     launches_per_step = 2 + rsvd_launches(256, 256, 16)   # features, forward, then the randomized SVD
 
-    def plain_ms(self, stream):
-        """The plain adaptive method (no hints) on the same blocks: time, rounds, worst error."""
-        import torch
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            self._rsvd(torch.cuda.current_stream(), None, 16)
-        g.replay()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(3):
-            g.replay()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        info = self.info.cpu().numpy()
-        out = {"plain_ms": e0.elapsed_time(e1) / 3, "plain_rounds_mean": float((info & 0xff).mean()),
-               "plain_max_rel_error_sampled": self.error_sample(), "plain_rank_mean": float(self.rank.float().mean())}
-        return out
+    mixed_form = "ranks predicted by the learned network (sketch features + MLP on the GPU) as first guesses"
 
     def cpu_sample(self, n):
         import gen
@@ -706,16 +883,133 @@ class HmatrixMlp(RsvdBase):
             rb = self._cpu_rb = gen.kernel_blocks_3d(n_points=8192, seed_index=0)
         cnt, dt, cores = self.cpu_sample_blocks(rb, n, None)
         return {"value": cnt / dt, "count": cnt, "seconds": dt, "unit": self.unit, "cores": cores, "kind": "oracle",
-                "sample": f"{cnt} kernel blocks (8192-point set), FP64 RSVD with 8 columns + power step, "
-                          f"{dt:.2f} s wall"}
+                "sample": f"{cnt} kernel blocks (8192-point set), FP64 adaptive RSVD from 8 columns (one power "
+                          f"step, rounds of 8), {dt:.2f} s wall"}
 
 
-WORKLOADS = {c.name: c for c in (SvdQr64, Fp64_32, Block512, RsvdUneven, HmatrixMlp)}
+class H2Truncation:
+    """Truncation of an H^2 nested row basis (Section 8.2): Chebyshev-interpolation basis (q = 8,
+    rank 64) over a k-d tree of depth 14 (mean split) on 2^20 points of a perturbed grid."""
+    name = "h2_truncation"
+    metric = "H2 basis-tree truncations/s (depth-14 Chebyshev basis, 16384 leaves, eps 1e-5)"
+    unit = "trees/s"
+    dtype = "f32"
+    units = 1
+
+    def __init__(self, args):
+        self.args = args
+        self.depth = getattr(args, "h2_depth", 14)
+
+    def config(self, world):
+        return {"workload": f"h2_truncation: truncation to eps 1e-5 of the Chebyshev-interpolation row basis (q = 8, "
+                            f"rank 64) of a k-d tree of depth {self.depth} (mean split, {2 ** self.depth} leaves of "
+                            "~64 points) over a perturbed grid of the unit square; FP32; leaf SVDs and one batched "
+                            "SVD per level", "leaves": 2 ** self.depth,
+                "l2": f"basis ({2 ** self.depth * 64 * 64 * 4 * 2 / 1e6:.0f} MB of leaves and transfers) "
+                      f"{'larger' if 2 ** self.depth * 64 * 64 * 8 > 129e6 else 'smaller'} than L2",
+                "parallelism": f"independent trees per GPU x{world}"}
+
+    def setup(self, rank, dev):
+        import gen.basis_tree as gb
+        import paper_1707_05141_gb300 as bs
+        self.bs = bs
+        self.tree = gb.chebyshev_basis_tree(self.depth, q=8, seed_index=rank)
+        self.plan = bs.H2Plan(self.tree.leaves, self.tree.transfers, self.tree.k)
+        self.d_in = [self.plan.leaf, self.plan.E]
+        self.h_in = None
+        self.outs = [self.plan.new_leaf, self.plan.new_transfer, self.plan.T, self.plan.rank]
+        self.launches_per_step = 1 + 2 + 3 * self.depth   # setup, leaves (SVD, finish), per level (TE, SVD, finish)
+
+    def step(self, stream, kev=None):
+        if kev is not None:
+            kev[0].record(stream)
+        self.plan.run(1e-5, stream)
+        if kev is not None:
+            kev[1].record(stream)
+
+    def roofline(self, kernel_ms):
+        p = self.plan
+        info = p.info.cpu().numpy()
+        rot = p.rotations.cpu().numpy().astype(np.float64)
+        rank = p.rank.cpu().numpy()
+        nl = 2 ** self.depth
+        k = p.k
+        sweeps = np.where(info >= (1 << 20), info - (1 << 20), np.maximum(info, 0)).astype(np.float64)
+        # Jacobi flops per node: pairs visited 6 max(m, n) per sweep, rotations 6 (m + n)
+        rows = np.empty(2 * nl - 1)
+        rows[nl - 1:] = p.m
+        for g in range(nl - 2, -1, -1):
+            rows[g] = rank[2 * g + 1] + rank[2 * g + 2]
+        kmin = np.minimum(rows, k)
+        fl = float(np.sum(sweeps * kmin * (kmin - 1) / 2 * 6 * np.maximum(rows, k) + rot * 6 * (rows + k)))
+        achieved = fl / (kernel_ms * 1e-3) / 1e12
+        return ({"kernel": "bsvd_h2_truncate (all levels of one tree)", "bound": "alu", "achieved": achieved,
+                 "peak": PEAKS["fp32"]["tflops"], "unit": "TFLOP/s", "frac": achieved / PEAKS["fp32"]["tflops"],
+                 "traffic": None, "ms_per_launch": kernel_ms,
+                 "peak_note": PEAKS["fp32"]["note"] + "; achieved counts the Jacobi flops of every node's SVD"},
+                {"leaves_per_s": nl / (kernel_ms * 1e-3), "leaf_rank_mean": float(rank[nl - 1:].mean()),
+                 "root_rank": int(rank[0]), "sweeps_mean_leaves": float(sweeps[nl - 1:].mean())})
+
+    def cpu_sample(self, n):
+        import oracle.h2 as oh2
+        import gen.basis_tree as gb
+        import oracle
+        d = 6
+        tree = gb.chebyshev_basis_tree(d, q=8)
+        t0 = time.time()
+        oh2.truncate_basis_tree(tree.leaves, tree.transfers, 1e-5)
+        dt = time.time() - t0
+        # per-leaf rate of a depth-6 tree, scaled to the benchmark's tree (leaves dominate the work)
+        per_tree = dt * (2 ** self.depth) / (2 ** d)
+        return {"value": 1.0 / per_tree, "count": 1, "seconds": per_tree, "unit": self.unit, "cores": 1,
+                "kind": "oracle", "sample": f"one depth-{d} tree ({2 ** d} leaves) by the FP64 oracle in {dt:.2f} s "
+                                            f"(one thread), scaled by leaf count to depth {self.depth}"}
+
+
+WORKLOADS = {c.name: c for c in (SvdQr64, Fp64_32, Block512, RsvdUneven, HmatrixMlp, H2Truncation)}
 
 
 # ----------------------------------------------------------------------------------------------
 # harness
 # ----------------------------------------------------------------------------------------------
+
+def time_arm(step, stream, steps, local_rank, world, dev, flush=None):
+    """Times exactly `steps` calls of step(stream, events) on `stream` with CUDA events, between a
+    barrier and a synchronize on both sides, with the SM clocks sampled meanwhile.  With `flush` (a
+    buffer larger than L2) L2 is overwritten before every step, outside that step's own events.
+    Returns the per-step time (max over ranks), the mean time between the events the step records
+    around its dominant call, and the clock record."""
+    import torch
+    kev, step_ev = [], []
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    t0e.record(stream)
+    for _ in range(steps):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        if flush is not None:
+            flush.fill_(1)
+            se = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            se[0].record(stream)
+        step(stream, ev)
+        if flush is not None:
+            se[1].record(stream)
+            step_ev.append(se)
+        kev.append(ev)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop(wall0, wall1)
+    own_ms = (sum(a.elapsed_time(b) for a, b in step_ev) if step_ev else t0e.elapsed_time(t1e)) / steps
+    return {"ms_step": max_over_ranks(own_ms, world, dev),
+            "kernel_ms": statistics.mean(a.elapsed_time(b) for a, b in kev), "clocks": ck}
+
 
 def run_ours(W, args, rank, world, local_rank):
     import torch
@@ -733,48 +1027,41 @@ def run_ours(W, args, rank, world, local_rank):
         W.capture(stream)
         W.step(stream)
         torch.cuda.synchronize()
-    kev = []
     # a batch smaller than L2 is evicted before every timed step by writing a buffer larger than L2
     # (256 MB against 129 MB); each step then has its own events, which exclude the flush
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if getattr(W, "flush_l2", False) else None
-    step_ev = []
-    clocks = Clocks(local_rank)
-    clocks.start()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    wall0 = time.time()
-    t0e.record(stream)
-    for _ in range(args.steps):
-        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        if flush is not None:
-            flush.fill_(1)
-            se = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            se[0].record(stream)
-        W.step(stream, ev)
-        if flush is not None:
-            se[1].record(stream)
-            step_ev.append(se)
-        kev.append(ev)
-    t1e.record(stream)
-    torch.cuda.synchronize()
-    wall1 = time.time()
-    if world > 1:
-        torch.distributed.barrier()
-    ck = clocks.stop(wall0, wall1)
-    own_ms = (sum(a.elapsed_time(b) for a, b in step_ev) if step_ev else t0e.elapsed_time(t1e)) / args.steps
-    ms_step = max_over_ranks(own_ms, world, dev)
-    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    t = time_arm(W.step, stream, args.steps, local_rank, world, dev, flush)
+    ms_step, kernel_ms, ck = t["ms_step"], t["kernel_ms"], t["clocks"]
     roof, detail = W.roofline(kernel_ms)
-    extra = W.plain_ms(stream) if hasattr(W, "plain_ms") else {}
+
+    # the plain form of the same workload (FP32 SIMT products, no learned or given ranks), timed
+    # the same way over the same number of steps: the "mixed vs plain FP32 at 1e-5" comparison
+    if hasattr(W, "plain_arm"):
+        quality = W.quality()
+        pstep, pfinish = W.plain_arm(stream)
+        for _ in range(args.warmup):
+            pstep(stream)
+        torch.cuda.synchronize()
+        pt = time_arm(pstep, stream, args.steps, local_rank, world, dev, flush)
+        detail["mixed_vs_plain"] = {
+            "mixed": {"form": W.mixed_form, "ms_per_step": ms_step, "clocks": ck, **quality},
+            "plain": {"form": W.plain_form, "ms_per_step": pt["ms_step"], "clocks": pt["clocks"], **pfinish()},
+            "speedup": pt["ms_step"] / ms_step}
+    if hasattr(W, "extra_arms"):
+        # the other forms of the workload (reported beside the timed one): fewer steps each
+        xs = max(1, min(args.steps, 5))
+        extra = W.extra_arms(stream, xs, args.warmup,
+                             lambda step: dict(time_arm(step, stream, xs, local_rank, world, dev, flush), steps=xs))
+        detail.update(extra)
     if hasattr(W, "train_info"):
-        extra["training"] = W.train_info
+        detail["training"] = W.train_info
 
     # end to end through the public API: pinned host inputs copied in, every output copied out;
     # where a quarter of the batch still fills the GPU (svd64_qr128: 5000 matrices per chunk), the
     # copies of one chunk overlap the computation of another (paper_1707_05141_gb300.pipeline);
     # smaller batches (fp64_32, block512) measured slower chunked and run the copies serially
+    if getattr(W, "h_in", None) is None:
+        W.h_in = [d.cpu().pin_memory() for d in W.d_in]
     houts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in W.outs]
     e2e_steps = max(1, min(args.steps, 5))
     pipe = None
@@ -807,7 +1094,6 @@ def run_ours(W, args, rank, world, local_rank):
     e2e_ms = max_over_ranks(x0.elapsed_time(x1) / e2e_steps, world, dev)
     h2d = sum(h.numel() * h.element_size() for h in W.h_in)
     d2h = sum(h.numel() * h.element_size() for h in houts)
-    detail.update(extra)
     return {"ms_step": ms_step, "value": world * W.units / (ms_step * 1e-3),
             "e2e": {"value": world * W.units / (e2e_ms * 1e-3), "unit": W.unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
@@ -815,14 +1101,37 @@ def run_ours(W, args, rank, world, local_rank):
             "roofline": roof, "clocks": ck, "gpu_launches": W.launches_per_step * args.steps, "detail": detail}
 
 
+SECONDARY = ("fp64_32", "block512", "rsvd_uneven", "hmatrix_mlp", "h2_truncation")
+CPU_SAMPLE = {"svd64_qr128": 4000, "fp64_32": 1000, "block512": 4, "rsvd_uneven": 256, "hmatrix_mlp": 512,
+              "h2_truncation": 1}
+# bounded oracle samples of the other workloads in a default run (a few seconds of host time each)
+CPU_SAMPLE_SECONDARY = {"fp64_32": 500, "block512": 2, "rsvd_uneven": 96, "hmatrix_mlp": 256, "h2_truncation": 1}
+
+
+def line_of(W, res, args, world, cb):
+    return {"metric": W.metric, "value": res["value"], "unit": W.unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": W.dtype, "data": "synthetic", "config": W.config(world),
+            "roofline": res["roofline"], "cpu_baseline": cb, "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": res["gpu_launches"], "detail": res["detail"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="svd64_qr128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=None,
+                    help="time this workload alone (default: svd64_qr128 as the headline line, the other four "
+                         "in detail.workloads)")
+    ap.add_argument("--headline-only", action="store_true", help="default run without the other workloads")
+    ap.add_argument("--host-inputs", action="store_true",
+                    help="block512 / rsvd_uneven inputs from the host generator (byte-identical to the tests', "
+                         "minutes of LAPACK time) instead of the same recipe on the device")
     ap.add_argument("--svd-batch", type=int, default=20000)
+    ap.add_argument("--jacobi-tier", default=None,
+                    help="svd64_qr128: run this encoded register variant (e.g. 0xa01) instead of autotuning")
     ap.add_argument("--qr-batch", type=int, default=20000)
     ap.add_argument("--block-batch", type=int, default=500, help="block512: matrices per GPU")
     ap.add_argument("--rsvd-batch", type=int, default=16384, help="rsvd_uneven: blocks per GPU")
@@ -832,9 +1141,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    W = WORKLOADS[args.workload](args)
-    default_sample = {"svd64_qr128": 4000, "fp64_32": 1000, "block512": 4, "rsvd_uneven": 256, "hmatrix_mlp": 512}
-    ns = args.cpu_sample or default_sample[W.name]
+    name = args.workload or "svd64_qr128"
+    W = WORKLOADS[name](args)
+    ns = args.cpu_sample or CPU_SAMPLE[W.name]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -864,22 +1173,40 @@ def main():
                           "e2e": {"value": v, "unit": W.unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
+    import torch
     if world > 1:
-        import torch
         torch.distributed.init_process_group("nccl")
+    import paper_1707_05141_gb300 as bs
+    torch.cuda.set_device(torch.device("cuda", local_rank))
+    measure_alu_peaks(bs, torch.device("cuda", local_rank), local_rank)
     res = run_ours(W, args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = {key: val for key, val in W.cpu_sample(ns).items() if key not in ("count", "seconds")}
+    line = line_of(W, res, args, world, cb)
+    line["detail"]["alu_peaks"] = PEAKS
+    if args.workload is None and not args.headline_only:
+        # the other four workloads, each timed the same way (K steps after W warm-ups, clocks,
+        # roofline, plain arm, end to end, bounded oracle sample), one after the other
+        del W
+        torch.cuda.empty_cache()
+        others = {}
+        for other in SECONDARY:
+            W2 = WORKLOADS[other](args)
+            r2 = run_ours(W2, args, rank, world, local_rank)
+            cb2 = None
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                cb2 = {key: val for key, val in W2.cpu_sample(CPU_SAMPLE_SECONDARY[other]).items()
+                       if key not in ("count", "seconds")}
+            l2 = line_of(W2, r2, args, world, cb2)
+            others[other] = {k: v for k, v in l2.items() if k not in ("n_gpus", "scaling", "vs_baseline", "data",
+                                                                       "higher_is_better", "warmup")}
+            del W2
+            torch.cuda.empty_cache()
+        line["detail"]["workloads"] = others
     if rank == 0:
-        line = {"metric": W.metric, "value": res["value"], "unit": W.unit, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": W.dtype, "data": "synthetic", "config": W.config(world),
-                "roofline": res["roofline"], "cpu_baseline": cb, "e2e": res["e2e"], "clocks": res["clocks"],
-                "gpu_launches": res["gpu_launches"], "detail": res["detail"]}
         print(json.dumps(line))
     if world > 1:
-        import torch
         torch.distributed.destroy_process_group()
 
 
