@@ -188,17 +188,37 @@ def block_qr_launches(n_cols, bw=32, sweeps=20):
 
 
 def rsvd_launches(max_m, max_n, rounds):
-    """Kernels one batched_rsvd call launches: plan and scan; per round the arrays kernel, four
-    GEMM + QR pairs (sample, power step, projection), the small SVD (register tier, plus the shared
-    tier when samples may pass 64), two GEMMs for U and V and the estimate; then the fallback and
-    arrays kernels, the full-rank QR path (QR, SVD, GEMM, copy), the shared tier (min > 64), the
-    block tier (min > 128) and the finish kernel."""
+    """Kernels one batched_rsvd call launches: plan and scan; per round the arrays kernel, the
+    sampling GEMM, the QRs of the sample, the power step's two products and two QRs, the projection
+    and its QR (each QR once per size bin the bounds can populate: rows in (0, 64], (64, 128],
+    (128, 256], columns in (0, 32], (32, 64], (64, 128], no bin with more columns than rows), the
+    small SVD per column bin (register tier; plus the shared tier when samples may pass 64), two
+    GEMMs for U and V and the estimate; then the fallback and arrays kernels, the full-rank QR path
+    (QR per row bin and column bin up to 64, SVD per column bin, GEMM, copy), the shared tier
+    (min > 64), the block tier on R^T of a blocked QR (min > 128) and the finish kernel."""
     kx = min(max_m, max_n)
     lx = min(kx, 128)
-    per_round = 14 + (1 if lx > 64 else 0)
+
+    def bins(rows_max, cols_max, col_bins):
+        n = 0
+        for rb in range(3):
+            if rb > 0 and (64 << (rb - 1)) >= rows_max:
+                break
+            for cb in range(col_bins):
+                if cb > 0 and (32 << (cb - 1)) >= cols_max:
+                    break
+                if min(32 << cb, cols_max) <= min(64 << rb, rows_max):
+                    n += 1
+        return n
+
+    qy, qz = bins(max_m, lx, 3), bins(max_n, lx, 3)
+    small = 1 + (1 if lx > 32 else 0)
+    per_round = 1 + 1 + qy + (qz + 1 + qy + 1) + (1 + qz) + small + (1 if lx > 64 else 0) + 2 + 1
     n = 2 + rounds * per_round + 2
     if kx > 0:
-        n += 4 + (1 if kx > 64 else 0) + (block_qr_launches(kx) if kx > 128 else 0)
+        kq = min(kx, 64)
+        n += bins(max(max_m, max_n), kq, 2) + (1 + (1 if kq > 32 else 0)) + 2 + (1 if kx > 64 else 0)
+        n += block_qr_launches(kx) if kx > 128 else 0
     return n + 1
 
 
@@ -275,8 +295,14 @@ class SvdQr64:
             self.tuned = autotune.tune_jacobi(self.d_svd, m, n)
         self.outs = [self.S, self.U, self.V, self.Q, self.R]
         self.d_in = [self.d_svd, self.d_qr]
+        self.qr_ev = []  # (before, after) the QR launch of every timed step
 
     def step(self, stream, kev=None):
+        if kev is not None:
+            import torch
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            self.qr_ev.append((e, kev[0]))
         self.bs.batched_qr(self.AQ, self.Qb, self.Rb, self.qinfo, stream)
         if kev is not None:
             kev[0].record(stream)
@@ -287,21 +313,21 @@ class SvdQr64:
     launches_per_step = 2
     units = property(lambda self: self.nb)
 
-    def prepare_chunks(self, bounds):
-        """Per-chunk batch views for the pipelined end-to-end run (built once, before timing)."""
+    def host_step(self, houts, chunks):
+        """One end-to-end step through the host entries: QR then SVD of the host batches, outputs to
+        the pinned host buffers (S, U, V, Q, R)."""
+        import torch
         bs = self.bs
-        assert self.nb == self.nq
-        self.chunk_batches = {
-            (c0, c1): (bs.Batch.uniform(self.d_qr[c0:c1], 128, 32), bs.Batch.uniform(self.Q[c0:c1], 128, 32),
-                       bs.Batch.uniform(self.R[c0:c1], 32, 32), bs.Batch.uniform(self.d_svd[c0:c1], 64, 64),
-                       bs.Batch.uniform(self.S[c0:c1], 64, 1), bs.Batch.uniform(self.U[c0:c1], 64, 64),
-                       bs.Batch.uniform(self.V[c0:c1], 64, 64))
-            for c0, c1 in bounds}
+        dev = self.d_svd.device
+        h_svd, h_qr = self.h_in
+        hs, hu, hv, hq, hr = houts
+        ws_q = torch.empty(bs.host_qr_workspace(bs.F32, self.nq, 128, 32), dtype=torch.uint8, device=dev)
+        ws_s = torch.empty(bs.host_svd_workspace(bs.F32, self.nb, 64, 64), dtype=torch.uint8, device=dev)
 
-    def chunk_step(self, c0, c1, stream):
-        aq, q, r, a, s, u, v = self.chunk_batches[(c0, c1)]
-        self.bs.batched_qr(aq, q, r, self.qinfo[c0:c1], stream)
-        self.bs.batched_svd_jacobi(a, s, u, v, self.info[c0:c1], self.rots[c0:c1], stream=stream)
+        def step(stream):
+            bs.host_qr(h_qr, hq, hr, chunks=chunks, workspace=ws_q, stream=stream)
+            bs.host_svd(h_svd, hs, hu, hv, chunks=chunks, workspace=ws_s, stream=stream)
+        return step
 
     def roofline(self, kernel_ms):
         bs = self.bs
@@ -321,6 +347,16 @@ class SvdQr64:
                 "peak_note": PEAKS["fp32"]["note"]}
         detail = {"svd_sweeps_mean": float(np.mean(info_h)), "rotations_mean": float(np.mean(rots_h)),
                   "jacobi_gflop_per_launch": fl / 1e9, "autotune": self.tuned}
+        if self.qr_ev:
+            # the QR launch: HBM-bound, one read of A and the Q, R writes per matrix
+            qr_ms = statistics.mean(a.elapsed_time(b) for a, b in self.qr_ev)
+            qbytes = self.nq * (128 * 32 * 2 + 32 * 32) * 4
+            gbs = qbytes / (qr_ms * 1e-3) / 1e9
+            peak = measured_hbm_gbs()
+            detail["qr"] = {"kernel": "qr_warp_kernel<float, 128, 1>", "ms_per_launch": qr_ms,
+                            "bytes_per_launch": qbytes, "achieved_gbs": gbs, "peak_gbs": peak,
+                            "frac": gbs / peak, "bound": "hbm", "peak_note": "measured copy bandwidth"}
+            self.qr_ev = []
         return roof, detail
 
     def extra_arms(self, stream, steps, warmup, time_fn):
@@ -432,6 +468,22 @@ class Fp64_32:
             kev[1].record(stream)
 
     units = property(lambda self: self.nb)
+
+    def host_step(self, houts, chunks):
+        """One end-to-end step through the host entries: QR and SVD of the host batch (one chunk:
+        a quarter of this 1000-matrix batch no longer fills the GPU)."""
+        import torch
+        bs = self.bs
+        dev = self.d.device
+        h_a = self.h_in[0]
+        hs, hu, hv, hq, hr = houts
+        ws_q = torch.empty(bs.host_qr_workspace(bs.F64, self.nb, 32, 32), dtype=torch.uint8, device=dev)
+        ws_s = torch.empty(bs.host_svd_workspace(bs.F64, self.nb, 32, 32), dtype=torch.uint8, device=dev)
+
+        def step(stream):
+            bs.host_qr(h_a, hq, hr, chunks=1, workspace=ws_q, stream=stream)
+            bs.host_svd(h_a, hs, hu, hv, chunks=1, workspace=ws_s, stream=stream)
+        return step
 
     def roofline(self, kernel_ms):
         info_h, rots_h = self.info.cpu().numpy(), self.rots.cpu().numpy()
@@ -1056,24 +1108,19 @@ def run_ours(W, args, rank, world, local_rank):
     if hasattr(W, "train_info"):
         detail["training"] = W.train_info
 
-    # end to end through the public API: pinned host inputs copied in, every output copied out;
-    # where a quarter of the batch still fills the GPU (svd64_qr128: 5000 matrices per chunk), the
-    # copies of one chunk overlap the computation of another (paper_1707_05141_gb300.pipeline);
-    # smaller batches (fp64_32, block512) measured slower chunked and run the copies serially
+    # end to end through the public API: pinned host inputs copied in, every output copied out.
+    # Workloads with a host entry (uniform SVD + QR batches) call the library's host-in/host-out
+    # functions, whose chunked copies overlap the computation (bsvd_host_qr / bsvd_host_svd); the
+    # others copy with torch around their device call.
     if getattr(W, "h_in", None) is None:
         W.h_in = [d.cpu().pin_memory() for d in W.d_in]
     houts = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in W.outs]
     e2e_steps = max(1, min(args.steps, 5))
-    pipe = None
-    if hasattr(W, "chunk_step") and args.e2e_chunks > 1:
-        from paper_1707_05141_gb300.pipeline import ChunkPipeline
-        pipe = ChunkPipeline(W.h_in, houts, W.d_in, W.outs, lambda c0, c1, di, do, s: W.chunk_step(c0, c1, s),
-                             chunks=args.e2e_chunks)
-        W.prepare_chunks(pipe.bounds)
+    host_step = W.host_step(houts, args.e2e_chunks) if hasattr(W, "host_step") else None
 
     def e2e_step():
-        if pipe is not None:
-            pipe.run(stream)
+        if host_step is not None:
+            host_step(stream)
             return
         for d, h in zip(W.d_in, W.h_in):
             d.copy_(h, non_blocking=True)
@@ -1097,7 +1144,9 @@ def run_ours(W, args, rank, world, local_rank):
     return {"ms_step": ms_step, "value": world * W.units / (ms_step * 1e-3),
             "e2e": {"value": world * W.units / (e2e_ms * 1e-3), "unit": W.unit, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "pipelined_chunks": len(pipe.bounds) if pipe is not None else 1},
+                    "path": ("C ABI host entries (bsvd_host_qr, bsvd_host_svd), "
+                             f"{args.e2e_chunks} overlapped chunks") if host_step is not None
+                    else "torch copies around the device entry points, serial"},
             "roofline": roof, "clocks": ck, "gpu_launches": W.launches_per_step * args.steps, "detail": detail}
 
 
@@ -1136,7 +1185,7 @@ def main():
     ap.add_argument("--block-batch", type=int, default=500, help="block512: matrices per GPU")
     ap.add_argument("--rsvd-batch", type=int, default=16384, help="rsvd_uneven: blocks per GPU")
     ap.add_argument("--e2e-chunks", type=int, default=4,
-                    help="chunks of the end-to-end run whose copies overlap the computation (1: serial)")
+                    help="chunks of the host entries' end-to-end run whose copies overlap the computation")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

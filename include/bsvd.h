@@ -398,6 +398,25 @@ int bsvd_h2_truncate(int dtype, int depth, int k, int max_leaf_m, void* const* d
                      int* d_info, long long* d_rotations, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Host-in, host-out calls on uniform batches (HOST arrays; no counterpart in the paper, whose
+ * batches already live on the GPU).  Matrix b of the batch is column-major at element b * m * n of
+ * hA (leading dimension m); outputs are packed the same way: S k values (k = min(m, n)), U m x k,
+ * V n x k, Q m x n, R n x n per matrix, info one int.  The batch is cut into `chunks` chunks whose
+ * host -> device copy, computation and device -> host copy overlap (two library-owned copy streams,
+ * created once per device; `stream` computes and, on return, is ordered after the last copy:
+ * synchronising it completes the call).  Host buffers must stay valid until then and should be
+ * page-locked for the copies to overlap.  The device copies of the whole batch live in `workspace`
+ * (at least *_workspace(...) bytes, else BSVD_ERR_WORKSPACE); nothing is allocated.  Calls on one
+ * device share the copy streams.  hU, hV, hQ, hR, h_info may be NULL (not computed / not copied).
+ */
+size_t bsvd_host_svd_workspace(int dtype, int batch, int m, int n);
+int bsvd_host_svd(int dtype, int batch, int m, int n, const void* hA, void* hS, void* hU, void* hV, int* h_info,
+                  int chunks, void* workspace, size_t workspace_bytes, void* stream);
+size_t bsvd_host_qr_workspace(int dtype, int batch, int m, int n);
+int bsvd_host_qr(int dtype, int batch, int m, int n, const void* hA, void* hQ, void* hR, int* h_info, int chunks,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * Diagnostics (outside the method; for tests and the benchmark).
  *
  * bsvd_philox_gauss -- for each of `count` counters (d_ctr: 4 x count words, DEVICE) the

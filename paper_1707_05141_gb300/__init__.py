@@ -82,6 +82,14 @@ def lib() -> ctypes.CDLL:
             L.bsvd_h2_truncate_workspace.argtypes = [i, i, i, i]
             L.bsvd_h2_truncate.restype = i
             L.bsvd_h2_truncate.argtypes = [i, i, i, i, p, p, p, p, d, p, p, p, p, p, p, p, p, ctypes.c_size_t, p]
+            L.bsvd_host_svd_workspace.restype = ctypes.c_size_t
+            L.bsvd_host_svd_workspace.argtypes = [i, i, i, i]
+            L.bsvd_host_svd.restype = i
+            L.bsvd_host_svd.argtypes = [i, i, i, i, p, p, p, p, p, i, p, ctypes.c_size_t, p]
+            L.bsvd_host_qr_workspace.restype = ctypes.c_size_t
+            L.bsvd_host_qr_workspace.argtypes = [i, i, i, i]
+            L.bsvd_host_qr.restype = i
+            L.bsvd_host_qr.argtypes = [i, i, i, i, p, p, p, p, i, p, ctypes.c_size_t, p]
             L.bsvd_philox_gauss.restype = i
             L.bsvd_philox_gauss.argtypes = [i, p, ctypes.c_ulonglong, p, p, p, p]
             L.bsvd_fma_probe.restype = ctypes.c_longlong
@@ -396,6 +404,57 @@ def h2_truncate(leaves, transfers, k: int, eps: float, dtype=None, stream=None):
     plan = H2Plan(leaves, transfers, k, dtype)
     plan.run(eps, stream)
     return plan
+
+
+def _host_ptr(t, name: str, dtype, numel: int):
+    """Address of a host tensor's data (None: null) after checks of device, type and size."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name}: a host tensor is required")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: {dtype} required, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"{name}: a contiguous tensor of at least {numel} elements is required")
+    return ctypes.c_void_p(int(t.data_ptr()))
+
+
+def host_svd_workspace(dtype_code: int, batch: int, m: int, n: int) -> int:
+    return int(lib().bsvd_host_svd_workspace(dtype_code, batch, m, n))
+
+
+def host_svd(a, s, u=None, v=None, info=None, chunks: int = 4, workspace=None, stream=None) -> None:
+    """Jacobi SVD of the host batch ``a`` (batch, n, m) into host ``s`` (batch, k), ``u`` (batch, k, m),
+    ``v`` (batch, k, n), ``info`` (batch) int32, copies overlapped with the computation in ``chunks``
+    chunks; ``workspace`` a uint8 CUDA tensor of host_svd_workspace(...) bytes."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    k = min(m, n)
+    code = F32 if a.dtype == torch.float32 else F64
+    rc = lib().bsvd_host_svd(code, bsz, m, n, _host_ptr(a, "a", a.dtype, bsz * m * n),
+                             _host_ptr(s, "s", a.dtype, bsz * k), _host_ptr(u, "u", a.dtype, bsz * m * k),
+                             _host_ptr(v, "v", a.dtype, bsz * n * k), _host_ptr(info, "info", torch.int32, bsz),
+                             int(chunks), _dptr(workspace, "workspace", torch.uint8), int(workspace.numel()),
+                             _stream_ptr(stream))
+    _check("bsvd_host_svd", rc)
+
+
+def host_qr_workspace(dtype_code: int, batch: int, m: int, n: int) -> int:
+    return int(lib().bsvd_host_qr_workspace(dtype_code, batch, m, n))
+
+
+def host_qr(a, q=None, r=None, info=None, chunks: int = 4, workspace=None, stream=None) -> None:
+    """Householder QR of the host batch ``a`` (batch, n, m) into host ``q`` (batch, n, m), ``r``
+    (batch, n, n), ``info`` (batch) int32, copies overlapped with the computation."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    code = F32 if a.dtype == torch.float32 else F64
+    rc = lib().bsvd_host_qr(code, bsz, m, n, _host_ptr(a, "a", a.dtype, bsz * m * n),
+                            _host_ptr(q, "q", a.dtype, bsz * m * n), _host_ptr(r, "r", a.dtype, bsz * n * n),
+                            _host_ptr(info, "info", torch.int32, bsz), int(chunks),
+                            _dptr(workspace, "workspace", torch.uint8), int(workspace.numel()), _stream_ptr(stream))
+    _check("bsvd_host_qr", rc)
 
 
 def philox_gauss(ctr, seed: int, stream=None):

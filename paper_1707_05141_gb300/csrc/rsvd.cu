@@ -117,10 +117,32 @@ struct RsArrays {
     // item lists (see ItemList) built with the arrays: blocks sampling in this round, split by
     // the tier of their small SVD; full-rank blocks of the QR path and of the shared tier
     int *list_act, *list_lreg, *list_lsmem, *list_reg, *list_smem;
-    int* cnt;                             // their lengths, RL_* order
+    // size-binned lists (RB_* bins, `batch` entries each): the QR and small-SVD stages are launched
+    // once per bin with that bin's bounds, so small blocks get the shared memory and threads of
+    // their own size (occupancy), not those of the batch's largest
+    int* binned;
+    int* cnt;                             // list lengths: RL_* then the bins; cnt[kTimeoutSlot]: timeouts
     RsState* st;
 };
 enum { RL_ACT = 0, RL_LREG, RL_LSMEM, RL_REG, RL_SMEM, RL_COUNT };
+// bins: rows (m or n; max(m, n) on the full-rank path) in (0, 64], (64, 128], (128, 256]; columns
+// (l, or k) in (0, 32], (32, 64], (64, 128]
+constexpr int kRowBins = 3, kColBins = 3;
+constexpr int RB_QY = RL_COUNT;                         // QR of Y (m x l): 9 bins
+constexpr int RB_QZ = RB_QY + kRowBins * kColBins;      // QR of Z and B^T (n x l): 9 bins
+constexpr int RB_LREG = RB_QZ + kRowBins * kColBins;    // small SVD, register tier (l <= 32, <= 64)
+constexpr int RB_FQR = RB_LREG + 2;                     // full-rank QR path: QR of A (max(m,n) x k), k <= 64
+constexpr int RB_FSVD = RB_FQR + kRowBins * 2;          // ... and the SVD of R^T (k <= 32, <= 64)
+constexpr int RB_END = RB_FSVD + 2;
+constexpr int kBins = RB_END - RL_COUNT;
+constexpr int kCounters = 64;                           // list lengths and flags (ints)
+constexpr int kTimeoutSlot = kCounters - 1;
+static_assert(RB_END <= kTimeoutSlot, "counter slots");
+
+__host__ __device__ inline int rs_row_bin(int r) { return r <= 64 ? 0 : (r <= 128 ? 1 : 2); }
+__host__ __device__ inline int rs_col_bin(int c) { return c <= 32 ? 0 : (c <= 64 ? 1 : 2); }
+__host__ __device__ inline int rs_row_bound(int b) { return 64 << b; }
+__host__ __device__ inline int rs_col_bound(int b) { return 32 << b; }
 
 // ------------------------------------------------------------------------------------------------
 // batched GEMM  C (M x N) = op(A) (M x K) * B (K x N), per-block sizes, element type T.
@@ -424,12 +446,26 @@ __global__ void rs_arrays_kernel(int batch, T* scratch, RsArrays<T> ar, int fina
     ar.n_smem[b] = smem ? n : 0;
     ar.m_blk[b] = blk ? m : 0;
     ar.n_blk[b] = blk ? n : 0;
+    auto bin_push = [&](int which) {
+        const int bi = which - RL_COUNT;
+        ar.binned[(size_t)bi * batch + atomicAdd(&ar.cnt[which], 1)] = b;
+    };
     if (act) {
         ar.list_act[atomicAdd(&ar.cnt[RL_ACT], 1)] = b;
-        if (l <= 64) ar.list_lreg[atomicAdd(&ar.cnt[RL_LREG], 1)] = b;
-        else ar.list_lsmem[atomicAdd(&ar.cnt[RL_LSMEM], 1)] = b;
+        bin_push(RB_QY + rs_row_bin(m) * kColBins + rs_col_bin(l));
+        bin_push(RB_QZ + rs_row_bin(n) * kColBins + rs_col_bin(l));
+        if (l <= 64) {
+            ar.list_lreg[atomicAdd(&ar.cnt[RL_LREG], 1)] = b;
+            bin_push(RB_LREG + (l <= 32 ? 0 : 1));
+        } else {
+            ar.list_lsmem[atomicAdd(&ar.cnt[RL_LSMEM], 1)] = b;
+        }
     }
-    if (reg) ar.list_reg[atomicAdd(&ar.cnt[RL_REG], 1)] = b;
+    if (reg) {
+        ar.list_reg[atomicAdd(&ar.cnt[RL_REG], 1)] = b;
+        bin_push(RB_FQR + rs_row_bin(mm) * 2 + (k <= 32 ? 0 : 1));
+        bin_push(RB_FSVD + (k <= 32 ? 0 : 1));
+    }
     if (smem) ar.list_smem[atomicAdd(&ar.cnt[RL_SMEM], 1)] = b;
 }
 
@@ -568,7 +604,7 @@ __global__ void __launch_bounds__(256) rs_finish_kernel(RsArrays<T> ar, T* const
     const int b = blockIdx.x;
     RsState* s = ar.st + b;
     if (info[b] == BSVD_INFO_BAD_SHAPE) return;
-    if (ar.cnt[7] != 0) {  // a tensor-core completion wait gave up: the call's results are not valid
+    if (ar.cnt[kTimeoutSlot] != 0) {  // a tensor-core completion wait gave up: the call's results are invalid
         if (threadIdx.x == 0) info[b] = BSVD_INFO_DEVICE_TIMEOUT;
         return;
     }
@@ -647,9 +683,9 @@ static RsFixed rs_fixed(int batch, int max_m, int max_n)
     F.off_ptr = o;
     o = al256(o + sizeof(T*) * (size_t)batch * kPtrArrays);
     F.off_int = o;
-    o = al256(o + sizeof(int) * (size_t)batch * kIntArrays);
+    o = al256(o + sizeof(int) * (size_t)batch * (kIntArrays + kBins));
     F.off_ctr = o;
-    o = al256(o + sizeof(unsigned long long) * 8 + sizeof(int) * 8);  // claim counters, list lengths
+    o = al256(o + sizeof(unsigned long long) * 8 + sizeof(int) * kCounters);  // claim counters, list lengths
     F.off_bjws = o;
     const int kmx = max_m < max_n ? max_m : max_n;
     F.bj_bytes = kmx > RsCap<T>::smem ? block_jacobi_workspace<T>(batch, max_m, max_n, 32, kBlockMethod) : 0;
@@ -726,14 +762,18 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
                                 &ar.list_lsmem, &ar.list_reg, &ar.list_smem, &ar.qtr, &ar.ld_q, nullptr};
     for (int i = 0; i < kIntArrays; ++i)
         if (islots[i]) *islots[i] = ip + (size_t)i * batch;
+    ar.binned = ip + (size_t)kIntArrays * batch;
     T* scratch = reinterpret_cast<T*>(w + F.off_scratch);
     unsigned long long* claim = reinterpret_cast<unsigned long long*>(w + F.off_ctr);  // one launch at a time
     ar.cnt = reinterpret_cast<int*>(claim + 8);
     auto listed = [&](const int* idx, int which) { return ItemList{idx, ar.cnt + which, claim}; };
+    auto bin_list = [&](int which) {
+        return ItemList{ar.binned + (size_t)(which - RL_COUNT) * batch, ar.cnt + which, claim};
+    };
     const long long capacity = (long long)((ws_bytes - F.off_scratch) / sizeof(T));
 
-    // tensor-core waits that gave up (cnt[7]; the round memsets clear only the list lengths)
-    if (cudaMemsetAsync(ar.cnt + 7, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
+    // tensor-core waits that gave up (the round memsets clear only the list lengths)
+    if (cudaMemsetAsync(ar.cnt + kTimeoutSlot, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
     rs_plan_kernel<T><<<batch, 256, 0, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, fixed, hint, tol_arr, tol,
                                              p, ar.st, info);
     rs_scan_kernel<<<1, 1024, 0, st>>>(batch, ar.st, capacity, info);
@@ -745,52 +785,71 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     const int lx = kx < RsCap<T>::l ? kx : RsCap<T>::l;
     int rc = BSVD_SUCCESS;
     const ItemList act = listed(ar.list_act, RL_ACT);
+    // QR of the active blocks' m x l (rows = M) or n x l (rows = N) panels, one launch per size bin
+    // that the batch's bounds can populate
+    auto qr_binned = [&](int base, int rows_max, T** P, const int* rows, const int* ldp, bool r_t) {
+        for (int rb = 0; rb < kRowBins; ++rb) {
+            if (rb > 0 && rs_row_bound(rb - 1) >= rows_max) break;
+            for (int cb = 0; cb < kColBins; ++cb) {
+                if (cb > 0 && rs_col_bound(cb - 1) >= lx) break;
+                // the last row bin has no upper bound: it takes the batch's bound
+                const int rbd = rb < kRowBins - 1 && rs_row_bound(rb) < rows_max ? rs_row_bound(rb) : rows_max;
+                const int cbd = rs_col_bound(cb) < lx ? rs_col_bound(cb) : lx;
+                if (cbd > rbd) continue;  // l < min(m, n): no block in this bin
+                const int e = launch_qr<T>(batch, rbd, cbd, (void* const*)P, rows, ar.l_act, ldp, (void* const*)P,
+                                           ldp, (void* const*)ar.pR, ar.ld_l, ar.info, st,
+                                           bin_list(base + rb * kColBins + cb), r_t);
+                if (e) return e;
+            }
+        }
+        return (int)BSVD_SUCCESS;
+    };
     for (int r = 0; r < rounds && rc == BSVD_SUCCESS && lx > 0; ++r) {
-        if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RL_COUNT, st) != cudaSuccess) return BSVD_ERR_CUDA;
+        if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RB_END, st) != cudaSuccess) return BSVD_ERR_CUDA;
         rs_arrays_kernel<T><<<tb, 128, 0, st>>>(batch, scratch, ar, 0);
         // sample: Y = A [Omega | probes]
         if constexpr (sizeof(T) == 4) {
             if (tc_sample)
-                rc = launch_rs_sample_tc(batch, act, fA, LDA, ar.pY, ar.m_act, ar.n_act, ar.l_act, seed, ar.cnt + 7,
-                                         st);
+                rc = launch_rs_sample_tc(batch, act, fA, LDA, ar.pY, ar.m_act, ar.n_act, ar.l_act, seed,
+                                         ar.cnt + kTimeoutSlot, st);
         }
         if (!tc_sample)
             rc = gemm<false, true, T>(batch, act, fA, LDA, nullptr, nullptr, ar.pY, ar.ld_m, ar.m_act, ar.lp_act,
                                       ar.n_act, ar.l_act, seed, st);
         if (rc) break;
-        rc = launch_qr<T>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY, ar.ld_m,
-                          (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
+        rc = qr_binned(RB_QY, mx, ar.pY, ar.m_act, ar.ld_m, false);
         if (rc) break;
         // q power steps: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
         for (int it = 0; it < q && rc == BSVD_SUCCESS; ++it) {
             rc = gemm<true, false, T>(batch, act, fA, LDA, ar.pY, ar.ld_m, ar.pZ, ar.ld_n, ar.n_act, ar.l_act, ar.m_act,
                                       nullptr, seed, st);
             if (rc) break;
-            rc = launch_qr<T>(batch, nx, lx, (void* const*)ar.pZ, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pZ,
-                              ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
+            rc = qr_binned(RB_QZ, nx, ar.pZ, ar.n_act, ar.ld_n, false);
             if (rc) break;
             rc = gemm<false, false, T>(batch, act, fA, LDA, ar.pZ, ar.ld_n, ar.pY, ar.ld_m, ar.m_act, ar.l_act,
                                        ar.n_act, nullptr, seed, st);
             if (rc) break;
-            rc = launch_qr<T>(batch, mx, lx, (void* const*)ar.pY, ar.m_act, ar.l_act, ar.ld_m, (void* const*)ar.pY,
-                              ar.ld_m, (void* const*)ar.pR, ar.ld_l, ar.info, st, act);
+            rc = qr_binned(RB_QY, mx, ar.pY, ar.m_act, ar.ld_m, false);
         }
         if (rc) break;
         // project: B^T = A^T Q, [Q_B, R_B] = qr(B^T)
         rc = gemm<true, false, T>(batch, act, fA, LDA, ar.pY, ar.ld_m, ar.pBt, ar.ld_n, ar.n_act, ar.l_act, ar.m_act,
                                   nullptr, seed, st);
         if (rc) break;
-        rc = launch_qr<T>(batch, nx, lx, (void* const*)ar.pBt, ar.n_act, ar.l_act, ar.ld_n, (void* const*)ar.pBt,
-                          ar.ld_n, (void* const*)ar.pR, ar.ld_l, ar.info, st, act, true);
+        rc = qr_binned(RB_QZ, nx, ar.pBt, ar.n_act, ar.ld_n, true);
         if (rc) break;
         // small SVD of R_B^T (l x l): register tier up to 64, shared tier above; with
         // BSVD_RSVD_SMALL_FP64 the register-tier ones in FP64 (operands widened, results narrowed)
         // and the shared-tier ones with FP64 rotation parameters
-        const int lr = lx < 64 ? lx : 64;
-        rc = small64 ? small_svd_fp64(batch, lr, ar.l_reg, listed(ar.list_lreg, RL_LREG), ar, st)
-                     : launch_jacobi_reg<T>(batch, lr, lr, 0, (void* const*)ar.pR, ar.l_reg, ar.l_reg, ar.ld_l,
-                                            (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
-                                            ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_lreg, RL_LREG));
+        for (int cb = 0; cb < 2 && rc == BSVD_SUCCESS; ++cb) {  // l in (0, 32], (32, 64]
+            if (cb > 0 && lx <= 32) break;
+            const int lr = (32 << cb) < lx ? (32 << cb) : lx;
+            const ItemList wl = bin_list(RB_LREG + cb);
+            rc = small64 ? small_svd_fp64(batch, lr, ar.l_reg, wl, ar, st)
+                         : launch_jacobi_reg<T>(batch, lr, lr, 0, (void* const*)ar.pR, ar.l_reg, ar.l_reg, ar.ld_l,
+                                                (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l,
+                                                (void* const*)ar.pVp, ar.ld_l, 0.0, 0, ar.info, nullptr, st, wl);
+        }
         if (rc) break;
         if (lx > 64) {
             rc = launch_jacobi_smem<T>(batch, lx, lx, (void* const*)ar.pR, ar.l_smem, ar.l_smem, ar.ld_l,
@@ -814,7 +873,7 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     if (rc) return rc;
     // full-rank blocks, and blocks whose estimate never passed, by the direct Jacobi tiers
     rs_fallback_kernel<<<tb, 128, 0, st>>>(batch, ar.st);
-    if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RL_COUNT, st) != cudaSuccess) return BSVD_ERR_CUDA;
+    if (cudaMemsetAsync(ar.cnt, 0, sizeof(int) * RB_END, st) != cudaSuccess) return BSVD_ERR_CUDA;
     rs_arrays_kernel<T><<<tb, 128, 0, st>>>(batch, scratch, ar, 1);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     const int mm_x = mx > nx ? mx : nx;
@@ -824,14 +883,29 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
         // the Q side by the batched GEMM, U~ copied
         const ItemList qlist = listed(ar.list_reg, RL_REG);
         const int kq = kx < 64 ? kx : 64;
-        rc = launch_qr<T>(batch, mm_x, kq, A, ar.m_reg, ar.n_reg, LDA, (void* const*)ar.pQf, ar.ld_q,
-                          (void* const*)ar.pR, ar.ld_l, ar.info, st, qlist, true, ar.qtr);
-        if (rc) return rc;
-        rc = small64 ? small_svd_fp64(batch, kq, ar.n_reg, qlist, ar, st)
-                     : launch_jacobi_reg<T>(batch, kq, kq, 0, (void* const*)ar.pR, ar.n_reg, ar.n_reg, ar.ld_l,
-                                            (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
-                                            ar.ld_l, 0.0, 0, ar.info, nullptr, st, qlist);
-        if (rc) return rc;
+        for (int rb = 0; rb < kRowBins; ++rb) {  // QR of A (A^T): max(m, n) x k, by size bin
+            if (rb > 0 && rs_row_bound(rb - 1) >= mm_x) break;
+            for (int cb = 0; cb < 2; ++cb) {
+                if (cb > 0 && kq <= 32) break;
+                const int rbd = rb < kRowBins - 1 && rs_row_bound(rb) < mm_x ? rs_row_bound(rb) : mm_x;
+                const int cbd = (32 << cb) < kq ? (32 << cb) : kq;
+                if (cbd > rbd) continue;
+                rc = launch_qr<T>(batch, rbd, cbd, A, ar.m_reg, ar.n_reg, LDA, (void* const*)ar.pQf, ar.ld_q,
+                                  (void* const*)ar.pR, ar.ld_l, ar.info, st, bin_list(RB_FQR + rb * 2 + cb), true,
+                                  ar.qtr);
+                if (rc) return rc;
+            }
+        }
+        for (int cb = 0; cb < 2; ++cb) {  // SVD of R^T: k x k, by size bin
+            if (cb > 0 && kq <= 32) break;
+            const int kb = (32 << cb) < kq ? (32 << cb) : kq;
+            const ItemList wl = bin_list(RB_FSVD + cb);
+            rc = small64 ? small_svd_fp64(batch, kb, ar.n_reg, wl, ar, st)
+                         : launch_jacobi_reg<T>(batch, kb, kb, 0, (void* const*)ar.pR, ar.n_reg, ar.n_reg, ar.ld_l,
+                                                (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l,
+                                                (void* const*)ar.pVp, ar.ld_l, 0.0, 0, ar.info, nullptr, st, wl);
+            if (rc) return rc;
+        }
         rc = gemm<false, false, T>(batch, qlist, ar.pQf, ar.ld_q, ar.pVp, ar.ld_l, ar.pCf, ar.ld_q, ar.m_reg, ar.n_reg,
                                    ar.n_reg, nullptr, seed, st);
         if (rc) return rc;

@@ -73,17 +73,6 @@ def test_max_over_ranks_single_rank_is_identity():
     assert bench.max_over_ranks(3.25, 1, None) == 3.25
 
 
-@pytest.mark.parametrize("n,chunks", [(20000, 4), (1000, 3), (7, 4), (5, 8), (1, 4), (0, 4), (10, 1)])
-def test_chunk_bounds_cover_the_batch_once(n, chunks):
-    from paper_1707_05141_gb300.pipeline import chunk_bounds
-    b = chunk_bounds(n, chunks)
-    assert len(b) <= max(1, chunks)
-    covered = [i for c0, c1 in b for i in range(c0, c1)]
-    assert covered == list(range(n))
-    assert all(c1 > c0 for c0, c1 in b)
-    assert len({c1 - c0 for c0, c1 in b[:-1]}) <= 1
-
-
 def test_launch_counts_follow_the_host_drivers():
     # block tier, 512 columns of width 32: 16 blocks, 15 steps x (Gram, inner SVD, polish, update)
     # and the sweep-end kernel for each of 20 sweeps, plus setup and finalize
@@ -93,6 +82,11 @@ def test_launch_counts_follow_the_host_drivers():
     # shared tier, the block tier over 256 columns (8 blocks, 7 steps) and the finish kernel
     # the block tier on R^T of a blocked QR: setup, 8 panels, 7 trailing updates, R^T, the block
     # Jacobi, the zero fill, 8 block-reflector applications
-    assert bench.rsvd_launches(256, 256, 4) == 2 + 4 * 15 + 2 + 4 + 1 + (1 + 8 + 7 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1 + 8) + 1
+    # per round: arrays, sample, 8 QR bins of Y, power step (8 + GEMM + 8 + GEMM), projection (GEMM + 8),
+    # 2 small-SVD bins, the shared tier, 2 GEMMs, estimate; full-rank path: 6 QR bins, 2 SVD bins,
+    # GEMM, copy, shared tier
+    assert bench.rsvd_launches(256, 256, 4) == (2 + 4 * (1 + 1 + 8 + (8 + 1 + 8 + 1) + (1 + 8) + 2 + 1 + 2 + 1) + 2
+                                               + (6 + 2 + 2 + 1)
+                                               + (1 + 8 + 7 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1 + 8) + 1)
     # blocks up to 64 x 64: no shared or block tier
-    assert bench.rsvd_launches(64, 64, 4) == 2 + 4 * 14 + 2 + 4 + 1
+    assert bench.rsvd_launches(64, 64, 4) == 2 + 4 * (1 + 1 + 2 + (2 + 1 + 2 + 1) + (1 + 2) + 2 + 2 + 1) + 2 + (2 + 2 + 2) + 1

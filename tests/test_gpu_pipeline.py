@@ -1,5 +1,6 @@
-"""The host-in/host-out pipeline (copies overlapped with the computation, chunk by chunk) gives
-the same results, bit for bit, as one direct call on the device."""
+"""The host-in/host-out entry points (bsvd_host_svd, bsvd_host_qr: copies overlapped with the
+computation, chunk by chunk) give the same results, bit for bit, as one direct call on the device:
+every matrix is computed by the same kernel whatever chunk it falls in."""
 import numpy as np
 import pytest
 
@@ -9,48 +10,56 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_chunked_pipeline_matches_direct_call():
+@pytest.fixture(scope="module")
+def bs():
     import paper_1707_05141_gb300 as bs
-    from paper_1707_05141_gb300.pipeline import ChunkPipeline
     bs.build()
+    assert torch.cuda.is_available()
+    return bs
+
+
+@pytest.mark.parametrize("chunks,pinned", [(1, True), (4, True), (7, True), (3, False)])
+def test_host_svd_matches_direct_call(bs, chunks, pinned):
     dev = torch.device("cuda")
     b = gen.svd64_exp8(batch=1000)
-    h_a = torch.from_numpy(b.a).pin_memory()
+    h_a = torch.from_numpy(b.a)
+    if pinned:
+        h_a = h_a.pin_memory()
     d_a = h_a.to(dev)
-    outs = [torch.empty((1000, 1, 64), device=dev), torch.empty((1000, 64, 64), device=dev),
-            torch.empty((1000, 64, 64), device=dev)]
-    info = torch.empty(1000, dtype=torch.int32, device=dev)
-    # direct: the whole batch in one call
-    s, u, v = (torch.empty_like(o) for o in outs)
-    bs.batched_svd_jacobi(bs.Batch.uniform(d_a, 64, 64), bs.Batch.uniform(s, 64, 1), bs.Batch.uniform(u, 64, 64),
-                          bs.Batch.uniform(v, 64, 64), info)
+    u0, s0, v0, i0, _ = bs.svd(d_a)
+    mk = lambda *shape, dt=torch.float32: (torch.zeros(shape, dtype=dt).pin_memory() if pinned
+                                           else torch.zeros(shape, dtype=dt))
+    s, u, v, info = mk(1000, 64), mk(1000, 64, 64), mk(1000, 64, 64), mk(1000, dt=torch.int32)
+    ws = torch.empty(bs.host_svd_workspace(bs.F32, 1000, 64, 64), dtype=torch.uint8, device=dev)
+    bs.host_svd(h_a, s, u, v, info, chunks=chunks, workspace=ws)
     torch.cuda.synchronize()
-    # pipelined: 4 chunks, host in, host out
-    h_out = [torch.zeros(o.shape, dtype=o.dtype).pin_memory() for o in outs]
-    d_in = [torch.zeros_like(d_a)]
-    chunk_info = torch.empty(1000, dtype=torch.int32, device=dev)
-
-    pipe = ChunkPipeline([h_a], h_out, d_in, outs, lambda c0, c1, di, do, st: None, chunks=4)
-    batches = {(c0, c1): (bs.Batch.uniform(d_in[0][c0:c1], 64, 64), bs.Batch.uniform(outs[0][c0:c1], 64, 1),
-                          bs.Batch.uniform(outs[1][c0:c1], 64, 64), bs.Batch.uniform(outs[2][c0:c1], 64, 64))
-               for c0, c1 in pipe.bounds}
-
-    def compute(c0, c1, di, do, st):
-        a, sb, ub, vb = batches[(c0, c1)]
-        bs.batched_svd_jacobi(a, sb, ub, vb, chunk_info[c0:c1], stream=st)
-
-    pipe.compute = compute
-    assert len(pipe.bounds) == 4
-    pipe.run()
-    torch.cuda.synchronize()
-    assert torch.equal(chunk_info, info)
-    for h, d in zip(h_out, (s, u, v)):
-        assert torch.equal(h, d.cpu())
+    assert torch.equal(info, i0.cpu())
+    assert torch.equal(s, s0.cpu().reshape(1000, 64)) and torch.equal(u, u0.cpu()) and torch.equal(v, v0.cpu())
 
 
-def test_pipeline_rejects_pageable_host_buffers():
-    from paper_1707_05141_gb300.pipeline import ChunkPipeline
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_host_qr_matches_direct_call(bs, dtype):
     dev = torch.device("cuda")
-    h = torch.zeros((8, 4))
+    b = gen.qr128x32_exp8(batch=300) if dtype == np.float32 else gen.fp64_32_graded(batch=300)
+    h_a = torch.from_numpy(b.a).pin_memory()
+    q0, r0, i0 = bs.qr(h_a.to(dev))
+    bsz, n, m = h_a.shape
+    q = torch.zeros((bsz, n, m), dtype=h_a.dtype).pin_memory()
+    r = torch.zeros((bsz, n, n), dtype=h_a.dtype).pin_memory()
+    info = torch.zeros(bsz, dtype=torch.int32).pin_memory()
+    code = bs.F32 if dtype == np.float32 else bs.F64
+    ws = torch.empty(bs.host_qr_workspace(code, bsz, m, n), dtype=torch.uint8, device=dev)
+    bs.host_qr(h_a, q, r, info, chunks=5, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(info, i0.cpu()) and torch.equal(q, q0.cpu()) and torch.equal(r, r0.cpu())
+
+
+def test_host_entries_refuse_device_tensors_and_short_workspaces(bs):
+    dev = torch.device("cuda")
+    a = torch.zeros((4, 8, 8))
+    s = torch.zeros((4, 8))
     with pytest.raises(ValueError):
-        ChunkPipeline([h], [h], [h.to(dev)], [h.to(dev)], lambda *a: None)
+        bs.host_svd(a.to(dev), s, workspace=torch.empty(1 << 20, dtype=torch.uint8, device=dev))
+    with pytest.raises(bs.BsvdError) as e:
+        bs.host_svd(a, s, workspace=torch.empty(16, dtype=torch.uint8, device=dev))
+    assert e.value.code == bs.ERR_WORKSPACE
