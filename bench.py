@@ -324,9 +324,15 @@ class SvdQr64:
         ws_q = torch.empty(bs.host_qr_workspace(bs.F32, self.nq, 128, 32), dtype=torch.uint8, device=dev)
         ws_s = torch.empty(bs.host_svd_workspace(bs.F32, self.nb, 64, 64), dtype=torch.uint8, device=dev)
 
+        side = torch.cuda.Stream(device=dev)
+
         def step(stream):
-            bs.host_qr(h_qr, hq, hr, chunks=chunks, workspace=ws_q, stream=stream)
+            # the two independent calls on two streams: the QR's copies and kernels overlap the
+            # SVD's (the library's copy streams keep each direction's transfers in issue order)
+            side.wait_stream(stream)
+            bs.host_qr(h_qr, hq, hr, chunks=chunks, workspace=ws_q, stream=side)
             bs.host_svd(h_svd, hs, hu, hv, chunks=chunks, workspace=ws_s, stream=stream)
+            stream.wait_stream(side)
         return step
 
     def roofline(self, kernel_ms):

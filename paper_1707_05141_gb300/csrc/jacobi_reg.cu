@@ -273,11 +273,18 @@ __global__ void __launch_bounds__(NS * PARTS, MINB)
                         }
                     }
                 } else {
+                    // gamma alone: four chains (a0, b0 serve as the third and fourth), so that the
+                    // dot product's FMA latency is not the step's critical path
 #pragma unroll
-                    for (int k = 0; k < RA; k += 2) {
+                    for (int k = 0; k < RA; k += 4) {
                         c0 = fma(aL[k], aR[k], c0);
                         if (k + 1 < RA) c1 = fma(aL[k + 1], aR[k + 1], c1);
+                        if (k + 2 < RA) a0 = fma(aL[k + 2], aR[k + 2], a0);
+                        if (k + 3 < RA) b0 = fma(aL[k + 3], aR[k + 3], b0);
                     }
+                    c0 += a0;
+                    c1 += b0;
+                    a0 = b0 = T(0);
                 }
                 T sa = a0 + a1, sb = b0 + b1, sc = c0 + c1;
                 if (PPW == 2) {

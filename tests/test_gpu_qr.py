@@ -56,18 +56,28 @@ RAGGED = [(1, 1), (2, 1), (7, 3), (33, 33), (64, 1), (100, 37), (129, 64), (5, 0
           (256, 96)]
 
 
-@pytest.mark.parametrize("dt,shapes", [(np.float32, RAGGED), (np.float64, RAGGED),
-                                       (np.float32, [(256, 192), (255, 191), (3, 2)]),    # 200 KiB in shared memory
-                                       (np.float32, [(1024, 16), (1000, 15), (17, 16)]),  # tallest supported
-                                       (np.float64, [(1024, 24), (512, 20)])])
-def test_qr_ragged_shapes_and_edges(bs, dt, shapes):
+# the warp-per-matrix register form: FP32 m <= 128, n <= 32 (one column per lane) and m <= 64,
+# n <= 64 (two); FP64 m <= 64, n <= 32
+WARP_F32 = [(1, 1), (2, 1), (7, 3), (33, 32), (64, 1), (100, 31), (128, 32), (5, 0), (0, 0), (31, 31), (48, 17),
+            (127, 32)]
+WARP_F32_WIDE = [(64, 64), (63, 40), (33, 33), (64, 33), (2, 2), (60, 59), (0, 0), (40, 1)]
+WARP_F64 = [(1, 1), (64, 32), (37, 20), (40, 32), (64, 1), (50, 31), (3, 0), (32, 32), (2, 2), (63, 31)]
+
+
+@pytest.mark.parametrize("dt,shapes,special", [
+    (np.float32, RAGGED, (3, 5)), (np.float64, RAGGED, (3, 5)),
+    (np.float32, WARP_F32, (3, 5)), (np.float32, WARP_F32_WIDE, (0, 1)), (np.float64, WARP_F64, (1, 5)),
+    (np.float32, [(256, 192), (255, 191), (3, 2)], ()),    # 200 KiB in shared memory
+    (np.float32, [(1024, 16), (1000, 15), (17, 16)], ()),  # tallest supported
+    (np.float64, [(1024, 24), (512, 20)], ())])
+def test_qr_ragged_shapes_and_edges(bs, dt, shapes, special):
     rng = np.random.default_rng(7)
     mats = [rng.standard_normal(sh) * 10.0 ** rng.uniform(-2, 2) for sh in shapes]
-    special = set()
-    if shapes is RAGGED:
-        mats[3][:, 5] = 0.0                  # a zero column: identity reflector
-        mats[5][:, 10] = mats[5][:, 2]      # repeated column: R is rank deficient
-        special = {3, 5}
+    if special:
+        z, rep = special
+        mats[z][:, 5] = 0.0                  # a zero column: identity reflector
+        mats[rep][:, 10] = mats[rep][:, 2]  # repeated column: R is rank deficient
+    special = set(special)
     ms = np.array([s[0] for s in shapes], np.int32)
     ns = np.array([s[1] for s in shapes], np.int32)
     sizes = (ms.astype(np.int64) * ns + 1)
