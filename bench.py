@@ -191,24 +191,27 @@ def rsvd_launches(max_m, max_n, rounds):
     """Kernels one batched_rsvd call launches: plan and scan; per round the arrays kernel, the
     sampling GEMM, the QRs of the sample, the power step's two products and two QRs, the projection
     and its QR (each QR once per size bin the bounds can populate: rows in (0, 64], (64, 128],
-    (128, 256], columns in (0, 32], (32, 64], (64, 128], no bin with more columns than rows), the
+    (128, ...), columns in (0, 32], (32, 64], (64, ...), no bin with more columns than rows), the
     small SVD per column bin (register tier; plus the shared tier when samples may pass 64), two
     GEMMs for U and V and the estimate; then the fallback and arrays kernels, the full-rank QR path
-    (QR per row bin and column bin up to 64, SVD per column bin, GEMM, copy), the shared tier
-    (min > 64), the block tier on R^T of a blocked QR (min > 128) and the finish kernel."""
+    (QR per row bin and column bin up to 128, the SVD of R^T per register-tier column bin and in the
+    shared tier when min > 64, GEMM, copy), the block tier on R^T of a blocked QR (min > 128) and
+    the finish kernel."""
     kx = min(max_m, max_n)
-    lx = min(kx, 128)
+    lx = min(kx, 160)  # the FP32 sample cap
 
     def bins(rows_max, cols_max, col_bins):
         n = 0
         for rb in range(3):
             if rb > 0 and (64 << (rb - 1)) >= rows_max:
                 break
+            rbd = (64 << rb) if rb < 2 and (64 << rb) < rows_max else rows_max
             for cb in range(col_bins):
                 if cb > 0 and (32 << (cb - 1)) >= cols_max:
                     break
-                if min(32 << cb, cols_max) <= min(64 << rb, rows_max):
-                    n += 1
+                if cb > 0 and (32 << (cb - 1)) >= rbd:
+                    continue  # no block has more samples than rows
+                n += 1
         return n
 
     qy, qz = bins(max_m, lx, 3), bins(max_n, lx, 3)
@@ -216,8 +219,8 @@ def rsvd_launches(max_m, max_n, rounds):
     per_round = 1 + 1 + qy + (qz + 1 + qy + 1) + (1 + qz) + small + (1 if lx > 64 else 0) + 2 + 1
     n = 2 + rounds * per_round + 2
     if kx > 0:
-        kq = min(kx, 64)
-        n += bins(max(max_m, max_n), kq, 2) + (1 + (1 if kq > 32 else 0)) + 2 + (1 if kx > 64 else 0)
+        kq = min(kx, 128)
+        n += bins(max(max_m, max_n), kq, 3) + (1 + (1 if kq > 32 else 0)) + (1 if kq > 64 else 0) + 2
         n += block_qr_launches(kx) if kx > 128 else 0
     return n + 1
 
@@ -819,7 +822,7 @@ class RsvdBase:
         from concurrent.futures import ThreadPoolExecutor
 
         def one(b):
-            oracle.rsvd_adaptive(rb.a64(b), 1707, b, int(hint[b]) if hint is not None else 0, 1e-5, 8, 1, 16, 128)
+            oracle.rsvd_adaptive(rb.a64(b), 1707, b, int(hint[b]) if hint is not None else 0, 1e-5, 8, 1, 16, 160)
 
         t0 = time.time()
         with ThreadPoolExecutor(max_workers=cores) as ex:

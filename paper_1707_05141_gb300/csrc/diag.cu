@@ -30,7 +30,7 @@ __global__ void philox_gauss_kernel(int count, const unsigned* ctr, unsigned lon
         gauss[4 * i + 3] = z.w;
     }
     if (gauss64) {
-        const double4 z = gauss4d(seed, c.z, c.w, c.x, c.y);
+        const Gauss4d z = gauss4d(seed, c.z, c.w, c.x, c.y);
         gauss64[4 * i] = z.x;
         gauss64[4 * i + 1] = z.y;
         gauss64[4 * i + 2] = z.z;

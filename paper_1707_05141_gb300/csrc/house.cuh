@@ -60,4 +60,51 @@ __device__ __forceinline__ void house_factor_smem(T* S, int ld, T* diag, int m, 
     }
 }
 
+// The same factorisation for m <= 32 RPL: each warp keeps reflector i's rows (i + lane + 32 t) in
+// registers for the whole step and each of its trailing columns in registers between the product and
+// the update, so an element costs one shared load, one shared store and two FMAs (the loop above
+// reads the reflector twice and the column twice).
+template <typename T, int RPL>
+__device__ __forceinline__ void house_factor_smem_rows(T* S, int ld, T* diag, int m, int n)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (n > 0 && warp == 0) house_reflector(S, 0, m, diag, lane);
+    __syncthreads();
+    for (int i = 0; i < n; ++i) {
+        const T* col = S + (size_t)i * ld;
+        T v[RPL];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int r = i + lane + 32 * t;
+            v[t] = r < m ? col[r] : T(0);
+        }
+        const int first = i + 1 + ((warp - (i + 1) % nwarps) + nwarps) % nwarps;
+        for (int j = first; j < n; j += nwarps) {
+            T* cj = S + (size_t)j * ld;
+            T x[RPL];
+            T w0 = T(0), w1 = T(0);
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int r = i + lane + 32 * t;
+                x[t] = r < m ? cj[r] : T(0);
+                if (t & 1)
+                    w1 = fma(v[t], x[t], w1);
+                else
+                    w0 = fma(v[t], x[t], w0);
+            }
+            const T w = T(2) * warp_sum(w0 + w1);
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                const int r = i + lane + 32 * t;
+                if (r < m) cj[r] = fma(-w, v[t], x[t]);
+            }
+            if (j == i + 1) {
+                __syncwarp();
+                house_reflector(cj, j, m, diag, lane);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace bsvd

@@ -19,7 +19,7 @@
 namespace bsvd {
 
 template <typename T, typename P, int G, int MAXR>
-__global__ void __launch_bounds__(64 * G > 1024 ? 1024 : 64 * G) jacobi_smem_kernel(int batch, int max_mm, int max_np, T* const* A, const int* M, const int* N,
+__global__ void __launch_bounds__(80 * G > 1024 ? 1024 : 80 * G) jacobi_smem_kernel(int batch, int max_mm, int max_np, T* const* A, const int* M, const int* N,
                                    const int* LDA, T* const* Sout, T* const* U, const int* LDU, T* const* V,
                                    const int* LDV, double tol_in, int max_sweeps, int* info, long long* rot_out,
                                    ItemList wl)
@@ -233,14 +233,22 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
     const int max_mm = max_m > max_n ? max_m : max_n;
     const int max_nn = max_m > max_n ? max_n : max_m;
     const int max_np = (max_nn + 1) & ~1;
-    const int maxk_lim = sizeof(T) == 4 ? 128 : 64;
+    const int maxk_lim = sizeof(T) == 4 ? 160 : 64;  // and the matrix and V must fit in shared memory
     if (max_mm > 256 || max_nn > maxk_lim) return BSVD_ERR_UNSUPPORTED;
     if (max_np == 0) return launch_g<T, T, 1, 16>(batch, max_mm, 2, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps,
                                                  info, rot, st, wl);
     if (jacobi_smem_bytes<T>(max_mm, max_np) > 220 * 1024) return BSVD_ERR_UNSUPPORTED;
     int g = 1;
     while (g * 16 < max_mm) g *= 2;
-    if ((max_np / 2) * g > 1024) return BSVD_ERR_UNSUPPORTED;
+    if ((max_np / 2) * g > 1024) {
+        // more than 1024 threads at 16 rows per lane: 8 lanes per pair with up to 24 rows each
+        if (max_mm > 8 * 24 || (max_np / 2) * 8 > 1024) return BSVD_ERR_UNSUPPORTED;
+        return p64 && sizeof(T) == 4
+                   ? launch_g<T, double, 8, 24>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol,
+                                                max_sweeps, info, rot, st, wl)
+                   : launch_g<T, T, 8, 24>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps,
+                                           info, rot, st, wl);
+    }
 #define BSVD_LAUNCH_G(GG)                                                                                          \
     return p64 && sizeof(T) == 4                                                                                   \
                ? launch_g<T, double, GG, 16>(batch, max_mm, max_np, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, \

@@ -44,9 +44,14 @@ __device__ __forceinline__ float4 gauss4(unsigned long long seed, uint32_t index
     return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
 }
 
+// four FP64 normals
+struct Gauss4d {
+    double x, y, z, w;
+};
+
 // the same four normals in FP64 (the FP64 randomized SVD): uniforms exact in double, double log
 // and sin / cos
-__device__ __forceinline__ double4 gauss4d(unsigned long long seed, uint32_t index, uint32_t tag, uint32_t g,
+__device__ __forceinline__ Gauss4d gauss4d(unsigned long long seed, uint32_t index, uint32_t tag, uint32_t g,
                                            uint32_t c)
 {
     const uint4 w = philox4x32_10(make_uint4(g, c, index, tag), (uint32_t)seed, (uint32_t)(seed >> 32));
@@ -57,7 +62,7 @@ __device__ __forceinline__ double4 gauss4d(unsigned long long seed, uint32_t ind
     double s0, c0, s1, c1;
     sincospi(2.0 * ub, &s0, &c0);
     sincospi(2.0 * ud, &s1, &c1);
-    return make_double4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+    return Gauss4d{r0 * c0, r0 * s0, r1 * c1, r1 * s1};
 }
 
 __device__ __forceinline__ float gauss1(unsigned long long seed, uint32_t index, uint32_t tag, uint32_t r, uint32_t c)

@@ -66,7 +66,10 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         if (__syncthreads_or(nonfinite) && tid == 0) info[b] = BSVD_INFO_NONFINITE;
 
         // ---- factorisation: v_i = house(R(i:m, i)); R = (I - 2 v v^T) R ----
-        house_factor_smem(S, ld, diag, m, n);
+        if (max_m <= 32 * QROWS)
+            house_factor_smem_rows<T, QROWS>(S, ld, diag, m, n);
+        else
+            house_factor_smem(S, ld, diag, m, n);
 
         // ---- R: strict upper part from S, diagonal from diag, zeros below ----
         if (R) {
@@ -260,8 +263,16 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// CTAs per SM the register allocation is capped for: the 128-row FP32 form fits three (12 warps)
+// in 170 registers with a few bytes of spill outside the loops; the others keep the compiler's
+// allocation
 template <typename T, int ROWS, int CPL>
-__global__ void __launch_bounds__(128) qr_warp_kernel(int batch, int max_m, int max_n, T* const* A, const int* M,
+struct QrWarpMinBlocks {
+    static constexpr int value = (sizeof(T) == 4 && ROWS == 128 && CPL == 1) ? 3 : 1;
+};
+
+template <typename T, int ROWS, int CPL>
+__global__ void __launch_bounds__(128, QrWarpMinBlocks<T, ROWS, CPL>::value) qr_warp_kernel(int batch, int max_m, int max_n, T* const* A, const int* M,
                                                       const int* N, const int* LDA, T* const* Q, const int* LDQ,
                                                       T* const* R, const int* LDR, int* info, ItemList wl, int r_trans,
                                                       const int* a_trans)

@@ -3,15 +3,16 @@
 // Every block b (m x n, any shape up to 256 x 256) is processed by one batched pipeline, all
 // blocks at once, sizes per block:
 //   plan     ||A||_F (FP64 sums), l = k + p for a fixed rank k (Algorithm 4 as stated), else
-//            hint + p; a block whose l reaches min(m, n), or passes the sample cap (128 columns
-//            in FP32, 64 in FP64: the small SVD stays in the register / shared tiers), is full
+//            hint + p; a block whose l reaches min(m, n), or passes the sample cap (160 columns
+//            in FP32, 128 with tensor-core sampling, 64 in FP64: the small SVD stays in the
+//            register / shared tiers), is full
 //            rank: it skips the randomized steps and is factored directly at the end.
 //   sample   Y = A [Omega | Omega_probe]: Omega (n x l) and 8 probe columns are generated on the
 //            fly from Philox (no Omega in memory), one batched GEMM.
 //   range    [Q, ~] = qr(Y);  q power steps: Z = A^T Q, Qz = qr(Z), Y = A Qz, Q = qr(Y)
 //            (randomized subspace iteration, the robust variant Section 7 mentions).
 //   project  B^T = A^T Q (n x l), [Q_B, R_B] = qr(B^T)   (Section 7, phase 2).
-//   small    SVD of R_B^T by one-sided Jacobi (register tier for l <= 64, shared tier to 128):
+//   small    SVD of R_B^T by one-sided Jacobi (register tier for l <= 64, shared tier to 160):
 //            R_B^T = U_R S V_R^T, so A ~ Q B = Q R_B^T Q_B^T and U = Q U_R, V = Q_B V_R (the QR
 //            writes R_B transposed; one-sided Jacobi on the lower-triangular R_B^T, whose rows are
 //            graded like the singular values, converges in fewer sweeps than on R_B: the same
@@ -37,13 +38,13 @@
 namespace bsvd {
 
 constexpr int kProbes = 8;     // probe columns of the posterior estimate
-constexpr int kLCapMax = 128;  // largest sample cap (FP32)
+constexpr int kLCapMax = 160;  // largest sample cap (FP32)
 constexpr int kMaxDim = 256;
 
 // sample cap (the small l x l SVD stays in the register / shared tiers) and the largest min(m, n)
 // the shared tier takes for a full-rank block, per element type
 template <typename T> struct RsCap;
-template <> struct RsCap<float> { static constexpr int l = 128, smem = 128; };
+template <> struct RsCap<float> { static constexpr int l = 160, smem = 128; };
 template <> struct RsCap<double> { static constexpr int l = 64, smem = 64; };
 
 enum { RS_RSVD = 0, RS_FULL = 1, RS_DONE = 2 };
@@ -59,6 +60,7 @@ struct RsState {
     int mode;          // RS_*
     int rank, flags, rounds;
     int fixed;         // fixed rank (> 0), or 0: tolerance mode
+    int cap;           // sample cap of this call (RsCap<T>::l, or less)
     double eps;        // relative Frobenius tolerance of this block
     double norm2;      // ||A||_F^2
     double est2;       // posterior estimate of ||A - U S V^T||_F^2 (rank ell)
@@ -125,14 +127,14 @@ struct RsArrays {
     RsState* st;
 };
 enum { RL_ACT = 0, RL_LREG, RL_LSMEM, RL_REG, RL_SMEM, RL_COUNT };
-// bins: rows (m or n; max(m, n) on the full-rank path) in (0, 64], (64, 128], (128, 256]; columns
-// (l, or k) in (0, 32], (32, 64], (64, 128]
+// bins: rows (m or n; max(m, n) on the full-rank path) in (0, 64], (64, 128], (128, ...); columns
+// (l, or k) in (0, 32], (32, 64], (64, ...)
 constexpr int kRowBins = 3, kColBins = 3;
 constexpr int RB_QY = RL_COUNT;                         // QR of Y (m x l): 9 bins
 constexpr int RB_QZ = RB_QY + kRowBins * kColBins;      // QR of Z and B^T (n x l): 9 bins
 constexpr int RB_LREG = RB_QZ + kRowBins * kColBins;    // small SVD, register tier (l <= 32, <= 64)
-constexpr int RB_FQR = RB_LREG + 2;                     // full-rank QR path: QR of A (max(m,n) x k), k <= 64
-constexpr int RB_FSVD = RB_FQR + kRowBins * 2;          // ... and the SVD of R^T (k <= 32, <= 64)
+constexpr int RB_FQR = RB_LREG + 2;                     // full-rank QR path: QR of A (max(m,n) x k), 3 x 3 bins
+constexpr int RB_FSVD = RB_FQR + kRowBins * kColBins;   // ... and the SVD of R^T, register tier (k <= 32, <= 64)
 constexpr int RB_END = RB_FSVD + 2;
 constexpr int kBins = RB_END - RL_COUNT;
 constexpr int kCounters = 64;                           // list lengths and flags (ints)
@@ -179,7 +181,7 @@ __device__ __forceinline__ void gauss4t(unsigned long long seed, uint32_t idx, u
 __device__ __forceinline__ void gauss4t(unsigned long long seed, uint32_t idx, uint32_t tag, uint32_t g, uint32_t c,
                                         double (&z)[4])
 {
-    const double4 v = gauss4d(seed, idx, tag, g, c);
+    const Gauss4d v = gauss4d(seed, idx, tag, g, c);
     z[0] = v.x;
     z[1] = v.y;
     z[2] = v.z;
@@ -303,7 +305,8 @@ static int gemm(int batch, ItemList wl, T* const* A, const int* LDA, T* const* B
 template <typename T>
 __global__ void __launch_bounds__(256) rs_plan_kernel(int batch, int max_m, int max_n, T* const* A, const int* M,
                                                       const int* N, const int* LDA, const int* fixed, const int* hint,
-                                                      const double* tol_arr, double tol, int p, RsState* st, int* info)
+                                                      const double* tol_arr, double tol, int p, int cap, RsState* st,
+                                                      int* info)
 {
     const int b = blockIdx.x;
     const int m = M[b], n = N[b], lda = LDA[b];
@@ -336,7 +339,8 @@ __global__ void __launch_bounds__(256) rs_plan_kernel(int batch, int max_m, int 
         int l = h + p;
         if (l < 1) l = 1;
         r.ell = l;
-        r.mode = bad || r.k == 0 ? RS_DONE : ((l >= r.k || l > RsCap<T>::l) ? RS_FULL : RS_RSVD);
+        r.mode = bad || r.k == 0 ? RS_DONE : ((l >= r.k || l > cap) ? RS_FULL : RS_RSVD);
+        r.cap = cap;
         r.rank = 0;
         r.flags = 0;
         r.rounds = 0;
@@ -430,9 +434,10 @@ __global__ void rs_arrays_kernel(int batch, T* scratch, RsArrays<T> ar, int fina
     ar.ld_l[b] = l > 1 ? l : 1;
     const bool full = final && s.mode == RS_FULL;
     const int mm = m > n ? m : n;
-    const bool reg = full && k <= 64;  // the QR path (max(m, n) <= 256)
+    // the QR path: A = Q R, the SVD of R^T (register tier for k <= 64, shared tier above), Q V~
+    const bool reg = full && k <= RsCap<T>::smem;
     const bool blk = full && k > RsCap<T>::smem;
-    const bool smem = full && !reg && !blk;
+    const bool smem = reg && k > 64;  // its SVD of R^T in the shared tier
     const bool wide = m < n;
     ar.m_reg[b] = reg ? mm : 0;
     ar.n_reg[b] = reg ? k : 0;
@@ -442,8 +447,8 @@ __global__ void rs_arrays_kernel(int batch, T* scratch, RsArrays<T> ar, int fina
     ar.pCf[b] = wide ? ar.pVw[b] : ar.pUw[b];
     ar.pDf[b] = wide ? ar.pUw[b] : ar.pVw[b];
     if (reg) ar.ld_l[b] = k > 1 ? k : 1;
-    ar.m_smem[b] = smem ? m : 0;
-    ar.n_smem[b] = smem ? n : 0;
+    ar.m_smem[b] = 0;
+    ar.n_smem[b] = 0;
     ar.m_blk[b] = blk ? m : 0;
     ar.n_blk[b] = blk ? n : 0;
     auto bin_push = [&](int which) {
@@ -463,8 +468,8 @@ __global__ void rs_arrays_kernel(int batch, T* scratch, RsArrays<T> ar, int fina
     }
     if (reg) {
         ar.list_reg[atomicAdd(&ar.cnt[RL_REG], 1)] = b;
-        bin_push(RB_FQR + rs_row_bin(mm) * 2 + (k <= 32 ? 0 : 1));
-        bin_push(RB_FSVD + (k <= 32 ? 0 : 1));
+        bin_push(RB_FQR + rs_row_bin(mm) * kColBins + rs_col_bin(k));
+        if (!smem) bin_push(RB_FSVD + (k <= 32 ? 0 : 1));
     }
     if (smem) ar.list_smem[atomicAdd(&ar.cnt[RL_SMEM], 1)] = b;
 }
@@ -526,7 +531,7 @@ __device__ __forceinline__ void rs_estimate_item(int b, const RsArrays<T>& ar, u
             s->mode = RS_DONE;  // fixed rank, or range accepted: finish from this round's factors
         } else {
             const int next = s->ell + p;
-            if (next >= s->k || next > RsCap<T>::l) {
+            if (next >= s->k || next > s->cap) {
                 s->mode = RS_FULL;
                 s->est2 = 0.0;
                 s->flags |= RSF_FALLBACK;
@@ -755,6 +760,8 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     const bool small64 = sizeof(T) == 4 && (flags & BSVD_RSVD_SMALL_FP64) != 0;
     // the sampling product on the tensor cores: FP32 runs only
     const bool tc_sample = sizeof(T) == 4 && (flags & BSVD_RSVD_TC_SAMPLING) != 0;
+    // sample cap of this call: the tensor-core sampling kernel takes l <= 128
+    const int lcap_run = tc_sample && RsCap<T>::l > 128 ? 128 : RsCap<T>::l;
     int* ip = reinterpret_cast<int*>(w + F.off_int);
     int** islots[kIntArrays] = {&ar.m_act, &ar.n_act, &ar.l_act, &ar.lp_act, &ar.l_reg, &ar.l_smem,
                                 &ar.ld_m, &ar.ld_n, &ar.ld_l, &ar.m_reg, &ar.n_reg, &ar.m_smem,
@@ -775,14 +782,14 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     // tensor-core waits that gave up (the round memsets clear only the list lengths)
     if (cudaMemsetAsync(ar.cnt + kTimeoutSlot, 0, sizeof(int), st) != cudaSuccess) return BSVD_ERR_CUDA;
     rs_plan_kernel<T><<<batch, 256, 0, st>>>(batch, max_m, max_n, (T* const*)A, M, N, LDA, fixed, hint, tol_arr, tol,
-                                             p, ar.st, info);
+                                             p, lcap_run, ar.st, info);
     rs_scan_kernel<<<1, 1024, 0, st>>>(batch, ar.st, capacity, info);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     const int tb = (batch + 127) / 128;
     T* const* fA = (T* const*)A;
     const int mx = max_m, nx = max_n;
     const int kx = mx < nx ? mx : nx;
-    const int lx = kx < RsCap<T>::l ? kx : RsCap<T>::l;
+    const int lx = kx < lcap_run ? kx : lcap_run;
     int rc = BSVD_SUCCESS;
     const ItemList act = listed(ar.list_act, RL_ACT);
     // QR of the active blocks' m x l (rows = M) or n x l (rows = N) panels, one launch per size bin
@@ -792,10 +799,11 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
             if (rb > 0 && rs_row_bound(rb - 1) >= rows_max) break;
             for (int cb = 0; cb < kColBins; ++cb) {
                 if (cb > 0 && rs_col_bound(cb - 1) >= lx) break;
-                // the last row bin has no upper bound: it takes the batch's bound
+                // the last bins have no upper bound: they take the batch's bounds
                 const int rbd = rb < kRowBins - 1 && rs_row_bound(rb) < rows_max ? rs_row_bound(rb) : rows_max;
-                const int cbd = rs_col_bound(cb) < lx ? rs_col_bound(cb) : lx;
-                if (cbd > rbd) continue;  // l < min(m, n): no block in this bin
+                if (cb > 0 && rs_col_bound(cb - 1) >= rbd) continue;  // l <= rows: no block in this bin
+                int cbd = cb < kColBins - 1 && rs_col_bound(cb) < lx ? rs_col_bound(cb) : lx;
+                if (cbd > rbd) cbd = rbd;
                 const int e = launch_qr<T>(batch, rbd, cbd, (void* const*)P, rows, ar.l_act, ldp, (void* const*)P,
                                            ldp, (void* const*)ar.pR, ar.ld_l, ar.info, st,
                                            bin_list(base + rb * kColBins + cb), r_t);
@@ -878,32 +886,40 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     const int mm_x = mx > nx ? mx : nx;
     if (kx > 0) {
-        // min(m, n) <= 64: A (A^T when m < n) = Q R with R written transposed, the SVD of
-        // R^T = U~ S V~^T in the register tier (R^T: the preconditioned form), then A = (Q V~) S U~^T:
-        // the Q side by the batched GEMM, U~ copied
+        // min(m, n) <= 128 (FP32; 64 in FP64): A (A^T when m < n) = Q R with R written transposed,
+        // the SVD of R^T = U~ S V~^T (R^T: the preconditioned form; register tier for k <= 64, shared
+        // tier above), then A = (Q V~) S U~^T: the Q side by the batched GEMM, U~ copied
         const ItemList qlist = listed(ar.list_reg, RL_REG);
-        const int kq = kx < 64 ? kx : 64;
+        const int kq = kx < RsCap<T>::smem ? kx : RsCap<T>::smem;
         for (int rb = 0; rb < kRowBins; ++rb) {  // QR of A (A^T): max(m, n) x k, by size bin
             if (rb > 0 && rs_row_bound(rb - 1) >= mm_x) break;
-            for (int cb = 0; cb < 2; ++cb) {
-                if (cb > 0 && kq <= 32) break;
-                const int rbd = rb < kRowBins - 1 && rs_row_bound(rb) < mm_x ? rs_row_bound(rb) : mm_x;
-                const int cbd = (32 << cb) < kq ? (32 << cb) : kq;
-                if (cbd > rbd) continue;
+            const int rbd = rb < kRowBins - 1 && rs_row_bound(rb) < mm_x ? rs_row_bound(rb) : mm_x;
+            for (int cb = 0; cb < kColBins; ++cb) {
+                if (cb > 0 && rs_col_bound(cb - 1) >= kq) break;
+                if (cb > 0 && rs_col_bound(cb - 1) >= rbd) continue;  // k <= rows
+                int cbd = cb < kColBins - 1 && rs_col_bound(cb) < kq ? rs_col_bound(cb) : kq;
+                if (cbd > rbd) cbd = rbd;
                 rc = launch_qr<T>(batch, rbd, cbd, A, ar.m_reg, ar.n_reg, LDA, (void* const*)ar.pQf, ar.ld_q,
-                                  (void* const*)ar.pR, ar.ld_l, ar.info, st, bin_list(RB_FQR + rb * 2 + cb), true,
-                                  ar.qtr);
+                                  (void* const*)ar.pR, ar.ld_l, ar.info, st, bin_list(RB_FQR + rb * kColBins + cb),
+                                  true, ar.qtr);
                 if (rc) return rc;
             }
         }
-        for (int cb = 0; cb < 2; ++cb) {  // SVD of R^T: k x k, by size bin
-            if (cb > 0 && kq <= 32) break;
-            const int kb = (32 << cb) < kq ? (32 << cb) : kq;
+        const int kr = kq < 64 ? kq : 64;
+        for (int cb = 0; cb < 2; ++cb) {  // SVD of R^T: k x k, register tier by size bin
+            if (cb > 0 && kr <= 32) break;
+            const int kb = (32 << cb) < kr ? (32 << cb) : kr;
             const ItemList wl = bin_list(RB_FSVD + cb);
             rc = small64 ? small_svd_fp64(batch, kb, ar.n_reg, wl, ar, st)
                          : launch_jacobi_reg<T>(batch, kb, kb, 0, (void* const*)ar.pR, ar.n_reg, ar.n_reg, ar.ld_l,
                                                 (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l,
                                                 (void* const*)ar.pVp, ar.ld_l, 0.0, 0, ar.info, nullptr, st, wl);
+            if (rc) return rc;
+        }
+        if (kq > 64) {  // 64 < k <= 128: the SVD of R^T in the shared tier
+            rc = launch_jacobi_smem<T>(batch, kq, kq, (void* const*)ar.pR, ar.n_reg, ar.n_reg, ar.ld_l,
+                                       (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
+                                       ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_smem, RL_SMEM), small64);
             if (rc) return rc;
         }
         rc = gemm<false, false, T>(batch, qlist, ar.pQf, ar.ld_q, ar.pVp, ar.ld_l, ar.pCf, ar.ld_q, ar.m_reg, ar.n_reg,
@@ -914,13 +930,6 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
             if (gc == 0) return BSVD_ERR_CUDA;
             rs_copy_kernel<T><<<gc, 256, 0, st>>>(qlist, ar);
             if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
-        }
-        if (kx > 64 && RsCap<T>::smem > 64) {  // 64 < min(m, n) <= 128 (FP32)
-            rc = launch_jacobi_smem<T>(batch, mm_x, kx < RsCap<T>::smem ? kx : RsCap<T>::smem, A, ar.m_smem,
-                                       ar.n_smem, LDA, (void* const*)ar.pS, (void* const*)ar.pUw, ar.ld_m,
-                                       (void* const*)ar.pVw, ar.ld_n, 0.0, 0, ar.info, nullptr, st,
-                                       listed(ar.list_smem, RL_SMEM), small64);
-            if (rc) return rc;
         }
         if (kx > RsCap<T>::smem) {
             // the block tier keeps its own list of live matrices: blocks not routed to it are 0 x 0

@@ -86,7 +86,7 @@ def test_launch_counts_follow_the_host_drivers():
     # 2 small-SVD bins, the shared tier, 2 GEMMs, estimate; full-rank path: 6 QR bins, 2 SVD bins,
     # GEMM, copy, shared tier
     assert bench.rsvd_launches(256, 256, 4) == (2 + 4 * (1 + 1 + 8 + (8 + 1 + 8 + 1) + (1 + 8) + 2 + 1 + 2 + 1) + 2
-                                               + (6 + 2 + 2 + 1)
+                                               + (8 + 2 + 1 + 2)  # full rank: 8 QR bins, 2 + 1 SVDs, GEMM, copy
                                                + (1 + 8 + 7 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1 + 8) + 1)
     # blocks up to 64 x 64: no shared or block tier
     assert bench.rsvd_launches(64, 64, 4) == 2 + 4 * (1 + 1 + 2 + (2 + 1 + 2 + 1) + (1 + 2) + 2 + 2 + 1) + 2 + (2 + 2 + 2) + 1

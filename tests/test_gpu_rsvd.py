@@ -194,7 +194,7 @@ def test_rsvd_fixed_rank_matches_the_oracle(bs, dtype, q):
     k = np.maximum(1, (rb.extra["rank_hint"] * rng.uniform(0.3, 1.1, rb.batch)).astype(np.int32))
     k[0] = kk[0]                         # k + p past min(m, n): the full SVD, k columns kept
     k[1] = max(1, kk[1] - 8)             # k + p = min(m, n) exactly: the full SVD
-    lcap = 128 if dtype == np.float32 else 64
+    lcap = 160 if dtype == np.float32 else 64  # the library's sample caps
     res = _run_mode(bs, rb, dtype, fixed_rank=k, power_iters=q)
     g = 1e-5 if dtype == np.float32 else 1e-12
     c = 256.0 if dtype == np.float32 else 64.0
@@ -209,6 +209,25 @@ def test_rsvd_fixed_rank_matches_the_oracle(bs, dtype, q):
         s_all = O.rsvd(a, SEED, b, l, q)[1] if l < kk[b] else O.svd(a)[1]
         assert vector_errors(u, Uo, So, dtype, c, s_all) <= 1.0, b
         assert vector_errors(v, Vo, So, dtype, c, s_all) <= 1.0, b
+
+
+def test_rsvd_samples_past_128_columns(bs):
+    """256 x 256 blocks with k + p in (128, 160] stay randomized (the FP32 sample cap is 160: the
+    small SVD of R_B^T runs in the shared tier with up to 160 columns); k + p = 161 takes the full
+    SVD.  Samples, rank and sigma against the oracle's fixed-rank RSVD at the same cap."""
+    rb = gen.rsvd_uneven_blocks(batch=6, sizes=(256,))
+    k = np.array([121, 125, 140, 150, 152, 153], np.int32)
+    res = _run_mode(bs, rb, np.float32, fixed_rank=k, power_iters=1)
+    for b in range(rb.batch):
+        a = rb.a64(b)
+        Uo, So, Vo, l = O.rsvd_rank(a, SEED, b, int(k[b]), 8, 1, 160)
+        assert l == (int(k[b]) + 8 if k[b] + 8 <= 160 else 256), (b, l)
+        assert int(res.samples_h[b]) == l and int(res.rank_h[b]) == int(k[b]), (b, int(res.samples_h[b]), l)
+        u, s, v = _unpack(res, b)
+        assert np.abs(s - So).max() <= 1e-5 * So[0], (b, np.abs(s - So).max() / So[0])
+        s_all = O.rsvd(a, SEED, b, l, 1)[1] if l < 256 else O.svd(a)[1]
+        assert vector_errors(u, Uo, So, np.float32, 256.0, s_all) <= 1.0, b
+        assert vector_errors(v, Vo, So, np.float32, 256.0, s_all) <= 1.0, b
 
 
 def _clear_rank(so, norm2, eps, est2, delta):
@@ -231,7 +250,7 @@ def test_rsvd_adaptive_decisions_match_the_oracle(bs, dtype):
     tol = rng.choice([1e-3, 1e-4, 1e-5], rb.batch)
     hint = (rb.extra["rank_hint"] // 2).astype(np.int32)
     hint[::5] = 0
-    lcap = 128 if dtype == np.float32 else 64
+    lcap = 160 if dtype == np.float32 else 64  # the library's sample caps
     res = _run_mode(bs, rb, dtype, rank_hint=hint, tol_per=tol, max_rounds=8)
     delta = (2e-6 if dtype == np.float32 else 1e-13)
     compared_rounds = compared_rank = 0
@@ -302,7 +321,7 @@ def test_rsvd_precision_options_match_the_oracle(bs, flags):
     assert np.all(res.info_h >= 0)
     for b in range(rb.batch):
         a = rb.a64(b)
-        Uo, So, Vo, l = O.rsvd_rank(a, SEED, b, int(k[b]), 8, 1, 128)
+        Uo, So, Vo, l = O.rsvd_rank(a, SEED, b, int(k[b]), 8, 1, 128 if flags & 2 else 160)
         assert int(res.samples_h[b]) == l and int(res.rank_h[b]) == min(int(k[b]), int(kk[b]))
         u, s, v = _unpack(res, b)
         tol = 1e-5 * So[0]

@@ -125,7 +125,7 @@ def test_hmatrix_mlp_full_workload(bs):
     info, samples = W.info.cpu().numpy(), W.samples.cpu().numpy()
     compared = 0
     for b in range(0, W.rb.batch, W.rb.batch // 48):
-        r = O.rsvd_adaptive(W.rb.a64(b), BENCH_SEED, b, int(hint[b]), EPS, 8, 1, 16, 128)
+        r = O.rsvd_adaptive(W.rb.a64(b), BENCH_SEED, b, int(hint[b]), EPS, 8, 1, 16, 160)
         thr = 0.25 * EPS * EPS * r["norm2"]
         if all(e >= 4 * thr or e <= thr / 4 for e in r["est2_round"]):
             compared += 1
