@@ -105,7 +105,9 @@ int batched_qr(int dtype, int batch, int max_m, int max_n,
  * Rotations use zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
  * c = 1 / sqrt(1 + t^2), s = c t on the 2 x 2 Gram matrix [[alpha, gamma], [gamma, beta]].
  * Tiers: the register tier holds min(m, n) <= 64 and max(m, n) <= 128 (F32) / 64 (F64); the shared
- * tier max(m, n) <= 256 and min(m, n) <= 128 (F32) / 64 (F64).  BSVD_TIER_AUTO uses the choice
+ * tier max(m, n) <= 256 and min(m, n) <= 160 (F32, while the matrix and V fit in 220 KiB of shared
+ * memory) / 64 (F64); FP32 matrices up to 128 x 128 in the shared tier keep their columns in
+ * registers and exchange one column per pair step through shared memory.  BSVD_TIER_AUTO uses the choice
  * recorded by bsvd_set_jacobi_choice for the size bin, else the register tier when it fits, else
  * the shared tier; larger shapes give BSVD_ERR_UNSUPPORTED.
  */
@@ -241,7 +243,8 @@ size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const 
  *   d_rank[b]      (nullable) FIXED-RANK MODE when > 0: k = d_rank[b]; l = k + oversample Gaussian
  *                  columns, `power_iters` power steps, one round, the first k columns of the rank-l
  *                  factorisation are returned (Algorithm 4 as stated).  When k + oversample reaches
- *                  min(m, n) or exceeds the sample cap (128 columns in FP32, 64 in FP64), the full
+ *                  min(m, n) or exceeds the sample cap (160 columns in FP32, 128 with
+ *                  BSVD_RSVD_TC_SAMPLING, 64 in FP64), the full
  *                  Jacobi SVD replaces the sampling and its first k columns are returned.  NULL, 0
  *                  or a negative value selects TOLERANCE MODE for that matrix.
  *   d_rank_hint[b] (nullable, tolerance mode) first rank guess k0: the first round draws
@@ -263,10 +266,9 @@ size_t batched_rsvd_workspace(int dtype, int batch, int max_m, int max_n, const 
  *   seed           Omega(r, c) of matrix b is Philox4x32-10 at counter (r/4, c, b, 0), key = seed,
  *                  through Box-Muller (the probes: counter (r/4, j, b, 1)).
  *   flags          0, or BSVD_RSVD_SMALL_FP64 (FP32 runs; ignored in FP64): the small SVDs -- of the
- *                  projected block's R_B^T and, for full-rank blocks with min(m, n) <= 64, of R^T
+ *                  projected block's R_B^T and, for full-rank blocks with min(m, n) <= 128, of R^T
  *                  -- run in FP64 when l <= 64 (operands widened, FP64 register tier, results
- *                  narrowed to FP32), and with FP64 rotation parameters in the shared tier above
- *                  (also for full-rank blocks with 64 < min(m, n) <= 128).
+ *                  narrowed to FP32), and with FP64 rotation parameters in the shared tier above.
  *                  | BSVD_RSVD_TC_SAMPLING (FP32 runs; ignored in FP64): the sample A Omega is a
  *                  tcgen05 product of kind::tf32 (the FP32 operands read with a 10-bit mantissa, FP32
  *                  accumulation), the 8 probe columns stay FP32 products; the power step and the

@@ -230,6 +230,11 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
                        int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl, bool p64)
 {
+    if (sizeof(T) == 4) {  // FP32 up to 128 x 128: the columns in registers (jacobi_rx.cu)
+        const int rc = launch_jacobi_rx(batch, max_m, max_n, A, M, N, LDA, S, U, LDU, V, LDV, tol, max_sweeps, info,
+                                        rot, st, wl, p64);
+        if (rc != BSVD_ERR_UNSUPPORTED) return rc;
+    }
     const int max_mm = max_m > max_n ? max_m : max_n;
     const int max_nn = max_m > max_n ? max_n : max_m;
     const int max_np = (max_nn + 1) & ~1;

@@ -26,6 +26,10 @@ int launch_jacobi_smem(int batch, int max_m, int max_n, void* const* A, const in
                        void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
                        int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl = all_items(),
                        bool p64 = false);  // p64: FP32 data, FP64 rotation parameters
+// the register-resident form of the shared tier (FP32, max(m, n) <= 128); BSVD_ERR_UNSUPPORTED otherwise
+int launch_jacobi_rx(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                     void* const* S, void* const* U, const int* LDU, void* const* V, const int* LDV, double tol,
+                     int max_sweeps, int* info, long long* rot, cudaStream_t st, ItemList wl, bool p64);
 template <typename T>
 size_t block_jacobi_workspace(int batch, int max_m, int max_n, int bw, int method);  // method: base | QR flag
 template <typename T>
