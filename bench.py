@@ -192,7 +192,7 @@ def rsvd_launches(max_m, max_n, rounds):
     sampling GEMM, the QRs of the sample, the power step's two products and two QRs, the projection
     and its QR (each QR once per size bin the bounds can populate: rows in (0, 64], (64, 128],
     (128, ...), columns in (0, 32], (32, 64], (64, ...), no bin with more columns than rows), the
-    small SVD per column bin (register tier; plus the shared tier when samples may pass 64), two
+    small SVD per column bin (register tier; the shared tier for samples in (64, 128] and above), two
     GEMMs for U and V and the estimate; then the fallback and arrays kernels, the full-rank QR path
     (QR per row bin and column bin up to 128, the SVD of R^T per register-tier column bin and in the
     shared tier when min > 64, GEMM, copy), the block tier on R^T of a blocked QR (min > 128) and
@@ -216,7 +216,7 @@ def rsvd_launches(max_m, max_n, rounds):
 
     qy, qz = bins(max_m, lx, 3), bins(max_n, lx, 3)
     small = 1 + (1 if lx > 32 else 0)
-    per_round = 1 + 1 + qy + (qz + 1 + qy + 1) + (1 + qz) + small + (1 if lx > 64 else 0) + 2 + 1
+    per_round = 1 + 1 + qy + (qz + 1 + qy + 1) + (1 + qz) + small + (1 if lx > 64 else 0) + (1 if lx > 128 else 0) + 2 + 1
     n = 2 + rounds * per_round + 2
     if kx > 0:
         kq = min(kx, 128)

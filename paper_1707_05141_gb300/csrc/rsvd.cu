@@ -135,7 +135,8 @@ constexpr int RB_QZ = RB_QY + kRowBins * kColBins;      // QR of Z and B^T (n x 
 constexpr int RB_LREG = RB_QZ + kRowBins * kColBins;    // small SVD, register tier (l <= 32, <= 64)
 constexpr int RB_FQR = RB_LREG + 2;                     // full-rank QR path: QR of A (max(m,n) x k), 3 x 3 bins
 constexpr int RB_FSVD = RB_FQR + kRowBins * kColBins;   // ... and the SVD of R^T, register tier (k <= 32, <= 64)
-constexpr int RB_END = RB_FSVD + 2;
+constexpr int RB_LSM = RB_FSVD + 2;                     // small SVD, shared tier (l <= 128, above)
+constexpr int RB_END = RB_LSM + 2;
 constexpr int kBins = RB_END - RL_COUNT;
 constexpr int kCounters = 64;                           // list lengths and flags (ints)
 constexpr int kTimeoutSlot = kCounters - 1;
@@ -464,6 +465,7 @@ __global__ void rs_arrays_kernel(int batch, T* scratch, RsArrays<T> ar, int fina
             bin_push(RB_LREG + (l <= 32 ? 0 : 1));
         } else {
             ar.list_lsmem[atomicAdd(&ar.cnt[RL_LSMEM], 1)] = b;
+            bin_push(RB_LSM + (l <= 128 ? 0 : 1));
         }
     }
     if (reg) {
@@ -859,13 +861,15 @@ int launch_rsvd(int batch, int max_m, int max_n, void* const* A, const int* M, c
                                                 (void* const*)ar.pVp, ar.ld_l, 0.0, 0, ar.info, nullptr, st, wl);
         }
         if (rc) break;
-        if (lx > 64) {
-            rc = launch_jacobi_smem<T>(batch, lx, lx, (void* const*)ar.pR, ar.l_smem, ar.l_smem, ar.ld_l,
+        // l in (64, 128] (FP32: the columns-in-registers form of the shared tier) and above 128
+        for (int cb = 0; cb < 2 && rc == BSVD_SUCCESS; ++cb) {
+            if (lx <= (cb ? 128 : 64)) break;
+            const int lb = cb == 0 && lx > 128 ? 128 : lx;
+            rc = launch_jacobi_smem<T>(batch, lb, lb, (void* const*)ar.pR, ar.l_smem, ar.l_smem, ar.ld_l,
                                        (void* const*)ar.pS, (void* const*)ar.pUp, ar.ld_l, (void* const*)ar.pVp,
-                                       ar.ld_l, 0.0, 0, ar.info, nullptr, st, listed(ar.list_lsmem, RL_LSMEM),
-                                       small64);
-            if (rc) break;
+                                       ar.ld_l, 0.0, 0, ar.info, nullptr, st, bin_list(RB_LSM + cb), small64);
         }
+        if (rc) break;
         // U = Q U_R, V = Q_B V_R
         rc = gemm<false, false, T>(batch, act, ar.pY, ar.ld_m, ar.pUp, ar.ld_l, ar.pUw, ar.ld_m, ar.m_act, ar.l_act,
                                    ar.l_act, nullptr, seed, st);

@@ -83,9 +83,9 @@ def test_launch_counts_follow_the_host_drivers():
     # the block tier on R^T of a blocked QR: setup, 8 panels, 7 trailing updates, R^T, the block
     # Jacobi, the zero fill, 8 block-reflector applications
     # per round: arrays, sample, 8 QR bins of Y, power step (8 + GEMM + 8 + GEMM), projection (GEMM + 8),
-    # 2 small-SVD bins, the shared tier, 2 GEMMs, estimate; full-rank path: 6 QR bins, 2 SVD bins,
-    # GEMM, copy, shared tier
-    assert bench.rsvd_launches(256, 256, 4) == (2 + 4 * (1 + 1 + 8 + (8 + 1 + 8 + 1) + (1 + 8) + 2 + 1 + 2 + 1) + 2
+    # 2 small-SVD bins, 2 shared-tier bins, 2 GEMMs, estimate; then the full-rank path and the block
+    # tier
+    assert bench.rsvd_launches(256, 256, 4) == (2 + 4 * (1 + 1 + 8 + (8 + 1 + 8 + 1) + (1 + 8) + 2 + 2 + 2 + 1) + 2
                                                + (8 + 2 + 1 + 2)  # full rank: 8 QR bins, 2 + 1 SVDs, GEMM, copy
                                                + (1 + 8 + 7 + 1 + (1 + 20 * (7 * 4 + 1) + 1) + 1 + 8) + 1)
     # blocks up to 64 x 64: no shared or block tier

@@ -50,3 +50,32 @@ def test_round_robin_meets_every_pair_once_per_sweep(tmp_path):
     assert r.returncode == 0, r.stderr
     bad, checked = map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split())
     assert checked == 129 and bad == 0
+
+
+def _odd_even_exchange_sweeps(ns, sweeps=2):
+    """The slot exchange of the columns-in-registers shared tier (csrc/jacobi_rx.cu) and of the
+    register tier, restated: slot s holds columns (L, R); even steps rotate every slot, odd steps all
+    but the wrap slot ns - 1; after an even step every slot takes its right neighbour's R, after an
+    odd step every slot takes its left neighbour's L, except that the wrap slot hands over its R and
+    keeps its L as the new R.  Yields the pairs met in each sweep of 2 ns steps."""
+    L = [2 * s for s in range(ns)]
+    R = [2 * s + 1 for s in range(ns)]
+    for _ in range(sweeps):
+        met = []
+        for st in range(2 * ns):
+            odd = st & 1
+            met += [frozenset((L[s], R[s])) for s in range(ns) if not (odd and s == ns - 1)]
+            if not odd:
+                R = [R[(s + 1) % ns] for s in range(ns)]
+            else:
+                sent = [R[s] if s == ns - 1 else L[s] for s in range(ns)]
+                R = [L[s] if s == ns - 1 else R[s] for s in range(ns)]
+                L = [sent[(s - 1) % ns] for s in range(ns)]
+        yield met
+
+
+@pytest.mark.parametrize("ns", list(range(1, 65)))
+def test_odd_even_exchange_meets_every_pair_once_per_sweep(ns):
+    every = {frozenset((i, j)) for i in range(2 * ns) for j in range(i + 1, 2 * ns)}
+    for met in _odd_even_exchange_sweeps(ns):
+        assert len(met) == len(set(met)) and set(met) == every
