@@ -85,6 +85,12 @@ def measured_hbm_gbs() -> float:
 # digest of the kernel's sources at capture time: a changed kernel has no entry and reports null
 # traffic, not stale counters.  profiles/ holds the capture summaries.
 TRAFFIC = {
+    # jacobi_reg_kernel tier 0xa01, 10 000 64x64 matrices: 164.61 MB read + 277.57 MB written, per
+    # 20 000-matrix launch (profiles/jacobi_reg_qr_svd64_qr128.md)
+    "jacobi_reg:657c5a9dca399a6b": 2 * (164.607744e6 + 277.571072e6),
+    # qr_warp_kernel<float, 128, 1>, 10 000 128x32 matrices: 164.38 MB read + 147.50 MB written, per
+    # 20 000-matrix launch
+    "qr:55170984508f3f39": 2 * (164.379392e6 + 147.502336e6),
 }
 
 
@@ -362,9 +368,11 @@ class SvdQr64:
             qbytes = self.nq * (128 * 32 * 2 + 32 * 32) * 4
             gbs = qbytes / (qr_ms * 1e-3) / 1e9
             peak = measured_hbm_gbs()
+            qtraffic = TRAFFIC.get("qr:" + kernel_digest("qr.cu"))
             detail["qr"] = {"kernel": "qr_warp_kernel<float, 128, 1>", "ms_per_launch": qr_ms,
                             "bytes_per_launch": qbytes, "achieved_gbs": gbs, "peak_gbs": peak,
-                            "frac": gbs / peak, "bound": "hbm", "peak_note": "measured copy bandwidth"}
+                            "frac": gbs / peak, "bound": "hbm", "peak_note": "measured copy bandwidth",
+                            "traffic": qtraffic * self.nq / 20000 if qtraffic is not None else None}
             self.qr_ev = []
         return roof, detail
 
