@@ -88,9 +88,6 @@ TRAFFIC = {
     # jacobi_reg_kernel tier 0xa01, 10 000 64x64 matrices: 164.61 MB read + 277.57 MB written, per
     # 20 000-matrix launch (profiles/jacobi_reg_qr_svd64_qr128.md)
     "jacobi_reg:657c5a9dca399a6b": 2 * (164.607744e6 + 277.571072e6),
-    # qr_warp_kernel<float, 128, 1>, 10 000 128x32 matrices: 164.38 MB read + 147.50 MB written, per
-    # 20 000-matrix launch
-    "qr:55170984508f3f39": 2 * (164.379392e6 + 147.502336e6),
 }
 
 

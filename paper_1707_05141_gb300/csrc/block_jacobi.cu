@@ -562,8 +562,13 @@ constexpr uint32_t kTcLbo = 128;                                // K-adjacent co
 constexpr uint32_t kTcGramSbo = (kTcGramKc / 4) * 128;          // 1024 B between 8-row groups
 constexpr uint32_t kTcGramStage = 128u * kTcGramKc * 4u;        // 16 KB: 64 hi + 64 lo rows x KC
 constexpr int kTcGramStages = 3;
-// 3 stages (48 KB) + alignment: at most four CTAs fit an SM, so 4 x 128 TMEM columns <= 512
-constexpr size_t kTcGramSmem = kTcGramStages * kTcGramStage + 1024 + 64;
+// raw FP32 chunks (64 columns x KC rows, 8 KB each) copied in asynchronously two chunks ahead of
+// the split; three slots, so the copy into a slot never overtakes the split that last read it
+constexpr uint32_t kTcRawStage = 64u * kTcGramKc * 4u;
+constexpr int kTcRawStages = 3;
+// 3 operand stages (48 KB) + 3 raw stages (24 KB) + alignment: three CTAs fit an SM (3 x 128 TMEM
+// columns <= 512)
+constexpr size_t kTcGramSmem = kTcGramStages * kTcGramStage + kTcRawStages * kTcRawStage + 1024 + 64;
 
 // next claimed position, or "none" once any tensor-core wait of the call has given up (uniform
 // over the CTA: thread 0 decides, the barrier publishes)
@@ -639,38 +644,50 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
     const int nch = (mm + kTcGramKc - 1) / kTcGramKc;
     constexpr uint32_t idesc = tc::idesc_tf32(128, 128);
     constexpr int kUnits = (K2 * kTcGramKc / 4) / 128;  // float4 units per thread per chunk
+    unsigned char* raw = sm + kTcGramStages * kTcGramStage;
     // unit j of this thread: column i, 4-row group g (consecutive threads take consecutive columns,
-    // so eight threads write one 128-byte core matrix)
-    auto load_unit = [&](int j, int c) {
-        const int u = tid + 128 * j;
-        const int i = u & (K2 - 1), g = u / K2;
-        const int col = bj_col(bi, bj, bw, i, nn);
-        const int r = c * kTcGramKc + 4 * g;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col >= 0) {
-            const float* src = W + (size_t)col * ldw + r;
-            if (vec && r + 3 < mm) {
-                v = *reinterpret_cast<const float4*>(src);
+    // so eight threads write one 128-byte core matrix).  Chunk c's units are copied asynchronously
+    // into raw slot c % 3 at unit offset u * 16 (rows past mm and padding columns zero-filled); the
+    // thread that copies a unit is the thread that later splits it, so its own wait suffices.
+    auto issue_chunk = [&](int c) {
+        unsigned char* slot = raw + (c % kTcRawStages) * kTcRawStage;
+#pragma unroll
+        for (int j = 0; j < kUnits; ++j) {
+            const int u = tid + 128 * j;
+            const int i = u & (K2 - 1), g = u / K2;
+            const int col = bj_col(bi, bj, bw, i, nn);
+            const int r = c * kTcGramKc + 4 * g;
+            const int left = col >= 0 ? (mm - r < 0 ? 0 : (mm - r > 4 ? 4 : mm - r)) : 0;
+            const float* src = col >= 0 && left > 0 ? W + (size_t)col * ldw + r : W;
+            const uint32_t dst = tc::smem_u32(slot + u * 16);
+            if (vec) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                             "r"(4 * left)
+                             : "memory");
             } else {
-                if (r + 0 < mm) v.x = src[0];
-                if (r + 1 < mm) v.y = src[1];
-                if (r + 2 < mm) v.z = src[2];
-                if (r + 3 < mm) v.w = src[3];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst + 4 * e),
+                                 "l"(e < left ? src + e : W), "r"(e < left ? 4 : 0)
+                                 : "memory");
             }
         }
-        return v;
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
-    float4 cur[kUnits], nxt[kUnits];
-#pragma unroll
-    for (int j = 0; j < kUnits; ++j) cur[j] = load_unit(j, 0);
+    issue_chunk(0);
+    if (nch > 1) issue_chunk(1);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
         const int s = c % kTcGramStages;
         unsigned char* stage = sm + s * kTcGramStage;
-        // the next chunk's loads are in flight while this one is split, stored and multiplied
-        if (c + 1 < nch) {
-#pragma unroll
-            for (int j = 0; j < kUnits; ++j) nxt[j] = load_unit(j, c + 1);
+        // two chunks ahead: the copy into slot (c + 2) % 3 follows the split of chunk c - 1 that read it
+        if (c + 2 < nch) {
+            issue_chunk(c + 2);
+            asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+        } else if (c + 1 < nch) {
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         if (c >= kTcGramStages) {  // the MMAs of chunk c - 3 read this stage
             // after a failure: no more waits.  `never` (failure-path test only) is a barrier nothing
@@ -678,13 +695,15 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
             if (ok) ok = never ? tc::mbar_wait(never, 0u, 1000000ull) : tc::mbar_wait(&bars[s], (phase >> s) & 1u);
             phase ^= 1u << s;
         }
+        const unsigned char* rs = raw + (c % kTcRawStages) * kTcRawStage;
 #pragma unroll
         for (int j = 0; j < kUnits; ++j) {
             const int u = tid + 128 * j;
             const int i = u & (K2 - 1), g = u / K2;
+            const float4 v = *reinterpret_cast<const float4*>(rs + u * 16);
             // hi to operand rows 0..63, lo to rows 64..127 of the same stage
             tc_split_store(stage + tc::kmajor_offset(i, 4 * g, kTcLbo, kTcGramSbo),
-                           stage + tc::kmajor_offset(K2 + i, 4 * g, kTcLbo, kTcGramSbo), 0u, cur[j]);
+                           stage + tc::kmajor_offset(K2 + i, 4 * g, kTcLbo, kTcGramSbo), 0u, v);
         }
         tc::fence_smem_to_async();
         __syncthreads();
@@ -699,10 +718,6 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
             tc::mma_commit(&bars[s]);
         }
         used |= 1u << s;  // stages that have received a commit (for the failure path's drain)
-        if (c + 1 < nch) {
-#pragma unroll
-            for (int j = 0; j < kUnits; ++j) cur[j] = nxt[j];
-        }
     }
     // drain: the last (up to three) chunks' commits, one per barrier
     for (int c = nch > kTcGramStages ? nch - kTcGramStages : 0; c < nch; ++c) {

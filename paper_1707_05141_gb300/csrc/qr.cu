@@ -485,10 +485,15 @@ int launch_qr(int batch, int max_m, int max_n, void* const* A, const int* M, con
         return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
     }
     const size_t smem = ((size_t)(max_m | 1) * max_n + max_n) * sizeof(T);
-    const int threads = max_n <= 32 ? 128 : 256;
+    // wide panels run one CTA per SM (the matrix fills shared memory): 16 warps hide the latency of
+    // the per-column reductions better than 8
     // rows per lane of the register Q formation from the batch's row bound
     auto kern = max_m <= 32 ? qr_kernel<T, 1> : (max_m <= 64 ? qr_kernel<T, 2> : (max_m <= 128 ? qr_kernel<T, 4>
                                                                                              : qr_kernel<T, 8>));
+    int threads = max_n <= 32 ? 128 : (max_n <= 64 ? 256 : 512);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return BSVD_ERR_CUDA;
+    while (threads > fa.maxThreadsPerBlock && threads > 128) threads /= 2;  // the kernel's registers allow fewer
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BSVD_ERR_CUDA;
