@@ -88,6 +88,9 @@ TRAFFIC = {
     # jacobi_reg_kernel tier 0xa01, 10 000 64x64 matrices: 164.61 MB read + 277.57 MB written, per
     # 20 000-matrix launch (profiles/jacobi_reg_qr_svd64_qr128.md)
     "jacobi_reg:657c5a9dca399a6b": 2 * (164.607744e6 + 277.571072e6),
+    # qr_warp_kernel<float, 128, 1>, 10 000 128x32 matrices: 164.69 MB read + 146.98 MB written, per
+    # 20 000-matrix launch
+    "qr:e67df0692f0a080a": 2 * (164.692224e6 + 146.980608e6),
 }
 
 
@@ -1198,7 +1201,7 @@ def main():
     ap.add_argument("--qr-batch", type=int, default=20000)
     ap.add_argument("--block-batch", type=int, default=500, help="block512: matrices per GPU")
     ap.add_argument("--rsvd-batch", type=int, default=16384, help="rsvd_uneven: blocks per GPU")
-    ap.add_argument("--e2e-chunks", type=int, default=4,
+    ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="chunks of the host entries' end-to-end run whose copies overlap the computation")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

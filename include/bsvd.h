@@ -404,12 +404,14 @@ int bsvd_h2_truncate(int dtype, int depth, int k, int max_leaf_m, void* const* d
  * batches already live on the GPU).  Matrix b of the batch is column-major at element b * m * n of
  * hA (leading dimension m); outputs are packed the same way: S k values (k = min(m, n)), U m x k,
  * V n x k, Q m x n, R n x n per matrix, info one int.  The batch is cut into `chunks` chunks whose
- * host -> device copy, computation and device -> host copy overlap (two library-owned copy streams,
- * created once per device; `stream` computes and, on return, is ordered after the last copy:
- * synchronising it completes the call).  Host buffers must stay valid until then and should be
- * page-locked for the copies to overlap.  The device copies of the whole batch live in `workspace`
- * (at least *_workspace(...) bytes, else BSVD_ERR_WORKSPACE); nothing is allocated.  Calls on one
- * device share the copy streams.  hU, hV, hQ, hR, h_info may be NULL (not computed / not copied).
+ * host -> device copy, computation and device -> host copy overlap (library-owned streams, created
+ * once per device: two for the copies, and two per call for the computation, consecutive chunks on
+ * different ones; every one of them starts after the work already enqueued on `stream`, and on
+ * return `stream` is ordered after the last copy: synchronising it completes the call).  Host
+ * buffers must stay valid until then and should be page-locked for the copies to overlap.  The
+ * device copies of the whole batch live in `workspace` (at least *_workspace(...) bytes, else
+ * BSVD_ERR_WORKSPACE); nothing is allocated.  Calls on one device share the copy streams and take
+ * turns on four compute streams.  hU, hV, hQ, hR, h_info may be NULL (not computed / not copied).
  */
 size_t bsvd_host_svd_workspace(int dtype, int batch, int m, int n);
 int bsvd_host_svd(int dtype, int batch, int m, int n, const void* hA, void* hS, void* hU, void* hV, int* h_info,

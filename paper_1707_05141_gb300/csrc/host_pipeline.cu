@@ -3,12 +3,14 @@
 //
 // The paper's routines take batches already resident on the GPU; a caller whose matrices live in
 // host memory would otherwise copy everything in, compute, and copy everything out in three serial
-// phases.  Here the batch is cut into chunks: chunk c is copied in on one stream, computed on the
-// caller's stream and copied out on a third, so that the transfer of chunk c + 1 and the read-back
-// of chunk c - 1 run while chunk c is computed.  The device copies of the whole batch live in the
-// caller's workspace; the two copy streams and the events are the library's own (created once per
-// device and reused), and the caller's stream waits for the last read-back, so synchronising it
-// covers the whole call.  Host buffers should be page-locked for the copies to overlap.
+// phases.  Here the batch is cut into chunks: chunk c is copied in on one stream, computed on a
+// compute stream and copied out on another, so that the transfer of chunk c + 1 and the read-back
+// of chunk c - 1 run while chunk c is computed; consecutive chunks are computed on two different
+// streams, so one chunk's last wave overlaps the next chunk's first.  The device copies of the whole
+// batch live in the caller's workspace; the streams and the events are the library's own (created
+// once per device and reused), every stream starts after the caller's earlier work, and the
+// caller's stream waits for the last read-back, so synchronising it covers the whole call.  Host
+// buffers should be page-locked for the copies to overlap.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -22,6 +24,8 @@ constexpr int kMaxDevices = 64;
 
 struct HostPipe {
     cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaStream_t s_comp[4] = {nullptr, nullptr, nullptr, nullptr};  // compute streams (two per call, in turn)
+    int next_pair = 0;
     std::vector<cudaEvent_t> ev;  // 2 per chunk (copied in, computed) + start + done
 };
 std::mutex g_pipe_mu;
@@ -35,6 +39,9 @@ HostPipe* host_pipe(int nev)
     HostPipe& p = g_pipe[dev];
     if (!p.s_in && cudaStreamCreateWithFlags(&p.s_in, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     if (!p.s_out && cudaStreamCreateWithFlags(&p.s_out, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    for (int i = 0; i < 4; ++i)
+        if (!p.s_comp[i] && cudaStreamCreateWithFlags(&p.s_comp[i], cudaStreamNonBlocking) != cudaSuccess)
+            return nullptr;
     while ((int)p.ev.size() < nev) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
@@ -85,8 +92,11 @@ __global__ void host_setup_kernel(int batch, int kinds, unsigned char* ws, HostL
     for (int i = 0; i < 8; ++i) q[(size_t)i * batch + b] = v[i];
 }
 
-// one chunked host -> device -> host pass; `compute(c0, c1)` enqueues the batched call for matrices
-// c0 .. c1 - 1 on `st`; kinds [0, nin) are copied in, [nin, kinds) copied out (plus the info array)
+// one chunked host -> device -> host pass; `compute(c0, c1, s)` enqueues the batched call for
+// matrices c0 .. c1 - 1 on stream s; kinds [0, nin) are copied in, [nin, kinds) copied out (plus the
+// info array).  Chunks alternate between two of the library's compute streams, so the last wave of
+// one chunk's kernel shares the GPU with the first waves of the next instead of leaving SMs idle;
+// the next call of the library takes the other two streams.
 template <typename F>
 int host_run(int batch, int chunks, const HostLayout& L, size_t es, unsigned char* ws, const void* const* host,
              int nin, int* h_info, int* d_info, cudaStream_t st, F compute)
@@ -103,6 +113,10 @@ int host_run(int batch, int chunks, const HostLayout& L, size_t es, unsigned cha
     if (cudaEventRecord(ev_start, st) != cudaSuccess) return BSVD_ERR_CUDA;
     if (cudaStreamWaitEvent(P->s_in, ev_start, 0) != cudaSuccess) return BSVD_ERR_CUDA;
     if (cudaStreamWaitEvent(P->s_out, ev_start, 0) != cudaSuccess) return BSVD_ERR_CUDA;
+    cudaStream_t sc[2] = {P->s_comp[P->next_pair], P->s_comp[P->next_pair + 1]};
+    P->next_pair ^= 2;
+    for (int i = 0; i < 2; ++i)
+        if (cudaStreamWaitEvent(sc[i], ev_start, 0) != cudaSuccess) return BSVD_ERR_CUDA;
     for (int c = 0; c < nch; ++c) {
         const int c0 = c * step, c1 = c0 + step < batch ? c0 + step : batch;
         const size_t nb = (size_t)(c1 - c0);
@@ -114,10 +128,11 @@ int host_run(int batch, int chunks, const HostLayout& L, size_t es, unsigned cha
         }
         cudaEvent_t ev_in = P->ev[2 * c], ev_comp = P->ev[2 * c + 1];
         if (cudaEventRecord(ev_in, P->s_in) != cudaSuccess) return BSVD_ERR_CUDA;
-        if (cudaStreamWaitEvent(st, ev_in, 0) != cudaSuccess) return BSVD_ERR_CUDA;
-        const int rc = compute(c0, c1);
+        cudaStream_t cs = sc[c & 1];
+        if (cudaStreamWaitEvent(cs, ev_in, 0) != cudaSuccess) return BSVD_ERR_CUDA;
+        const int rc = compute(c0, c1, cs);
         if (rc != BSVD_SUCCESS) return rc;
-        if (cudaEventRecord(ev_comp, st) != cudaSuccess) return BSVD_ERR_CUDA;
+        if (cudaEventRecord(ev_comp, cs) != cudaSuccess) return BSVD_ERR_CUDA;
         if (cudaStreamWaitEvent(P->s_out, ev_comp, 0) != cudaSuccess) return BSVD_ERR_CUDA;
         for (int i = nin; i < L.kinds; ++i) {
             if (!host[i]) continue;
@@ -130,7 +145,8 @@ int host_run(int batch, int chunks, const HostLayout& L, size_t es, unsigned cha
                           cudaSuccess)
             return BSVD_ERR_CUDA;
     }
-    // the caller's stream completes only after the last read-back
+    // the caller's stream completes only after the last read-back (which follows every chunk's
+    // computation)
     if (cudaEventRecord(ev_done, P->s_out) != cudaSuccess) return BSVD_ERR_CUDA;
     if (cudaStreamWaitEvent(st, ev_done, 0) != cudaSuccess) return BSVD_ERR_CUDA;
     return BSVD_SUCCESS;
@@ -188,13 +204,13 @@ int bsvd_host_svd(int dtype, int batch, int m, int n, const void* hA, void* hS, 
     const void* host[4] = {hA, hS, hU, hV};
     HostLayout Lc = L;
     Lc.kinds = 4;
-    return host_run(batch, chunks, Lc, es, ws, host, 1, h_info, d_info, st, [&](int c0, int c1) {
+    return host_run(batch, chunks, Lc, es, ws, host, 1, h_info, d_info, st, [&](int c0, int c1, cudaStream_t cs) {
         const int nb = c1 - c0;
         return batched_svd_jacobi(dtype, nb, m, n, p + c0, q + c0, q + (size_t)batch + c0,
                                   q + 2 * (size_t)batch + c0, p + (size_t)batch + c0,
                                   hU ? p + 2 * (size_t)batch + c0 : nullptr, q + 5 * (size_t)batch + c0,
                                   hV ? p + 3 * (size_t)batch + c0 : nullptr, q + 6 * (size_t)batch + c0, 0.0, 0,
-                                  BSVD_TIER_AUTO, d_info + c0, nullptr, st);
+                                  BSVD_TIER_AUTO, d_info + c0, nullptr, cs);
     });
 }
 
@@ -228,11 +244,11 @@ int bsvd_host_qr(int dtype, int batch, int m, int n, const void* hA, void* hQ, v
     const void* host[3] = {hA, hQ, hR};
     HostLayout Lc = L;
     Lc.kinds = 3;
-    return host_run(batch, chunks, Lc, es, ws, host, 1, h_info, d_info, st, [&](int c0, int c1) {
+    return host_run(batch, chunks, Lc, es, ws, host, 1, h_info, d_info, st, [&](int c0, int c1, cudaStream_t cs) {
         const int nb = c1 - c0;
         return batched_qr(dtype, nb, m, n, p + c0, q + c0, q + (size_t)batch + c0, q + 2 * (size_t)batch + c0,
                           hQ ? p + (size_t)batch + c0 : nullptr, q + 3 * (size_t)batch + c0,
-                          hR ? p + 2 * (size_t)batch + c0 : nullptr, q + 4 * (size_t)batch + c0, d_info + c0, st);
+                          hR ? p + 2 * (size_t)batch + c0 : nullptr, q + 4 * (size_t)batch + c0, d_info + c0, cs);
     });
 }
 

@@ -79,24 +79,37 @@ __device__ __forceinline__ void house_factor_smem_rows(T* S, int ld, T* diag, in
             v[t] = r < m ? col[r] : T(0);
         }
         const int first = i + 1 + ((warp - (i + 1) % nwarps) + nwarps) % nwarps;
-        for (int j = first; j < n; j += nwarps) {
+        // two of the warp's columns at a time: their reductions are independent, so their shuffle
+        // latencies overlap (the second is a column past n when the warp has an odd count left)
+        for (int j = first; j < n; j += 2 * nwarps) {
+            const int j2 = j + nwarps;
+            const bool two = j2 < n;
             T* cj = S + (size_t)j * ld;
-            T x[RPL];
+            T* cj2 = S + (size_t)(two ? j2 : j) * ld;
+            T x[RPL], y[RPL];
             T w0 = T(0), w1 = T(0);
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int r = i + lane + 32 * t;
                 x[t] = r < m ? cj[r] : T(0);
-                if (t & 1)
-                    w1 = fma(v[t], x[t], w1);
-                else
-                    w0 = fma(v[t], x[t], w0);
+                y[t] = r < m && two ? cj2[r] : T(0);
+                w0 = fma(v[t], x[t], w0);
+                w1 = fma(v[t], y[t], w1);
             }
-            const T w = T(2) * warp_sum(w0 + w1);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                w0 += __shfl_xor_sync(0xffffffffu, w0, o);
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+            }
+            w0 *= T(2);
+            w1 *= T(2);
 #pragma unroll
             for (int t = 0; t < RPL; ++t) {
                 const int r = i + lane + 32 * t;
-                if (r < m) cj[r] = fma(-w, v[t], x[t]);
+                if (r < m) {
+                    cj[r] = fma(-w0, v[t], x[t]);
+                    if (two) cj2[r] = fma(-w1, v[t], y[t]);
+                }
             }
             if (j == i + 1) {
                 __syncwarp();

@@ -84,31 +84,59 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         // ---- Q = H_0 ... H_{n-1} [I; 0] ----
         if (Q && m <= 32 * QROWS) {
             // column j of Q is H_0 H_1 ... H_j e_j (H_i e_j = e_j for i > j): every column on its own,
-            // one warp per column, in registers (rows lane + 32 t), with no barrier
+            // in registers (rows lane + 32 t), with no barrier.  A warp carries QC columns
+            // (j, j + nwarps, ...) at once: each reflector is read once for all of them, and their
+            // QC shuffle reductions are independent, so their latencies overlap.
+            constexpr int QC = 4;
             T* q_out = Q[b];
-            for (int j = warp; j < n; j += nwarps) {
-                T q[QROWS];
+            for (int j0 = warp; j0 < n; j0 += nwarps * QC) {
+                T q[QC][QROWS];
+                int jc[QC];
 #pragma unroll
-                for (int t = 0; t < QROWS; ++t) q[t] = (lane + 32 * t == j) ? T(1) : T(0);
-                for (int i = j; i >= 0; --i) {
+                for (int c = 0; c < QC; ++c) {
+                    jc[c] = j0 + c * nwarps;
+#pragma unroll
+                    for (int t = 0; t < QROWS; ++t) q[c][t] = (lane + 32 * t == jc[c]) ? T(1) : T(0);
+                }
+                int jtop = jc[0];
+#pragma unroll
+                for (int c = 1; c < QC; ++c)
+                    if (jc[c] < n) jtop = jc[c];
+                for (int i = jtop; i >= 0; --i) {
                     const T* v = S + (size_t)i * ld;
-                    T w = T(0);
+                    T vr[QROWS];
 #pragma unroll
                     for (int t = 0; t < QROWS; ++t) {
                         const int r = lane + 32 * t;
-                        if (r >= i && r < m) w = fma(v[r], q[t], w);
+                        vr[t] = (r >= i && r < m) ? v[r] : T(0);
                     }
-                    w = T(2) * warp_sum(w);
+                    T w[QC];
 #pragma unroll
-                    for (int t = 0; t < QROWS; ++t) {
-                        const int r = lane + 32 * t;
-                        if (r >= i && r < m) q[t] = fma(-w, v[r], q[t]);
+                    for (int c = 0; c < QC; ++c) {
+                        w[c] = T(0);
+#pragma unroll
+                        for (int t = 0; t < QROWS; ++t) w[c] = fma(vr[t], q[c][t], w[c]);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int c = 0; c < QC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+#pragma unroll
+                    for (int c = 0; c < QC; ++c) {
+                        // H_i leaves column j unchanged for i > j (and columns past n do not exist)
+                        const T wc = (i <= jc[c] && jc[c] < n) ? T(-2) * w[c] : T(0);
+#pragma unroll
+                        for (int t = 0; t < QROWS; ++t) q[c][t] = fma(wc, vr[t], q[c][t]);
                     }
                 }
 #pragma unroll
-                for (int t = 0; t < QROWS; ++t) {
-                    const int r = lane + 32 * t;
-                    if (r < m) q_out[(size_t)j * ldq + r] = q[t];
+                for (int c = 0; c < QC; ++c) {
+                    if (jc[c] >= n) break;
+#pragma unroll
+                    for (int t = 0; t < QROWS; ++t) {
+                        const int r = lane + 32 * t;
+                        if (r < m) q_out[(size_t)jc[c] * ldq + r] = q[c][t];
+                    }
                 }
             }
         } else if (Q) {

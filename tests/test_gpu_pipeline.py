@@ -63,3 +63,29 @@ def test_host_entries_refuse_device_tensors_and_short_workspaces(bs):
     with pytest.raises(bs.BsvdError) as e:
         bs.host_svd(a, s, workspace=torch.empty(16, dtype=torch.uint8, device=dev))
     assert e.value.code == bs.ERR_WORKSPACE
+
+
+def test_host_calls_on_two_streams_at_once(bs):
+    """A QR and an SVD host call enqueued on two streams without a synchronisation in between (the
+    bench's end-to-end step): each call's chunks take their own pair of the library's compute
+    streams, and both give the direct calls' results bit for bit."""
+    dev = torch.device("cuda")
+    bq, bsv = gen.qr128x32_exp8(batch=2000), gen.svd64_exp8(batch=2000)
+    hq_a, hs_a = torch.from_numpy(bq.a).pin_memory(), torch.from_numpy(bsv.a).pin_memory()
+    q0, r0, _ = bs.qr(hq_a.to(dev))
+    u0, s0, v0, _, _ = bs.svd(hs_a.to(dev))
+    torch.cuda.synchronize()
+    pin = lambda *shape: torch.zeros(shape, dtype=torch.float32).pin_memory()
+    q, r = pin(2000, 32, 128), pin(2000, 32, 32)
+    s, u, v = pin(2000, 64), pin(2000, 64, 64), pin(2000, 64, 64)
+    ws_q = torch.empty(bs.host_qr_workspace(bs.F32, 2000, 128, 32), dtype=torch.uint8, device=dev)
+    ws_s = torch.empty(bs.host_svd_workspace(bs.F32, 2000, 64, 64), dtype=torch.uint8, device=dev)
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    for _ in range(3):  # repeated: the calls alternate over the compute-stream pairs
+        side.wait_stream(main)
+        bs.host_qr(hq_a, q, r, chunks=5, workspace=ws_q, stream=side)
+        bs.host_svd(hs_a, s, u, v, chunks=8, workspace=ws_s, stream=main)
+        main.wait_stream(side)
+    torch.cuda.synchronize()
+    assert torch.equal(q, q0.cpu()) and torch.equal(r, r0.cpu())
+    assert torch.equal(s, s0.cpu().reshape(2000, 64)) and torch.equal(u, u0.cpu()) and torch.equal(v, v0.cpu())
