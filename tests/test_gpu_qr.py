@@ -61,12 +61,17 @@ RAGGED = [(1, 1), (2, 1), (7, 3), (33, 33), (64, 1), (100, 37), (129, 64), (5, 0
 WARP_F32 = [(1, 1), (2, 1), (7, 3), (33, 32), (64, 1), (100, 31), (128, 32), (5, 0), (0, 0), (31, 31), (48, 17),
             (127, 32)]
 WARP_F32_WIDE = [(64, 64), (63, 40), (33, 33), (64, 33), (2, 2), (60, 59), (0, 0), (40, 1)]
+# tall and wide FP32 panels (the randomized SVD's 256 x l samples): the CTA kernel with 512 threads,
+# every matrix of the batch in it, the small ones included
+TALL_F32 = [(256, 160), (255, 129), (200, 97), (129, 65), (256, 66), (130, 2), (3, 1), (0, 0), (64, 64), (160, 33),
+          (33, 0)]
 WARP_F64 = [(1, 1), (64, 32), (37, 20), (40, 32), (64, 1), (50, 31), (3, 0), (32, 32), (2, 2), (63, 31)]
 
 
 @pytest.mark.parametrize("dt,shapes,special", [
     (np.float32, RAGGED, (3, 5)), (np.float64, RAGGED, (3, 5)),
     (np.float32, WARP_F32, (3, 5)), (np.float32, WARP_F32_WIDE, (0, 1)), (np.float64, WARP_F64, (1, 5)),
+    (np.float32, TALL_F32, (0, 2)),
     (np.float32, [(256, 192), (255, 191), (3, 2)], ()),    # 200 KiB in shared memory
     (np.float32, [(1024, 16), (1000, 15), (17, 16)], ()),  # tallest supported
     (np.float64, [(1024, 24), (512, 20)], ())])
