@@ -83,6 +83,38 @@ int batched_qr(int dtype, int batch, int max_m, int max_n,
                int* d_info, void* stream);
 
 /*
+ * batched_qr_blocked_workspace -- bytes of DEVICE workspace batched_qr_blocked needs for these bounds
+ * (0 for invalid arguments).  Host only.
+ */
+size_t batched_qr_blocked_workspace(int dtype, int batch, int max_m, int max_n);
+
+/*
+ * batched_qr_blocked -- the same reduced Householder QR (Algorithm 1, same reflectors and signs) for
+ * matrices beyond batched_qr's shared-memory kernel: the blocked factorisation Section 3.1 leaves to
+ * larger matrices and Section 3.2 names for large squares.  Each matrix is copied to the workspace
+ * and factored in 32-column panels: the panel (all rows below its first) is factored on chip, its
+ * reflectors are gathered in the compact WY form H_j ... H_{j+31} = I - V T V^T, and the trailing
+ * columns are updated as C - V T^T (V^T C), streamed through shared memory in 128-row chunks.
+ * Q = H_0 ... H_{n-1} [I; 0] is formed by applying the panels' block reflectors, last panel first.
+ *
+ *   Arguments as batched_qr, plus:
+ *   workspace  DEVICE buffer of at least batched_qr_blocked_workspace(...) bytes, caller-owned,
+ *              contents need not be initialised; not used after the stream work completes.
+ *              Smaller -> BSVD_ERR_WORKSPACE.
+ * Limits: max_m <= batched_qr_blocked_max_rows(dtype) (a 32-column panel of that height fits in
+ * 200 KiB of shared memory: 1533 rows FP32, 733 FP64); any max_n <= max_m.  Otherwise
+ * BSVD_ERR_UNSUPPORTED.  d_info[b] as batched_qr.
+ */
+int batched_qr_blocked(int dtype, int batch, int max_m, int max_n,
+                       void* const* dA, const int* d_m, const int* d_n, const int* d_lda,
+                       void* const* dQ, const int* d_ldq,
+                       void* const* dR, const int* d_ldr,
+                       int* d_info, void* workspace, size_t workspace_bytes, void* stream);
+
+/* batched_qr_blocked_max_rows -- the tallest matrix batched_qr_blocked factors (host only). */
+int batched_qr_blocked_max_rows(int dtype);
+
+/*
  * batched_svd_jacobi -- reduced SVD A = U diag(S) V^T of each matrix by one-sided Jacobi
  * (Algorithm 2, Section 2.2; register / shared-memory kernels of Sections 4-5).
  *

@@ -63,6 +63,12 @@ def lib() -> ctypes.CDLL:
             L.bsvd_version.argtypes = []
             L.batched_qr.restype = i
             L.batched_qr.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, p]
+            L.batched_qr_blocked_workspace.restype = ctypes.c_size_t
+            L.batched_qr_blocked_workspace.argtypes = [i, i, i, i]
+            L.batched_qr_blocked.restype = i
+            L.batched_qr_blocked.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, p, ctypes.c_size_t, p]
+            L.batched_qr_blocked_max_rows.restype = i
+            L.batched_qr_blocked_max_rows.argtypes = [i]
             L.batched_svd_jacobi.restype = i
             L.batched_svd_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, p, p, p]
             L.bsvd_jacobi_variants.restype = i
@@ -266,6 +272,32 @@ def batched_qr(A: Batch, Q: Batch | None, R: Batch | None, info, stream=None) ->
                           _ptr(R.ptrs if R else None), _ptr(R.ld if R else None),
                           _dptr(info, "info", torch.int32, A.batch), _stream_ptr(stream))
     _check("batched_qr", rc)
+
+
+def batched_qr_blocked_workspace(A: Batch) -> int:
+    """Workspace bytes batched_qr_blocked needs for this batch's bounds."""
+    return int(lib().batched_qr_blocked_workspace(A.code, A.batch, A.max_m, A.max_n))
+
+
+def batched_qr_blocked_max_rows(dtype_code: int) -> int:
+    """The tallest matrix batched_qr_blocked factors."""
+    return int(lib().batched_qr_blocked_max_rows(dtype_code))
+
+
+def batched_qr_blocked(A: Batch, Q: Batch | None, R: Batch | None, info, workspace, stream=None) -> None:
+    """Blocked Householder QR (32-column panels, compact WY updates) of matrices beyond batched_qr's
+    shared-memory kernel; ``workspace`` a device uint8 tensor.  See include/bsvd.h."""
+    torch = _torch()
+    _same(Q, A, "Q")
+    _same(R, A, "R")
+    nbytes = batched_qr_blocked_workspace(A)
+    ws = _dptr(workspace, "workspace", torch.uint8, nbytes)
+    rc = lib().batched_qr_blocked(A.code, A.batch, A.max_m, A.max_n, _ptr(A.ptrs), _ptr(A.m), _ptr(A.n),
+                                  _ptr(A.ld), _ptr(Q.ptrs if Q else None), _ptr(Q.ld if Q else None),
+                                  _ptr(R.ptrs if R else None), _ptr(R.ld if R else None),
+                                  _dptr(info, "info", torch.int32, A.batch), ws, workspace.numel(),
+                                  _stream_ptr(stream))
+    _check("batched_qr_blocked", rc)
 
 
 def batched_svd_jacobi(A: Batch, S: Batch, U: Batch | None, V: Batch | None, info, rotations=None,
@@ -608,6 +640,20 @@ def batched_svd_block_jacobi_noalloc(A: Batch, S: Batch, U: Batch, V: Batch, inf
 # ----------------------------------------------------------------------------------------------
 # conveniences that allocate the outputs with torch (uniform batches)
 # ----------------------------------------------------------------------------------------------
+
+def qr_blocked(a, want_q: bool = True, want_r: bool = True, stream=None):
+    """Blocked QR of a uniform batch ``a`` (batch, n, m) -> (Q (batch, n, m), R (batch, n, n), info)."""
+    torch = _torch()
+    bsz, n, m = a.shape
+    A = Batch.uniform(a.contiguous(), m, n)
+    q = torch.empty((bsz, n, m), device=a.device, dtype=a.dtype) if want_q else None
+    r = torch.empty((bsz, n, n), device=a.device, dtype=a.dtype) if want_r else None
+    info = torch.empty(bsz, device=a.device, dtype=torch.int32)
+    ws = torch.empty(max(batched_qr_blocked_workspace(A), 1), device=a.device, dtype=torch.uint8)
+    batched_qr_blocked(A, Batch.uniform(q, m, n) if want_q else None, Batch.uniform(r, n, n) if want_r else None,
+                       info, ws, stream)
+    return q, r, info
+
 
 def qr(a, want_q: bool = True, want_r: bool = True, stream=None):
     """QR of a uniform batch ``a`` (batch, n, m) on the GPU -> (Q (batch, n, m), R (batch, n, n), info)."""

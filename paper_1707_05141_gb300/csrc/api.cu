@@ -84,6 +84,46 @@ int batched_qr(int dtype, int batch, int max_m, int max_n, void* const* dA, cons
                              : launch_qr<double>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dQ, d_ldq, dR, d_ldr, d_info, st);
 }
 
+size_t batched_qr_blocked_workspace(int dtype, int batch, int max_m, int max_n)
+{
+    if ((dtype != BSVD_F32 && dtype != BSVD_F64) || batch < 0 || max_m < 0 || max_n < 0 || max_n > max_m) return 0;
+    return dtype == BSVD_F32 ? qr_blocked_workspace<float>(batch, max_m, max_n)
+                             : qr_blocked_workspace<double>(batch, max_m, max_n);
+}
+
+int batched_qr_blocked_max_rows(int dtype)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    return dtype == BSVD_F32 ? qr_blocked_max_rows<float>() : qr_blocked_max_rows<double>();
+}
+
+int batched_qr_blocked(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
+                       const int* d_lda, void* const* dQ, const int* d_ldq, void* const* dR, const int* d_ldr,
+                       int* d_info, void* workspace, size_t workspace_bytes, void* stream)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (batch < 0) return -2;
+    if (max_m < 0) return -3;
+    if (max_n < 0 || max_n > max_m) return -4;
+    if (batch == 0) return BSVD_SUCCESS;
+    if (!dA) return -5;
+    if (!d_m) return -6;
+    if (!d_n) return -7;
+    if (!d_lda) return -8;
+    if (dQ && !d_ldq) return -10;
+    if (dR && !d_ldr) return -12;
+    if (!d_info) return -13;
+    if (!workspace) return -14;
+    if (max_m > batched_qr_blocked_max_rows(dtype)) return BSVD_ERR_UNSUPPORTED;
+    if (max_n == 0) max_n = 1;
+    if (max_m == 0) max_m = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    return dtype == BSVD_F32 ? launch_qr_blocked<float>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dQ, d_ldq, dR, d_ldr,
+                                                        d_info, workspace, workspace_bytes, st)
+                             : launch_qr_blocked<double>(batch, max_m, max_n, dA, d_m, d_n, d_lda, dQ, d_ldq, dR,
+                                                         d_ldr, d_info, workspace, workspace_bytes, st);
+}
+
 int batched_svd_jacobi(int dtype, int batch, int max_m, int max_n, void* const* dA, const int* d_m, const int* d_n,
                        const int* d_lda, void* const* dS, void* const* dU, const int* d_ldu, void* const* dV,
                        const int* d_ldv, double tol, int max_sweeps, int tier, int* d_info, long long* d_rotations,

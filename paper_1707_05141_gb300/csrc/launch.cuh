@@ -39,6 +39,15 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
                            const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU,
                            void* const* V, const int* LDV, double tol, int max_sweeps, int* info, long long* rot,
                            void* ws, size_t ws_bytes, cudaStream_t st);
+// the blocked Householder QR of matrices beyond the shared-memory kernel (qr_blocked.cu)
+template <typename T>
+size_t qr_blocked_workspace(int batch, int max_m, int max_n);
+template <typename T>
+int qr_blocked_max_rows();
+template <typename T>
+int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                      void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, void* ws,
+                      size_t ws_bytes, cudaStream_t st);
 template <typename T>
 int launch_block_jacobi(int batch, int max_m, int max_n, int bw, int method, void* const* A, const int* M,
                         const int* N, const int* LDA, void* const* S, void* const* U, const int* LDU, void* const* V,

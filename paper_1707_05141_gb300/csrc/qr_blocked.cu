@@ -39,8 +39,9 @@ struct QbLayout {
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// svd = false: the blocked QR alone (no R^T, no block-Jacobi workspace)
 template <typename T>
-QbLayout qb_layout(int batch, int max_m, int max_n, int bw, int method)
+QbLayout qb_layout(int batch, int max_m, int max_n, int bw, int method, bool svd = true)
 {
     QbLayout L;
     const size_t mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
@@ -48,7 +49,7 @@ QbLayout qb_layout(int batch, int max_m, int max_n, int bw, int method)
     L.strideX = mm * nn;
     L.strideT = P * kPw * kPw;
     L.strideRd = nn;
-    L.strideRt = nn * nn;
+    L.strideRt = svd ? nn * nn : 0;
     size_t o = 0;
     L.off_ptr = o;
     o = al256(o + sizeof(void*) * (size_t)batch * 3);
@@ -63,7 +64,7 @@ QbLayout qb_layout(int batch, int max_m, int max_n, int bw, int method)
     L.off_Rt = o;
     o = al256(o + sizeof(T) * L.strideRt * batch);
     L.off_inner = o;
-    L.inner_bytes = block_jacobi_workspace<T>(batch, (int)nn, (int)nn, bw, method & 0xff);
+    L.inner_bytes = svd ? block_jacobi_workspace<T>(batch, (int)nn, (int)nn, bw, method & 0xff) : 0;
     o = al256(o + L.inner_bytes);
     L.total = o;
     return L;
@@ -183,11 +184,12 @@ __global__ void __launch_bounds__(256) qb_panel_kernel(int p, unsigned char* ws,
 
 // block reflector of panel p applied to 32 columns of C (rows j0 .. mm-1):
 //   trans = 1: C <- (I - V T V^T)^T C = C - V T^T (V^T C)   (the QR's trailing update; C in X)
-//   trans = 0: C <- (I - V T V^T) C   = C - V T (V^T C)     (forming Q V~; C in the left vectors)
-// One CTA per (matrix, 32-column tile); rows in chunks of kCh through shared memory, twice.
+//   trans = 0: C <- (I - V T V^T) C   = C - V T (V^T C)     (forming Q V~ or Q; C in the output)
+// One CTA per (matrix, 32-column tile); tile t covers columns c0_base + 32 t ...; rows in chunks of
+// kCh through shared memory, twice.
 template <typename T>
 __global__ void __launch_bounds__(256) qb_apply_kernel(int p, int trans, int tiles, unsigned char* ws, QbLayout L,
-                                                       QbInts I, T* const* Cp, const int* LDC, int col0_from_panel)
+                                                       QbInts I, T* const* Cp, const int* LDC, int c0_base)
 {
     extern __shared__ __align__(16) unsigned char ap_sm[];
     T(*Vs)[kCh + 1] = reinterpret_cast<T(*)[kCh + 1]>(ap_sm);                       // V chunk (column i, row r)
@@ -198,8 +200,9 @@ __global__ void __launch_bounds__(256) qb_apply_kernel(int p, int trans, int til
     const int mm = I.mm[b], nn = I.nn[b];
     const int j0 = p * kPw;
     if (j0 >= nn) return;
-    // columns of C: trailing update X(:, j0+32+32t ..), or the left vectors' columns 32t ..
-    const int c0 = col0_from_panel ? j0 + kPw + kPw * t : kPw * t;
+    // columns of C: trailing update X(:, j0+32+32t ..), the left vectors' columns 32t .., or Q's
+    // columns j0 + 32t .. (those left of j0 are still e_c there, which the panel leaves alone)
+    const int c0 = c0_base + kPw * t;
     if (c0 >= nn) return;
     const int ncol = nn - c0 < kPw ? nn - c0 : kPw;
     const int vcols = nn - j0 < kPw ? nn - j0 : kPw;   // reflectors of this panel (zero beyond)
@@ -323,6 +326,64 @@ __global__ void __launch_bounds__(256) qb_mid_kernel(QbInts I, QbPtrs<T> Pp, int
     }
 }
 
+// ---- the blocked QR as an entry of its own (A = Q R of matrices beyond the shared-memory kernel) ----
+
+// setup: shapes (m >= n), X = A (ld m); a bad shape gets mm = nn = 0, so every later stage skips it
+template <typename T>
+__global__ void __launch_bounds__(256) qbq_setup_kernel(int max_mm, int max_nn, T* const* A, const int* M,
+                                                        const int* N, const int* LDA, T* const* Q, const int* LDQ,
+                                                        T* const* R, const int* LDR, unsigned char* ws, QbLayout L,
+                                                        QbInts I, int* info)
+{
+    const int b = blockIdx.x;
+    const int m = M[b], n = N[b], lda = LDA[b];
+    const int ldq = Q ? LDQ[b] : 1, ldr = R ? LDR[b] : 1;
+    const bool bad = m < 0 || n < 0 || m < n || m > max_mm || n > max_nn || lda < (m > 1 ? m : 1) ||
+                     (Q && ldq < (m > 1 ? m : 1)) || (R && ldr < (n > 1 ? n : 1));
+    if (threadIdx.x == 0) {
+        I.mm[b] = bad ? 0 : m;
+        I.nn[b] = bad ? 0 : n;
+        I.bad[b] = bad ? 1 : 0;
+        info[b] = bad ? BSVD_INFO_BAD_SHAPE : 0;
+    }
+    if (bad) return;
+    T* X = qb_X<T>(ws, L, b);
+    const T* a = A[b];
+    for (size_t e = threadIdx.x; e < (size_t)m * n; e += blockDim.x) {
+        const int j = (int)(e / m), i = (int)(e - (size_t)j * m);
+        X[e] = a[(size_t)j * lda + i];
+    }
+}
+
+// R (n x n: X's strict upper triangle, the diagonal from rd, exact zeros below) and Q = [I; 0]
+// (m x n), which the panels' block reflectors then turn into H_0 ... H_{n-1} [I; 0]
+template <typename T>
+__global__ void __launch_bounds__(256) qbq_out_kernel(T* const* Q, const int* LDQ, T* const* R, const int* LDR,
+                                                      unsigned char* ws, QbLayout L, QbInts I)
+{
+    const int b = blockIdx.x;
+    const int mm = I.mm[b], nn = I.nn[b];
+    if (nn == 0) return;
+    const T* X = qb_X<T>(ws, L, b);
+    const T* rd = reinterpret_cast<const T*>(ws + L.off_rd) + (size_t)b * L.strideRd;
+    if (R) {
+        T* r = R[b];
+        const int ldr = LDR[b];
+        for (size_t e = threadIdx.x; e < (size_t)nn * nn; e += blockDim.x) {
+            const int j = (int)(e / nn), i = (int)(e - (size_t)j * nn);
+            r[(size_t)j * ldr + i] = i < j ? X[(size_t)j * mm + i] : (i == j ? rd[i] : T(0));
+        }
+    }
+    if (Q) {
+        T* q = Q[b];
+        const int ldq = LDQ[b];
+        for (size_t e = threadIdx.x; e < (size_t)mm * nn; e += blockDim.x) {
+            const int j = (int)(e / mm), i = (int)(e - (size_t)j * mm);
+            q[(size_t)j * ldq + i] = i == j ? T(1) : T(0);
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -371,7 +432,7 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
         qb_panel_kernel<T><<<batch, 256, panel_smem, st>>>(p, ws, L, I);
         if (p + 1 < P)
             qb_apply_kernel<T><<<batch * (P - p - 1), 256, apply_smem, st>>>(p, 1, P - p - 1, ws, L, I, nullptr,
-                                                                              nullptr, 1);
+                                                                              nullptr, p * kPw + kPw);
         if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
     }
     qb_rt_kernel<T><<<batch, 256, 0, st>>>(ws, L, I);
@@ -392,6 +453,71 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
     return BSVD_SUCCESS;
 }
 
+// the blocked QR alone: X = A, panels and trailing updates, then R and Q = H_0 ... H_{n-1} [I; 0]
+// (panel p's block reflector applied, last panel first, to Q's columns from p's first on)
+// (bounds of 0 are taken as 1, as the launcher does)
+template <typename T>
+size_t qr_blocked_workspace(int batch, int max_m, int max_n)
+{
+    return qb_layout<T>(batch, max_m > 1 ? max_m : 1, max_n > 1 ? max_n : 1, 32, 0, false).total;
+}
+
+template <typename T>
+int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int* M, const int* N, const int* LDA,
+                      void* const* Q, const int* LDQ, void* const* R, const int* LDR, int* info, void* ws_v,
+                      size_t ws_bytes, cudaStream_t st)
+{
+    if (qr_blocked_max_rows<T>() < max_m) return BSVD_ERR_UNSUPPORTED;
+    const int ldp = (max_m > kPw ? max_m : kPw) | 1;
+    const size_t panel_smem = sizeof(T) * ((size_t)ldp * kPw + kPw + 2 * kPw * (kPw + 1));
+    const QbLayout L = qb_layout<T>(batch, max_m, max_n, 32, 0, false);
+    if (ws_bytes < L.total) return BSVD_ERR_WORKSPACE;
+    unsigned char* ws = static_cast<unsigned char*>(ws_v);
+    QbInts I;
+    int* ip = reinterpret_cast<int*>(ws + L.off_int);
+    int** slots[7] = {&I.mm, &I.nn, &I.bad, &I.ldL, &I.ldR, &I.n2, &I.ldRt};
+    for (int i = 0; i < 7; ++i) *slots[i] = ip + (size_t)i * batch;
+    qbq_setup_kernel<T><<<batch, 256, 0, st>>>(max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ, (T* const*)R,
+                                               LDR, ws, L, I, info);
+    if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    if (panel_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(qb_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem) !=
+            cudaSuccess)
+        return BSVD_ERR_CUDA;
+    constexpr size_t apply_smem = qb_apply_smem<T>();
+    if (apply_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(qb_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem) !=
+            cudaSuccess)
+        return BSVD_ERR_CUDA;
+    const int P = (max_n + kPw - 1) / kPw;
+    for (int p = 0; p < P; ++p) {
+        qb_panel_kernel<T><<<batch, 256, panel_smem, st>>>(p, ws, L, I);
+        if (p + 1 < P)
+            qb_apply_kernel<T><<<batch * (P - p - 1), 256, apply_smem, st>>>(p, 1, P - p - 1, ws, L, I, nullptr,
+                                                                              nullptr, p * kPw + kPw);
+        if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    }
+    qbq_out_kernel<T><<<batch, 256, 0, st>>>((T* const*)Q, LDQ, (T* const*)R, LDR, ws, L, I);
+    if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+    if (Q) {
+        for (int p = P - 1; p >= 0; --p) {
+            qb_apply_kernel<T><<<batch * (P - p), 256, apply_smem, st>>>(p, 0, P - p, ws, L, I, (T* const*)Q, LDQ,
+                                                                          p * kPw);
+            if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
+        }
+    }
+    return BSVD_SUCCESS;
+}
+
+// rows of the tallest matrix whose 32-column panel fits on chip (200 KiB of shared memory)
+template <typename T>
+int qr_blocked_max_rows()
+{
+    const size_t fixed = sizeof(T) * (kPw + 2 * kPw * (kPw + 1));
+    const size_t ld = (200 * 1024 - fixed) / (sizeof(T) * kPw);   // largest ld with the panel in 200 KiB
+    return (int)(ld % 2 ? ld : ld - 1);                          // ld = rows | 1
+}
+
 template size_t block_jacobi_qr_workspace<float>(int, int, int, int, int);
 template size_t block_jacobi_qr_workspace<double>(int, int, int, int, int);
 template int launch_block_jacobi_qr<float>(int, int, int, int, int, void* const*, const int*, const int*, const int*,
@@ -400,5 +526,14 @@ template int launch_block_jacobi_qr<float>(int, int, int, int, int, void* const*
 template int launch_block_jacobi_qr<double>(int, int, int, int, int, void* const*, const int*, const int*,
                                             const int*, void* const*, void* const*, const int*, void* const*,
                                             const int*, double, int, int*, long long*, void*, size_t, cudaStream_t);
+
+template size_t qr_blocked_workspace<float>(int, int, int);
+template size_t qr_blocked_workspace<double>(int, int, int);
+template int qr_blocked_max_rows<float>();
+template int qr_blocked_max_rows<double>();
+template int launch_qr_blocked<float>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
+                                      const int*, void* const*, const int*, int*, void*, size_t, cudaStream_t);
+template int launch_qr_blocked<double>(int, int, int, void* const*, const int*, const int*, const int*, void* const*,
+                                       const int*, void* const*, const int*, int*, void*, size_t, cudaStream_t);
 
 }  // namespace bsvd

@@ -113,3 +113,25 @@ def test_variant_descriptions(lib):
     assert L.bsvd_jacobi_variant_desc(0, -1, 64, 1, d) == -2
     assert L.bsvd_jacobi_variant_desc(0, 64, 64, 0, d) == -4
     assert L.bsvd_jacobi_variant_desc(0, 64, 64, 1, None) == -5
+
+
+def test_blocked_qr_host_checks(lib):
+    """The blocked QR's workspace query, height limit and argument checks (host only)."""
+    _, bs = lib
+    L = bs.lib()
+    z = None
+    assert L.batched_qr_blocked_max_rows(0) == 1533 and L.batched_qr_blocked_max_rows(1) == 733
+    assert L.batched_qr_blocked_max_rows(3) == -1
+    w1 = L.batched_qr_blocked_workspace(0, 10, 1000, 200)
+    w2 = L.batched_qr_blocked_workspace(0, 20, 1000, 200)
+    assert 10 * 1000 * 200 * 4 <= w1 < w2 and L.batched_qr_blocked_workspace(1, 10, 1000, 200) > w1
+    assert L.batched_qr_blocked_workspace(0, 10, 100, 200) == 0               # max_n > max_m
+    args = (z, z, z, z, z, z, z, z, z, z, 0, z)
+    assert L.batched_qr_blocked(7, 1, 64, 64, *args) == -1
+    assert L.batched_qr_blocked(0, -1, 64, 64, *args) == -2
+    assert L.batched_qr_blocked(0, 1, 64, 65, *args) == -4
+    assert L.batched_qr_blocked(0, 0, 64, 64, *args) == 0                    # empty batch: no-op
+    assert L.batched_qr_blocked(0, 1, 64, 64, *args) == -5
+    p = ctypes.c_void_p(8)                                                     # never dereferenced
+    assert L.batched_qr_blocked(0, 1, 64, 64, p, p, p, p, z, z, z, z, p, z, 0, z) == -14   # no workspace
+    assert L.batched_qr_blocked(0, 1, 2000, 64, p, p, p, p, z, z, z, z, p, p, 0, z) == bs.ERR_UNSUPPORTED

@@ -169,3 +169,95 @@ def test_qr_r_only_and_q_only(bs):
     q3, _, _ = bs.qr(a, want_r=False)
     torch.cuda.synchronize()
     assert torch.equal(r1, r2) and torch.equal(q1, q3)
+
+
+# ---- blocked QR (32-column panels, compact WY trailing updates) for matrices beyond the
+# shared-memory kernel: tall panels past 1024 rows and large squares (Sections 3.1-3.2) ----
+
+BLOCKED = [(np.float32, 1533, 96, 3, lambda i: np.logspace(0, -3, 96)),      # the tallest panel on chip
+           (np.float32, 1200, 300, 2, lambda i: np.exp(-np.arange(300) / 40.0)),
+           (np.float32, 700, 700, 2, lambda i: np.logspace(0, -4, 700)),      # a large square, 22 panels
+           (np.float64, 733, 200, 2, lambda i: np.logspace(0, -8, 200)),
+           (np.float64, 500, 500, 2, lambda i: 10.0 ** (-8.0 * np.arange(500) / 499))]
+
+
+@pytest.mark.parametrize("dt,m,n,nb,sig", BLOCKED)
+def test_qr_blocked_against_oracle(bs, dt, m, n, nb, sig):
+    """Every matrix of the batch against the oracle's Householder QR: R and Q after sign alignment,
+    exact zeros below R's diagonal, orthogonality and residual at the gate."""
+    b = gen.uniform_batch(81, nb, m, n, dt, sig)
+    a = torch.from_numpy(b.a).cuda()
+    q, r, info = bs.qr_blocked(a)
+    torch.cuda.synchronize()
+    assert np.all(info.cpu().numpy() == 0)
+    mats = [b.a64(i) for i in range(nb)]
+    Qo, Ro, _ = O.qr_batch(mats)
+    qh, rh = _host(q), _host(r)
+    for i in range(nb):
+        e = qr_errors(mats[i], qh[i].T, rh[i].T, Qo[i], Ro[i], dt)
+        assert e["r"] <= 1.0 and e["q"] <= 1.0, (i, e)
+        assert e["tril_zero"]
+        assert e["orth_q"] <= gate(dt) and e["resid"] <= gate(dt), (i, e)
+
+
+def test_qr_blocked_ragged_and_bad_shapes(bs):
+    """A ragged FP32 batch (1 x 1, single columns, n = 0, a panel edge at 32 and 33 columns, the
+    tallest height) with one wide matrix, which is flagged and left untouched; Q-only and R-only
+    calls give the same factors."""
+    shapes = [(1533, 40), (1, 1), (64, 64), (100, 1), (5, 0), (300, 299), (1000, 33), (129, 32), (40, 60)]
+    rng = np.random.default_rng(3)
+    mats = [rng.standard_normal((m, n)) for m, n in shapes]
+    dev = torch.device("cuda")
+    ms = np.array([s[0] for s in shapes], np.int32)
+    ns = np.array([s[1] for s in shapes], np.int32)
+    ks = np.minimum(ms, ns)
+    offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns + 1)[:-1]])
+    offR = np.concatenate([[0], np.cumsum(ns.astype(np.int64) * ns + 1)[:-1]])
+    flat = np.zeros(int(offA[-1] + ms[-1] * ns[-1] + 1), np.float32)
+    for mat, o in zip(mats, offA):
+        flat[o:o + mat.size] = mat.T.reshape(-1)
+    fa = torch.from_numpy(flat).to(dev)
+    results = []
+    for want_q, want_r in ((True, True), (True, False), (False, True)):
+        fq = torch.full_like(fa, float("nan"))
+        fr = torch.full((int(offR[-1] + ns[-1] ** 2 + 1),), float("nan"), device=dev)
+        info = torch.full((len(shapes),), -7, dtype=torch.int32, device=dev)
+        A = bs.Batch.packed(fa, offA, ms, ns)
+        ws = torch.empty(bs.batched_qr_blocked_workspace(A), dtype=torch.uint8, device=dev)
+        bs.batched_qr_blocked(A, bs.Batch.packed(fq, offA, ms, ns) if want_q else None,
+                              bs.Batch.packed(fr, offR, ns, ns) if want_r else None, info, ws)
+        torch.cuda.synchronize()
+        results.append((fq.cpu().numpy().astype(np.float64), fr.cpu().numpy().astype(np.float64), info.cpu().numpy()))
+    fq, fr, info = results[0]
+    assert all(np.array_equal(r[2], info) for r in results)
+    assert np.array_equal(results[1][0], fq, equal_nan=True) and np.array_equal(results[2][1], fr, equal_nan=True)
+    assert np.all(np.isnan(results[1][1])) and np.all(np.isnan(results[2][0]))
+    for b, ((m, n), mat) in enumerate(zip(shapes, mats)):
+        if m < n:
+            assert info[b] == bs.INFO_BAD_SHAPE
+            assert np.all(np.isnan(fq[offA[b]:offA[b] + m * n])) and np.all(np.isnan(fr[offR[b]:offR[b] + n * n]))
+            continue
+        assert info[b] == 0, (m, n, info[b])
+        if n == 0:
+            continue
+        a64 = flat[offA[b]:offA[b] + m * n].reshape(n, m).T.astype(np.float64)
+        qo, ro = O.qr(a64)
+        q = fq[offA[b]:offA[b] + m * n].reshape(n, m).T
+        r = fr[offR[b]:offR[b] + n * n].reshape(n, n).T
+        e = qr_errors(a64, q, r, qo, ro, np.float32)
+        assert e["r"] <= 1.0 and e["q"] <= 1.0 and e["tril_zero"], ((m, n), e)
+        assert e["orth_q"] <= 1e-5 and e["resid"] <= 1e-5, ((m, n), e)
+
+
+def test_qr_blocked_agrees_with_the_shared_memory_kernel(bs):
+    """On shapes both kernels take, the blocked QR and the one-CTA kernel give the same factors
+    within rounding (the same reflectors, applied in another order)."""
+    b = gen.uniform_batch(82, 64, 256, 96, np.float32, lambda i: np.exp(-np.arange(96) / 16.0))
+    a = torch.from_numpy(b.a).cuda()
+    q0, r0, i0 = bs.qr(a)
+    q1, r1, i1 = bs.qr_blocked(a)
+    torch.cuda.synchronize()
+    assert torch.equal(i0, i1)
+    scale = float(r0.abs().max())
+    assert float((r1 - r0).abs().max()) <= 64 * 6e-8 * 16 * scale
+    assert float((q1 - q0).abs().max()) <= 1e-4
