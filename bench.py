@@ -612,16 +612,23 @@ class Block512:
         return self._step_fn(self.bs.BLOCK_SIMT_PRODUCTS), self.quality
 
     def extra_arms(self, stream, steps, warmup, time_fn):
-        """GRAM on A itself (no QR preconditioning), tensor-core Gram."""
+        """GRAM on A itself (no QR preconditioning), tensor-core Gram; and the default form with every
+        block pair re-tested every sweep (no pair selection by the recorded tests)."""
         import torch
-        step = self._step_fn(0)
-        for _ in range(warmup):
-            step(stream)
-        torch.cuda.synchronize()
-        t = time_fn(step)
-        return {"no_qr_preconditioning": {"form": "GRAM block Jacobi on A (tensor-core Gram), no QR preconditioning",
-                                          "ms_per_step": t["ms_step"], "clocks": t["clocks"],
-                                          "value": self.units / (t["ms_step"] * 1e-3), **self.quality()}}
+        out = {}
+        for name, method, form in (
+                ("no_qr_preconditioning", 0, "GRAM block Jacobi on A (tensor-core Gram), no QR preconditioning"),
+                ("retest_every_pair", self.bs.BLOCK_QR_PRECONDITION | self.bs.BLOCK_RETEST_ALL,
+                 "the default form re-testing every block pair every sweep (BSVD_BLOCK_RETEST_ALL): the "
+                 "recorded pair tests skip pairs found orthogonal whose blocks did not change since")):
+            step = self._step_fn(method)
+            for _ in range(warmup):
+                step(stream)
+            torch.cuda.synchronize()
+            t = time_fn(step)
+            out[name] = {"form": form, "ms_per_step": t["ms_step"], "clocks": t["clocks"],
+                         "value": self.units / (t["ms_step"] * 1e-3), **self.quality()}
+        return out
 
     units = property(lambda self: self.nb)
 

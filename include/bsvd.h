@@ -206,6 +206,12 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
  * right vectors.  Needs max(m, n) * 32 * sizeof(element) <= 200 KiB (a panel on chip); the workspace
  * holds X, R^T and the panels' T factors besides the block tier's own. */
 #define BSVD_BLOCK_QR_PRECONDITION (1 << 18)
+/* Flag for `method`: test every block pair in every sweep.  By default a pair whose test found it
+ * orthogonal is not formed or tested again while neither of its two blocks has been rotated since
+ * (the block pairs are selected by their recorded off-diagonal tests, the adaptive pair selection
+ * Section 6.3 proposes, in its exact form: the skipped tests would have come out the same, so the
+ * results do not change).  This flag restores the plain cyclic visit, for comparison. */
+#define BSVD_BLOCK_RETEST_ALL (1 << 19)
 
 /*
  * batched_svd_block_jacobi_workspace -- bytes of DEVICE workspace batched_svd_block_jacobi needs

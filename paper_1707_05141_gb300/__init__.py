@@ -34,6 +34,7 @@ RSVD_TC_SAMPLING = 2
 BLOCK_SIMT_PRODUCTS = 1 << 16
 BLOCK_TEST_TIMEOUT = 1 << 17
 BLOCK_QR_PRECONDITION = 1 << 18
+BLOCK_RETEST_ALL = 1 << 19
 TIER_AUTO, TIER_REGISTER, TIER_SHARED = 0, 1, 2
 
 _lock = threading.Lock()

@@ -229,9 +229,9 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
     if (block_width != 16 && block_width != 32) return -16;
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
     // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
-    // 18 QR preconditioning, 24-30 inner sweep cap
+    // 18 QR preconditioning, 19 re-test every pair, 24-30 inner sweep cap
     if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | BSVD_BLOCK_QR_PRECONDITION |
-                   (0x7f << 24)))
+                   BSVD_BLOCK_RETEST_ALL | (0x7f << 24)))
         return -17;
     if (!d_info) return -18;
     if (!workspace) return -20;

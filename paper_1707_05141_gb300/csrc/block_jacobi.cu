@@ -46,6 +46,9 @@ struct BjLayout {
     size_t off_state;                                    // per-matrix state
     size_t off_mlist, off_plist;                         // live matrices, rotating pair items
     size_t off_ctr;                                      // BjCounters
+    size_t off_ver, off_pv;                              // block versions, pair test records
+    size_t npv;                                          // pair records per matrix
+    int retest;                                          // 1: re-test every pair every sweep
     size_t total;
 };
 
@@ -67,6 +70,29 @@ struct BjState {
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Pair selection by the recorded tests.  Every block carries a version, bumped when a rotating pair
+// that contains it is decided (its update follows in the same step, and no other pair of the step
+// touches it).  A pair whose test found it orthogonal records the two versions; while neither block
+// changes its Gram matrix -- and so its test -- would come out the same, so the pair is not formed
+// or tested again.  The choice is exact: results equal those of re-testing every pair.
+struct BjPairRecord {
+    int* ver;       // the two blocks' versions
+    unsigned* rec;  // the pair's record: (version i << 16) | version j when found orthogonal, else ~0
+    unsigned key;   // the current versions, packed the same way
+};
+
+__device__ __forceinline__ BjPairRecord bj_pair_record(unsigned char* ws, const BjLayout& L, int b, int bi, int bj)
+{
+    const int nbp = 2 * L.npairs;
+    int* ver = reinterpret_cast<int*>(ws + L.off_ver) + (size_t)b * nbp;
+    unsigned* rec = nullptr;   // (no pair: bi == bj when the item is not live)
+    if (bi < bj) {
+        const size_t idx = (size_t)bi * nbp - (size_t)bi * (bi + 1) / 2 + (size_t)(bj - bi - 1);
+        rec = reinterpret_cast<unsigned*>(ws + L.off_pv) + (size_t)b * L.npv + idx;
+    }
+    return BjPairRecord{ver, rec, ((unsigned)ver[bi] << 16) | ((unsigned)ver[bj] & 0xffffu)};
+}
 
 template <typename T>
 static BjLayout bj_layout(int batch, int max_m, int max_n, int bw, bool direct)
@@ -108,6 +134,10 @@ static BjLayout bj_layout(int batch, int max_m, int max_n, int bw, bool direct)
     L.off_mlist = take((size_t)batch * sizeof(int));
     L.off_plist = take(L.n_items * sizeof(int));
     L.off_ctr = take(sizeof(BjCounters));
+    L.npv = (size_t)(2 * L.npairs) * (2 * L.npairs - 1) / 2;
+    L.off_ver = take((size_t)batch * 2 * L.npairs * sizeof(int));
+    L.off_pv = take((size_t)batch * L.npv * sizeof(unsigned));
+    L.retest = 0;
     L.total = o;
     return L;
 }
@@ -167,6 +197,12 @@ __global__ void bj_setup_kernel(int batch, int max_mm, int max_nn, int bw, int n
         reinterpret_cast<int*>(ws + L.off_ld)[it] = 2 * bw;
         reinterpret_cast<int*>(ws + L.off_ldp)[it] = mm > 1 ? mm : 1;
     }
+    {
+        int* ver = reinterpret_cast<int*>(ws + L.off_ver) + (size_t)b * 2 * npairs;
+        unsigned* rec = reinterpret_cast<unsigned*>(ws + L.off_pv) + (size_t)b * L.npv;
+        for (int k = threadIdx.x; k < 2 * npairs; k += blockDim.x) ver[k] = 0;
+        for (size_t k = threadIdx.x; k < L.npv; k += blockDim.x) rec[k] = ~0u;
+    }
     if (bad) return;
     const T* a = A[b];
     for (size_t e = threadIdx.x; e < (size_t)mm * nn; e += blockDim.x) {
@@ -212,7 +248,8 @@ __device__ __forceinline__ void bj_gram_item(int it, int batch, int npairs, int 
     // orthogonalised internally through its pair with the empty block; a matrix with fewer blocks
     // than the batch's largest runs its own nbp - 1 steps of each sweep and idles in the rest
     const bool live = !st->converged && step < nbp - 1 && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn;
-    if (!live) {
+    const BjPairRecord pr = bj_pair_record(ws, L, b, bi, bj);
+    if (!live || (!L.retest && pr.rec && *pr.rec == pr.key)) {   // no pair, or unchanged since found orthogonal
         if (threadIdx.x == 0) im[it] = in[it] = 0;
         return;
     }
@@ -271,6 +308,10 @@ __device__ __forceinline__ void bj_gram_item(int it, int batch, int npairs, int 
             atomicAdd(&st->rot_sweep, 1);
             BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
             reinterpret_cast<int*>(ws + L.off_plist)[atomicAdd(&C->pcount, 1)] = it;
+            ++pr.ver[bi];
+            ++pr.ver[bj];
+        } else if (pr.rec) {
+            *pr.rec = pr.key;
         }
         // emax of the matrix over the sweep, as ordered bits of a non-negative double
         atomicMax(reinterpret_cast<unsigned long long*>(&st->emax), (unsigned long long)__double_as_longlong(em));
@@ -632,7 +673,8 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
     if (k < nbp / 2 && step < nbp - 1) round_robin_pair(nbp, step, k, bi, bj);
     const bool live = !st->converged && step < nbp - 1 && k < nbp / 2 && (bj < nblk || nblk == 1) && bi * bw < nn &&
                       mm > 0;  // (the SIMT item explains each condition)
-    if (!live) {
+    const BjPairRecord pr = bj_pair_record(ws, L, b, bi, bj);
+    if (!live || (!L.retest && pr.rec && *pr.rec == pr.key)) {   // as in the SIMT item
         if (threadIdx.x == 0) im[it] = in[it] = 0;
         return;
     }
@@ -809,6 +851,10 @@ __device__ __forceinline__ void bj_gram_tc_item(int it, int npairs, int step, in
         if (rot) {
             atomicAdd(&st->rot_sweep, 1);
             reinterpret_cast<int*>(ws + L.off_plist)[atomicAdd(&C->pcount, 1)] = it;
+            ++pr.ver[bi];
+            ++pr.ver[bj];
+        } else if (pr.rec) {
+            *pr.rec = pr.key;
         }
         atomicMax(reinterpret_cast<unsigned long long*>(&st->emax), (unsigned long long)__double_as_longlong(em));
     }
@@ -994,6 +1040,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
     const int cap_bits = (method >> 24) & 0x7f;
     const bool simt = (method & BSVD_BLOCK_SIMT_PRODUCTS) != 0;
     const int test_timeout = (method & BSVD_BLOCK_TEST_TIMEOUT) != 0 ? 1 : 0;
+    const int retest = (method & BSVD_BLOCK_RETEST_ALL) != 0 ? 1 : 0;
     method &= 0xff;
     const bool direct = method != 0;
     // sweep cap of each inner SVD: 127 = to convergence (as Algorithm 3 states), 0 = default.
@@ -1019,7 +1066,8 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
         int d[9];
         inner_u = jacobi_reg_variant_desc(sizeof(T) == 8, K2, K2, inner_variant, d) == BSVD_SUCCESS && d[6];
     }
-    const BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
+    BjLayout L = bj_layout<T>(batch, max_m, max_n, bw, direct);
+    L.retest = retest;
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
     const int npairs = L.npairs, nbp = 2 * npairs;
     // default pair threshold sqrt(m) u; DIRECT rotations are only as orthogonal as the pair's

@@ -115,7 +115,7 @@ int batched_svd_block_jacobi_noalloc(int dtype, int batch, int max_m, int max_n,
     // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
     // 18 QR preconditioning, 24-30 inner sweep cap
     if (method & ~(0xffff | BSVD_BLOCK_SIMT_PRODUCTS | BSVD_BLOCK_TEST_TIMEOUT | BSVD_BLOCK_QR_PRECONDITION |
-                   (0x7f << 24)))
+                   BSVD_BLOCK_RETEST_ALL | (0x7f << 24)))
         return -17;
     if (!d_info) return -18;
     const size_t need = dtype == BSVD_F32

@@ -66,7 +66,7 @@ def test_host_argument_checks_without_gpu(lib):
     # block Jacobi: unknown `method` bits are refused before anything is launched (the pointers
     # are never dereferenced: the checks return first)
     p = 64
-    for bad in (1 << 19, 1 << 20, 2, -(1 << 30)):
+    for bad in (1 << 21, 1 << 20, 2, -(1 << 30)):
         assert L.batched_svd_block_jacobi(0, 1, 64, 64, p, p, p, p, p, p, p, p, p, 0.0, 0, 32, bad, p, z, p, 1 << 20,
                                           z) == -17, bad
 

@@ -167,3 +167,28 @@ def test_block_workspace_and_errors(bs):
                                 bs.Batch.uniform(v, 40, 40), info, ws, block_width=16)
     torch.cuda.synchronize()
     assert info.tolist() == [1, 1] and float(s.abs().max()) == 0.0
+
+
+RETEST = 1 << 19   # BSVD_BLOCK_RETEST_ALL
+
+
+def _bits(t):
+    return t.view(torch.int32) if t.dtype == torch.float32 else t.view(torch.int64)
+
+
+@pytest.mark.parametrize("method,bw,dt", [(0, 32, np.float32), (0 | (1 << 16), 32, np.float32), (1, 32, np.float32),
+                                          (0 | QR, 32, np.float32), (0, 16, np.float64), (1 | QR, 16, np.float64)])
+def test_block_pair_selection_is_exact(bs, method, bw, dt):
+    """Pairs found orthogonal are not tested again while their blocks are unchanged (adaptive pair
+    selection, Section 6.3); the skipped tests would have come out the same, so U, S, V, the sweep
+    counts and the rotation counts equal those of re-testing every pair, bit for bit."""
+    b = gen.uniform_batch(91, 6, 320, 256, dt, lambda i: np.logspace(0, -5 if dt == np.float32 else -9, 256))
+    a = torch.from_numpy(b.a).cuda()
+    r0 = bs.svd_block(a, block_width=bw, method=method | RETEST, max_sweeps=30)
+    r1 = bs.svd_block(a, block_width=bw, method=method, max_sweeps=30)
+    torch.cuda.synchronize()
+    for x, y in zip(r0[:3], r1[:3]):
+        assert torch.equal(_bits(x), _bits(y)), method
+    assert torch.equal(r0[3], r1[3]) and torch.equal(r0[4], r1[4]), method
+    info = r1[3].cpu().numpy()
+    assert np.all((info > 0) & (info < (1 << 20))), info
