@@ -96,13 +96,16 @@ size_t batched_qr_blocked_workspace(int dtype, int batch, int max_m, int max_n);
  * reflectors are gathered in the compact WY form H_j ... H_{j+31} = I - V T V^T, and the trailing
  * columns are updated as C - V T^T (V^T C), streamed through shared memory in 128-row chunks.
  * Q = H_0 ... H_{n-1} [I; 0] is formed by applying the panels' block reflectors, last panel first.
+ * A panel taller than one CTA's shared memory holds (1533 rows FP32, 733 FP64) is factored by a
+ * thread-block cluster of up to 8 CTAs, each with a slab of its rows in shared memory; the
+ * reflectors' norms and products are summed across the cluster through distributed shared memory.
  *
  *   Arguments as batched_qr, plus:
  *   workspace  DEVICE buffer of at least batched_qr_blocked_workspace(...) bytes, caller-owned,
  *              contents need not be initialised; not used after the stream work completes.
  *              Smaller -> BSVD_ERR_WORKSPACE.
- * Limits: max_m <= batched_qr_blocked_max_rows(dtype) (a 32-column panel of that height fits in
- * 200 KiB of shared memory: 1533 rows FP32, 733 FP64); any max_n <= max_m.  Otherwise
+ * Limits: max_m <= batched_qr_blocked_max_rows(dtype) (8 slabs of a 32-column panel, each in
+ * 200 KiB of one CTA's shared memory: 11976 rows FP32, 5576 FP64); any max_n <= max_m.  Otherwise
  * BSVD_ERR_UNSUPPORTED.  d_info[b] as batched_qr.
  */
 int batched_qr_blocked(int dtype, int batch, int max_m, int max_n,
@@ -203,8 +206,9 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier);
  * 32-column panels (each panel on chip, the trailing columns updated through the compact WY form
  * I - V T V^T), the block Jacobi runs on the lower-triangular R^T, whose rows are graded like the
  * singular values (about half the outer sweeps), and X's left vectors are formed as Q times R^T's
- * right vectors.  Needs max(m, n) * 32 * sizeof(element) <= 200 KiB (a panel on chip); the workspace
- * holds X, R^T and the panels' T factors besides the block tier's own. */
+ * right vectors.  Needs max(m, n) <= batched_qr_blocked_max_rows(dtype) (the panels are factored as
+ * in batched_qr_blocked); the workspace holds X, R^T and the panels' T factors besides the block
+ * tier's own. */
 #define BSVD_BLOCK_QR_PRECONDITION (1 << 18)
 /* Flag for `method`: test every block pair in every sweep.  By default a pair whose test found it
  * orthogonal is not formed or tested again while neither of its two blocks has been rotated since

@@ -10,11 +10,16 @@
 //          T(0:c, c) = -2 T(0:c, 0:c) V(:, 0:c)^T v_c;
 //   update the trailing columns C = X(j0:, j0+32:) <- (I - V T V^T)^T C = C - V T^T (V^T C), in
 //          32-column tiles, rows streamed through shared memory in chunks (any mm).
+// A panel too tall for one CTA's shared memory is factored by a thread-block cluster of up to 8
+// CTAs, each holding a slab of its rows: per column, the CTAs' partial sums of squares, then their
+// partial products with the panel's other columns, are exchanged through distributed shared memory
+// (two cluster barriers), every CTA forming the same reflector from the same sums.
 // Preconditioned block Jacobi (the QR preconditioning Section 6.3 names as future work; the same
 // effect as the register tier's preconditioning, at the block level).  With X = Q R, the block tier
 // runs on R^T (nn x nn, lower triangular, rows graded like the singular values): R^T = U~ S V~^T
 // gives X = (Q V~) S U~^T, so X's right vectors are U~ and its left ones Q V~ = H_0 ... H_{nn-1} V~,
 // formed by applying the panels' block reflectors, last panel first, to [V~; 0].
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -384,7 +389,227 @@ __global__ void __launch_bounds__(256) qbq_out_kernel(T* const* Q, const int* LD
     }
 }
 
+// ---- tall panels: one thread-block cluster per matrix, a slab of the panel's rows per CTA ----
+
+namespace cg = cooperative_groups;
+
+constexpr int kClusterMax = 8;   // CTAs per cluster (the portable maximum)
+
+// dynamic shared memory of the cluster panel kernel for slabs of up to `slab` rows:
+// S (slab | 1) x 32, diag, partial Gram (32 x 33), G and T (32 x 33 each), part/xq (2 + 2),
+// wpart (2 x 32)
+template <typename T>
+size_t qb_cpanel_smem(int slab)
+{
+    return sizeof(T) * ((size_t)(slab | 1) * kPw + kPw + 3 * kPw * (kPw + 1) + 4 + 2 * kPw);
+}
+
+template <typename T>
+__device__ __forceinline__ T qb_block_sum(T v, T* red)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;   // in thread 0
+}
+
+// panel p of matrix blockIdx.x / cs, CTA `rank` of its cluster holding panel rows
+// [rank * slab, rank * slab + nr): Householder reflectors of the panel's columns (Algorithm 1, the
+// same reflectors and signs as the one-CTA factorisation), R, and the compact WY factor T
+template <typename T>
+__global__ void __launch_bounds__(256) qb_panel_cluster_kernel(int p, int cs, unsigned char* ws, QbLayout L, QbInts I)
+{
+    extern __shared__ __align__(16) unsigned char qc_sm[];
+    __shared__ T red[8];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.x / cs;
+    const int mm = I.mm[b], nn = I.nn[b];
+    const int j0 = p * kPw;
+    if (j0 >= nn) return;   // the whole cluster (one matrix) leaves together
+    const int rows = mm - j0;
+    const int slab = ((rows + cs - 1) / cs) > kPw ? (rows + cs - 1) / cs : kPw;   // CTA 0 holds rows 0 .. 31
+    const int lds = slab | 1;
+    const int r0 = rank * slab;
+    const int nr = rows - r0 < 0 ? 0 : (rows - r0 > slab ? slab : rows - r0);
+    const int vcols = nn - j0 < kPw ? nn - j0 : kPw;
+    T* S = reinterpret_cast<T*>(qc_sm);
+    T* diag = S + (size_t)lds * kPw;
+    T* Gp = diag + kPw;                 // this CTA's partial V^T V
+    T* G = Gp + kPw * (kPw + 1);        // the cluster's sum (CTA 0)
+    T* Ts = G + kPw * (kPw + 1);        // T (CTA 0)
+    T* part = Ts + kPw * (kPw + 1);     // [2]: partial sum of squares of the current column
+    T* xq = part + 2;                   // [2]: the column's diagonal entry (CTA 0)
+    T* wpart = xq + 2;                  // [2][32]: partial products with the columns to its right
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T* X = qb_X<T>(ws, L, b);
+    for (int e = tid; e < nr * kPw; e += blockDim.x) {
+        const int c = e / nr, lr = e - c * nr;
+        S[c * lds + lr] = j0 + c < nn ? X[(size_t)(j0 + c) * mm + j0 + r0 + lr] : T(0);
+    }
+    __syncthreads();
+    for (int i = 0; i < vcols; ++i) {
+        const int par = i & 1;
+        T* col = S + (size_t)i * lds;
+        // this CTA's share of ||x||^2 over the panel rows at and below i
+        T ss = T(0);
+        for (int lr = tid; lr < nr; lr += blockDim.x)
+            if (r0 + lr >= i) ss += col[lr] * col[lr];
+        ss = qb_block_sum(ss, red);
+        if (tid == 0) {
+            part[par] = ss;
+            if (rank == 0) xq[par] = col[i];
+        }
+        cluster.sync();
+        // every CTA forms the same reflector from the same sums (added in rank order)
+        T tot = T(0);
+        for (int q = 0; q < cs; ++q) tot += *cluster.map_shared_rank(part + par, q);
+        const T x0 = *cluster.map_shared_rank(xq + par, 0);
+        const T alpha = dsqrt(tot);
+        const T sg = x0 >= T(0) ? T(1) : T(-1);
+        const T inv = alpha > T(0) ? drsqrt(T(2) * alpha * (alpha + dabs(x0))) : T(0);
+        for (int lr = tid; lr < nr; lr += blockDim.x) {
+            const int pr = r0 + lr;
+            if (pr >= i) col[lr] = (pr == i ? x0 + sg * alpha : col[lr]) * inv;
+        }
+        if (rank == 0 && tid == 0) diag[i] = -sg * alpha;
+        __syncthreads();
+        // this CTA's share of v^T (column j) for the panel's columns right of i (a warp per column)
+        for (int j = i + 1 + warp; j < vcols; j += 8) {
+            const T* cj = S + (size_t)j * lds;
+            T d = T(0);
+            for (int lr = lane; lr < nr; lr += 32)
+                if (r0 + lr >= i) d += col[lr] * cj[lr];
+            d = warp_sum(d);
+            if (lane == 0) wpart[par * kPw + j] = d;
+        }
+        cluster.sync();
+        for (int j = i + 1 + warp; j < vcols; j += 8) {
+            T w = T(0);
+            for (int q = 0; q < cs; ++q) w += *cluster.map_shared_rank(wpart + par * kPw + j, q);
+            w *= T(2);
+            T* cj = S + (size_t)j * lds;
+            for (int lr = lane; lr < nr; lr += 32)
+                if (r0 + lr >= i) cj[lr] -= w * col[lr];
+        }
+        __syncthreads();
+    }
+    // this CTA's share of V^T V (V(r, c) = S(r, c) at and below the panel's diagonal)
+    for (int e = warp; e < kPw * kPw; e += 8) {
+        const int i = e / kPw, j = e - i * kPw;
+        if (j < i) continue;
+        T s = T(0);
+        if (j < vcols)
+            for (int lr = lane; lr < nr; lr += 32)
+                if (r0 + lr >= j) s += S[(size_t)i * lds + lr] * S[(size_t)j * lds + lr];
+        s = warp_sum(s);
+        if (lane == 0) Gp[i * (kPw + 1) + j] = s;
+    }
+    cluster.sync();
+    if (rank == 0) {
+        for (int e = tid; e < kPw * (kPw + 1); e += blockDim.x) {
+            T s = T(0);
+            for (int q = 0; q < cs; ++q) s += *cluster.map_shared_rank(Gp + e, q);
+            G[e] = s;
+            Ts[e] = T(0);
+        }
+        __syncthreads();
+        for (int c = 0; c < kPw; ++c) {   // T(c, c) = 2, T(0:c, c) = -2 T(0:c, 0:c) G(0:c, c)
+            if (tid < c) {
+                T s = T(0);
+                for (int k = tid; k < c; ++k) s += Ts[k * (kPw + 1) + tid] * G[k * (kPw + 1) + c];
+                Ts[c * (kPw + 1) + tid] = T(-2) * s;
+            }
+            if (tid == 0) Ts[c * (kPw + 1) + c] = T(2);
+            __syncthreads();
+        }
+        T* Tg = reinterpret_cast<T*>(ws + L.off_T) + (size_t)b * L.strideT + (size_t)p * kPw * kPw;
+        for (int e = tid; e < kPw * kPw; e += blockDim.x) {
+            const int c = e / kPw, i = e - c * kPw;
+            Tg[e] = Ts[c * (kPw + 1) + i];
+        }
+        T* rd = reinterpret_cast<T*>(ws + L.off_rd) + (size_t)b * L.strideRd;
+        if (tid < vcols) rd[j0 + tid] = diag[tid];
+    }
+    for (int e = tid; e < nr * kPw; e += blockDim.x) {
+        const int c = e / nr, lr = e - c * nr;
+        if (j0 + c < nn) X[(size_t)(j0 + c) * mm + j0 + r0 + lr] = S[c * lds + lr];
+    }
+    cluster.sync();   // no CTA leaves while CTA 0 may still read its shared memory
+}
+
 }  // namespace
+
+// rows of the tallest panel one CTA factors: its 32 columns in 200 KiB of shared memory
+template <typename T>
+static int qr_blocked_cta_rows()
+{
+    const size_t fixed = sizeof(T) * (kPw + 2 * kPw * (kPw + 1));
+    const size_t ld = (200 * 1024 - fixed) / (sizeof(T) * kPw);   // largest ld with the panel in 200 KiB
+    return (int)(ld % 2 ? ld : ld - 1);                          // ld = rows | 1
+}
+
+// rows of one cluster CTA's slab, the same way
+template <typename T>
+static int qb_cluster_slab_rows()
+{
+    const size_t fixed = qb_cpanel_smem<T>(1) - sizeof(T) * kPw;   // everything but S
+    const size_t ld = (200 * 1024 - fixed) / (sizeof(T) * kPw);
+    return (int)(ld % 2 ? ld : ld - 1);
+}
+
+// the tallest matrix the blocked QR factors: a cluster of 8 slabs
+template <typename T>
+int qr_blocked_max_rows()
+{
+    return kClusterMax * qb_cluster_slab_rows<T>();
+}
+
+// panels of every matrix: one CTA per panel when a 32-column panel of max_m rows fits in its shared
+// memory, else a cluster of ceil(max_m / rows_per_cta) CTAs (at most 8)
+template <typename T>
+static int qb_launch_panel(int p, int batch, int max_m, unsigned char* ws, const QbLayout& L, const QbInts& I,
+                           cudaStream_t st)
+{
+    const int one = qr_blocked_cta_rows<T>();
+    if (max_m <= one) {
+        const int ldp = (max_m > kPw ? max_m : kPw) | 1;
+        const size_t panel_smem = sizeof(T) * ((size_t)ldp * kPw + kPw + 2 * kPw * (kPw + 1));
+        if (panel_smem > 48 * 1024 &&
+            cudaFuncSetAttribute(qb_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem) !=
+                cudaSuccess)
+            return BSVD_ERR_CUDA;
+        qb_panel_kernel<T><<<batch, 256, panel_smem, st>>>(p, ws, L, I);
+        return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+    }
+    const int per = qb_cluster_slab_rows<T>();
+    const int cs = (max_m + per - 1) / per;
+    if (cs > kClusterMax) return BSVD_ERR_UNSUPPORTED;
+    const int slab = (max_m + cs - 1) / cs;
+    const size_t smem = qb_cpanel_smem<T>(slab > kPw ? slab : kPw);
+    if (cudaFuncSetAttribute(qb_panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return BSVD_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(batch * cs));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, qb_panel_cluster_kernel<T>, p, cs, ws, L, I) != cudaSuccess) return BSVD_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? BSVD_SUCCESS : BSVD_ERR_CUDA;
+}
 
 template <typename T>
 size_t block_jacobi_qr_workspace(int batch, int max_m, int max_n, int bw, int method)
@@ -399,9 +624,7 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
                            void* ws_v, size_t ws_bytes, cudaStream_t st)
 {
     const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
-    const int ldp = (mm > kPw ? mm : kPw) | 1;
-    const size_t panel_smem = sizeof(T) * ((size_t)ldp * kPw + kPw + 2 * kPw * (kPw + 1));
-    if (panel_smem > 200 * 1024) return BSVD_ERR_UNSUPPORTED;
+    if (mm > qr_blocked_max_rows<T>()) return BSVD_ERR_UNSUPPORTED;
     const QbLayout L = qb_layout<T>(batch, max_m, max_n, bw, method);
     if (ws_bytes < L.total) return BSVD_ERR_WORKSPACE;
     unsigned char* ws = static_cast<unsigned char*>(ws_v);
@@ -417,10 +640,6 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
     qb_setup_kernel<T><<<batch, 256, 0, st>>>(batch, mm, nn, (T* const*)A, M, N, LDA, (T* const*)U, LDU, (T* const*)V,
                                               LDV, ws, L, I, Pp, info);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
-    if (panel_smem > 48 * 1024 &&
-        cudaFuncSetAttribute(qb_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem) !=
-            cudaSuccess)
-        return BSVD_ERR_CUDA;
     constexpr size_t apply_smem = qb_apply_smem<T>();
     if (apply_smem > 48 * 1024 &&
         cudaFuncSetAttribute(qb_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem) !=
@@ -429,7 +648,8 @@ int launch_block_jacobi_qr(int batch, int max_m, int max_n, int bw, int method, 
     const int P = (nn + kPw - 1) / kPw;
     const int tiles = P;   // 32-column tiles of nn
     for (int p = 0; p < P; ++p) {
-        qb_panel_kernel<T><<<batch, 256, panel_smem, st>>>(p, ws, L, I);
+        const int rc = qb_launch_panel<T>(p, batch, mm, ws, L, I, st);
+        if (rc != BSVD_SUCCESS) return rc;
         if (p + 1 < P)
             qb_apply_kernel<T><<<batch * (P - p - 1), 256, apply_smem, st>>>(p, 1, P - p - 1, ws, L, I, nullptr,
                                                                               nullptr, p * kPw + kPw);
@@ -468,8 +688,6 @@ int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int
                       size_t ws_bytes, cudaStream_t st)
 {
     if (qr_blocked_max_rows<T>() < max_m) return BSVD_ERR_UNSUPPORTED;
-    const int ldp = (max_m > kPw ? max_m : kPw) | 1;
-    const size_t panel_smem = sizeof(T) * ((size_t)ldp * kPw + kPw + 2 * kPw * (kPw + 1));
     const QbLayout L = qb_layout<T>(batch, max_m, max_n, 32, 0, false);
     if (ws_bytes < L.total) return BSVD_ERR_WORKSPACE;
     unsigned char* ws = static_cast<unsigned char*>(ws_v);
@@ -480,10 +698,6 @@ int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int
     qbq_setup_kernel<T><<<batch, 256, 0, st>>>(max_m, max_n, (T* const*)A, M, N, LDA, (T* const*)Q, LDQ, (T* const*)R,
                                                LDR, ws, L, I, info);
     if (cudaGetLastError() != cudaSuccess) return BSVD_ERR_CUDA;
-    if (panel_smem > 48 * 1024 &&
-        cudaFuncSetAttribute(qb_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem) !=
-            cudaSuccess)
-        return BSVD_ERR_CUDA;
     constexpr size_t apply_smem = qb_apply_smem<T>();
     if (apply_smem > 48 * 1024 &&
         cudaFuncSetAttribute(qb_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem) !=
@@ -491,7 +705,8 @@ int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int
         return BSVD_ERR_CUDA;
     const int P = (max_n + kPw - 1) / kPw;
     for (int p = 0; p < P; ++p) {
-        qb_panel_kernel<T><<<batch, 256, panel_smem, st>>>(p, ws, L, I);
+        const int rc = qb_launch_panel<T>(p, batch, max_m, ws, L, I, st);
+        if (rc != BSVD_SUCCESS) return rc;
         if (p + 1 < P)
             qb_apply_kernel<T><<<batch * (P - p - 1), 256, apply_smem, st>>>(p, 1, P - p - 1, ws, L, I, nullptr,
                                                                               nullptr, p * kPw + kPw);
@@ -509,14 +724,6 @@ int launch_qr_blocked(int batch, int max_m, int max_n, void* const* A, const int
     return BSVD_SUCCESS;
 }
 
-// rows of the tallest matrix whose 32-column panel fits on chip (200 KiB of shared memory)
-template <typename T>
-int qr_blocked_max_rows()
-{
-    const size_t fixed = sizeof(T) * (kPw + 2 * kPw * (kPw + 1));
-    const size_t ld = (200 * 1024 - fixed) / (sizeof(T) * kPw);   // largest ld with the panel in 200 KiB
-    return (int)(ld % 2 ? ld : ld - 1);                          // ld = rows | 1
-}
 
 template size_t block_jacobi_qr_workspace<float>(int, int, int, int, int);
 template size_t block_jacobi_qr_workspace<double>(int, int, int, int, int);

@@ -120,7 +120,7 @@ def test_blocked_qr_host_checks(lib):
     _, bs = lib
     L = bs.lib()
     z = None
-    assert L.batched_qr_blocked_max_rows(0) == 1533 and L.batched_qr_blocked_max_rows(1) == 733
+    assert L.batched_qr_blocked_max_rows(0) == 11976 and L.batched_qr_blocked_max_rows(1) == 5576
     assert L.batched_qr_blocked_max_rows(3) == -1
     w1 = L.batched_qr_blocked_workspace(0, 10, 1000, 200)
     w2 = L.batched_qr_blocked_workspace(0, 20, 1000, 200)
@@ -134,4 +134,4 @@ def test_blocked_qr_host_checks(lib):
     assert L.batched_qr_blocked(0, 1, 64, 64, *args) == -5
     p = ctypes.c_void_p(8)                                                     # never dereferenced
     assert L.batched_qr_blocked(0, 1, 64, 64, p, p, p, p, z, z, z, z, p, z, 0, z) == -14   # no workspace
-    assert L.batched_qr_blocked(0, 1, 2000, 64, p, p, p, p, z, z, z, z, p, p, 0, z) == bs.ERR_UNSUPPORTED
+    assert L.batched_qr_blocked(0, 1, 12000, 64, p, p, p, p, z, z, z, z, p, p, 0, z) == bs.ERR_UNSUPPORTED

@@ -192,3 +192,20 @@ def test_block_pair_selection_is_exact(bs, method, bw, dt):
     assert torch.equal(r0[3], r1[3]) and torch.equal(r0[4], r1[4]), method
     info = r1[3].cpu().numpy()
     assert np.all((info > 0) & (info < (1 << 20))), info
+
+
+def test_block_qr_preconditioning_on_tall_matrices(bs):
+    """The block tier on R^T of a blocked QR whose panels (2600 rows) need a cluster of CTAs each:
+    sigma, orthogonality and residual against the oracle at the FP32 gate."""
+    b = gen.uniform_batch(92, 2, 2600, 96, np.float32, lambda i: np.logspace(0, -4, 96))
+    a = torch.from_numpy(b.a).cuda()
+    u, s, v, info, rots = bs.svd_block(a, block_width=32, method=QR, max_sweeps=30)
+    torch.cuda.synchronize()
+    u, s, v = _host(u, s, v)
+    info = info.cpu().numpy()
+    for i in range(b.batch):
+        assert 0 < info[i] < (1 << 20), (i, info[i])
+        a64 = b.a64(i)
+        So = O.svd(a64)[1]
+        e = svd_errors(a64, u[i].T, s[i], v[i].T, So)
+        assert max(e.values()) <= 1e-5, (i, e)

@@ -178,18 +178,36 @@ BLOCKED = [(np.float32, 1533, 96, 3, lambda i: np.logspace(0, -3, 96)),      # t
            (np.float32, 1200, 300, 2, lambda i: np.exp(-np.arange(300) / 40.0)),
            (np.float32, 700, 700, 2, lambda i: np.logspace(0, -4, 700)),      # a large square, 22 panels
            (np.float64, 733, 200, 2, lambda i: np.logspace(0, -8, 200)),
-           (np.float64, 500, 500, 2, lambda i: 10.0 ** (-8.0 * np.arange(500) / 499))]
+           (np.float64, 500, 500, 2, lambda i: 10.0 ** (-8.0 * np.arange(500) / 499)),
+           # panels taller than one CTA's shared memory: a cluster of CTAs per panel
+           (np.float32, 4096, 96, 2, lambda i: np.logspace(0, -3, 96)),             # 3 CTAs
+           (np.float32, 11976, 40, 1, lambda i: np.logspace(0, -2, 40)),            # the tallest: 8 CTAs (*)
+           (np.float32, 2000, 600, 1, lambda i: np.exp(-np.arange(600) / 80.0)),    # 2 CTAs, 19 panels
+           (np.float64, 5576, 48, 1, lambda i: np.logspace(0, -8, 48)),             # 8 CTAs
+           (np.float64, 1500, 300, 1, lambda i: 10.0 ** (-6.0 * np.arange(300) / 299))]
 
 
 @pytest.mark.parametrize("dt,m,n,nb,sig", BLOCKED)
 def test_qr_blocked_against_oracle(bs, dt, m, n, nb, sig):
     """Every matrix of the batch against the oracle's Householder QR: R and Q after sign alignment,
-    exact zeros below R's diagonal, orthogonality and residual at the gate."""
+    exact zeros below R's diagonal, orthogonality and residual at the gate.  (*) The oracle forms
+    the full m x m Q, out of reach at 11 976 rows: there the properties that hold at any size are
+    checked (R's diagonal magnitudes against the generator's spectrum's bounds included)."""
     b = gen.uniform_batch(81, nb, m, n, dt, sig)
     a = torch.from_numpy(b.a).cuda()
     q, r, info = bs.qr_blocked(a)
     torch.cuda.synchronize()
     assert np.all(info.cpu().numpy() == 0)
+    if m > 8000:
+        qh, rh = _host(q), _host(r)
+        for i in range(nb):
+            a64, qq, rr = b.a64(i), qh[i].T, rh[i].T
+            assert np.all(np.tril(rr, -1) == 0.0)
+            assert np.abs(qq.T @ qq - np.eye(n)).max() <= gate(dt)
+            assert np.linalg.norm(a64 - qq @ rr) / np.linalg.norm(a64) <= gate(dt)
+            # |det R| = prod sigma: the R factor carries A's volume
+            assert abs(np.sum(np.log(np.abs(np.diag(rr)))) - np.sum(np.log(b.sigma[i]))) <= 1e-3
+        return
     mats = [b.a64(i) for i in range(nb)]
     Qo, Ro, _ = O.qr_batch(mats)
     qh, rh = _host(q), _host(r)
@@ -261,3 +279,37 @@ def test_qr_blocked_agrees_with_the_shared_memory_kernel(bs):
     scale = float(r0.abs().max())
     assert float((r1 - r0).abs().max()) <= 64 * 6e-8 * 16 * scale
     assert float((q1 - q0).abs().max()) <= 1e-4
+
+
+def test_qr_blocked_cluster_panels_ragged(bs):
+    """Tall and short matrices in one batch whose bound needs the cluster panels: every matrix
+    against the oracle (the short ones factored by the same cluster launch)."""
+    shapes = [(3000, 33), (40, 40), (1600, 1), (12, 5), (2500, 70), (33, 32)]
+    rng = np.random.default_rng(8)
+    mats = [rng.standard_normal((m, n)) * np.logspace(0, -2, n) for m, n in shapes]
+    dev = torch.device("cuda")
+    ms = np.array([s[0] for s in shapes], np.int32)
+    ns = np.array([s[1] for s in shapes], np.int32)
+    offA = np.concatenate([[0], np.cumsum(ms.astype(np.int64) * ns + 1)[:-1]])
+    offR = np.concatenate([[0], np.cumsum(ns.astype(np.int64) * ns + 1)[:-1]])
+    flat = np.zeros(int(offA[-1] + ms[-1] * ns[-1] + 1), np.float32)
+    for mat, o in zip(mats, offA):
+        flat[o:o + mat.size] = mat.T.reshape(-1)
+    fa = torch.from_numpy(flat).to(dev)
+    fq = torch.full_like(fa, float("nan"))
+    fr = torch.full((int(offR[-1] + ns[-1] ** 2 + 1),), float("nan"), device=dev)
+    info = torch.full((len(shapes),), -7, dtype=torch.int32, device=dev)
+    A = bs.Batch.packed(fa, offA, ms, ns)
+    ws = torch.empty(bs.batched_qr_blocked_workspace(A), dtype=torch.uint8, device=dev)
+    bs.batched_qr_blocked(A, bs.Batch.packed(fq, offA, ms, ns), bs.Batch.packed(fr, offR, ns, ns), info, ws)
+    torch.cuda.synchronize()
+    fq, fr, info = fq.cpu().numpy().astype(np.float64), fr.cpu().numpy().astype(np.float64), info.cpu().numpy()
+    for b, (m, n) in enumerate(shapes):
+        assert info[b] == 0, (m, n, info[b])
+        a64 = flat[offA[b]:offA[b] + m * n].reshape(n, m).T.astype(np.float64)
+        qo, ro = O.qr(a64)
+        q = fq[offA[b]:offA[b] + m * n].reshape(n, m).T
+        r = fr[offR[b]:offR[b] + n * n].reshape(n, n).T
+        e = qr_errors(a64, q, r, qo, ro, np.float32)
+        assert e["r"] <= 1.0 and e["q"] <= 1.0 and e["tril_zero"], ((m, n), e)
+        assert e["orth_q"] <= 1e-5 and e["resid"] <= 1e-5, ((m, n), e)
