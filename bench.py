@@ -542,8 +542,9 @@ class Block512:
 
     def config(self, world):
         return {"workload": f"block512: block-Jacobi SVD (U,S,V) of {self.nb} FP32 512x512 per GPU per step, blocked "
-                            "Householder QR then GRAM block Jacobi on R^T (block width 32, pair Gram products on the "
-                            "tensor cores: TF32 hi/lo split, FP32 accumulation; updates on FP32 SIMT), U = Q V~; "
+                            "Householder QR then GRAM block Jacobi on R^T (block width and inner pair SVD by the autotuner, pair "
+                            "Gram products on the tensor cores for width 32: TF32 hi/lo split, FP32 accumulation; updates on "
+                            "FP32 SIMT), U = Q V~; "
                             "sigma log-uniform on [1e-6, 1]", "batch_per_gpu": self.nb,
                 "l2": f"inputs ({self.nb * 512 * 512 * 4 / 1e6:.0f} MB per GPU) "
                       f"{'larger' if self.nb * 512 * 512 * 4 > 129e6 else 'smaller'} than L2",
@@ -573,15 +574,20 @@ class Block512:
                                      bs.Batch.uniform(self.V, 512, k))
         self.info = torch.empty(self.nb, dtype=torch.int32, device=dev)
         self.rots = torch.empty(self.nb, dtype=torch.int64, device=dev)
-        self.ws = torch.empty(max(bs.batched_svd_block_jacobi_workspace(self.A, 32, m)
-                                  for m in (0, bs.BLOCK_QR_PRECONDITION)), dtype=torch.uint8, device=dev)
+        # block width and inner pair-SVD variant by the autotuner (block_width = 0 uses its choice)
+        from paper_1707_05141_gb300 import autotune
+        self.tuned = autotune.tune_block(self.d, method=bs.BLOCK_QR_PRECONDITION, sample=min(64, self.nb))
+        self.bw = int(self.tuned["block_width"])
+        self.ws = torch.empty(max(bs.batched_svd_block_jacobi_workspace(self.A, 0, m)
+                                  for m in (0, bs.BLOCK_QR_PRECONDITION, bs.BLOCK_SIMT_PRODUCTS)),
+                              dtype=torch.uint8, device=dev)
         self.outs = [self.S, self.U, self.V]
 
     def step(self, stream, kev=None):
         if kev is not None:
             kev[0].record(stream)
         self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
-                                         max_sweeps=20, block_width=32, method=self.bs.BLOCK_QR_PRECONDITION,
+                                         max_sweeps=20, block_width=0, method=self.bs.BLOCK_QR_PRECONDITION,
                                          stream=stream)
         if kev is not None:
             kev[1].record(stream)
@@ -603,7 +609,7 @@ class Block512:
             if kev is not None:
                 kev[0].record(st)
             self.bs.batched_svd_block_jacobi(self.A, self.Sb, self.Ub, self.Vb, self.info, self.ws, self.rots,
-                                             max_sweeps=20, block_width=32, method=method, stream=st)
+                                             max_sweeps=20, block_width=0, method=method, stream=st)
             if kev is not None:
                 kev[1].record(st)
         return step
@@ -635,17 +641,19 @@ class Block512:
     def roofline(self, kernel_ms):
         info_h = self.info.cpu().numpy()
         sweeps = np.where(info_h >= (1 << 20), info_h - (1 << 20), info_h)
-        # per pair: Gram 2 m (2bw)^2, update 2 (m + n) (2bw)^2 flops; 120 pairs per sweep; per matrix
-        # the blocked QR (4 n^3 / 3) and U = Q V~ (2 n^3)
-        pair_fl = 2 * 512 * 64 * 64 + 2 * 1024 * 64 * 64
-        fl = float(np.sum(sweeps) * 120 * pair_fl) + self.nb * (4.0 / 3.0 + 2.0) * 512 ** 3
+        # per pair: Gram 2 m (2bw)^2, update 2 (m + n) (2bw)^2 flops; nb (nb - 1) / 2 pairs per sweep
+        # (nb = 512 / bw blocks); per matrix the blocked QR (4 n^3 / 3) and U = Q V~ (2 n^3)
+        k2 = 2 * self.bw
+        nblk = 512 // self.bw
+        pair_fl = 2 * 512 * k2 * k2 + 2 * 1024 * k2 * k2
+        fl = float(np.sum(sweeps) * (nblk * (nblk - 1) // 2) * pair_fl) + self.nb * (4.0 / 3.0 + 2.0) * 512 ** 3
         achieved = fl / (kernel_ms * 1e-3) / 1e12
         return ({"kernel": "batched_svd_block_jacobi (all stages of one call)", "bound": "alu",
                  "achieved": achieved, "peak": PEAKS["fp32"]["tflops"], "unit": "TFLOP/s",
                  "frac": achieved / PEAKS["fp32"]["tflops"], "traffic": None, "ms_per_launch": kernel_ms,
                  "peak_note": PEAKS["fp32"]["note"] + "; achieved counts Gram + update flops of the pairs of "
                               "every sweep run, the blocked QR and U = Q V~"},
-                {"sweeps_max": int(np.max(sweeps)), **self.quality()})
+                {"sweeps_max": int(np.max(sweeps)), "autotune": self.tuned, **self.quality()})
 
     def cpu_sample(self, n):
         import oracle

@@ -226,6 +226,16 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
                                           int method);
 
 /*
+ * bsvd_set_block_choice -- record, for batches whose bounds fall in the same size bin as
+ * max_m x max_n (powers of two of max(m, n) and min(m, n), up to 16384), the block width (16 or 32)
+ * and the inner register variant (0: the default; k: the k-th variant of bsvd_jacobi_variants for
+ * 2bw x 2bw) that block_width = 0 selects; block_width 0 clears the entry.  Host only; the tuning
+ * of Sections 3-6 by measurement (the paper fixes bw = 32 by hand).  Returns 0 or a negative
+ * argument code.
+ */
+int bsvd_set_block_choice(int dtype, int max_m, int max_n, int block_width, int inner_variant);
+
+/*
  * batched_svd_block_jacobi -- reduced SVD by one-sided block Jacobi in global memory (Algorithm 3,
  * Section 6), for matrices too large for the register and shared-memory tiers.
  *
@@ -236,7 +246,10 @@ size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int m
  *                 |G_pq| / sqrt(G_pp G_qq) exceeds tol (tested in FP64); tol <= 0 selects
  *                 sqrt(max(m, n)) * u.  The same threshold drives the inner 2bw x 2bw Jacobi.
  *   max_sweeps    block sweeps launched (<= 0 selects 20); converged matrices skip the rest.
- *   block_width   bw = 16 or 32 columns per block (the paper uses 32, Section 6.3).
+ *   block_width   bw = 16 or 32 columns per block (the paper uses 32, Section 6.3), or 0: the
+ *                 block width and inner variant bsvd_set_block_choice recorded for the size bin
+ *                 (32 and the default inner variant when none; the workspace query resolves 0 the
+ *                 same way, so query and call must see the same table entry).
  *   method        BSVD_BLOCK_GRAM or BSVD_BLOCK_DIRECT, optionally | (k << 8) to run the inner
  *                 2bw x 2bw SVDs with the k-th register-tier variant (see bsvd_jacobi_variants).
  *                 | BSVD_BLOCK_TEST_TIMEOUT exercises the failure path (tests only; see the flag).

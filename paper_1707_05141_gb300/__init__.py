@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             L.batched_qr_blocked_max_rows.argtypes = [i]
             L.batched_svd_jacobi.restype = i
             L.batched_svd_jacobi.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, d, i, i, p, p, p]
+            L.bsvd_set_block_choice.restype = i
+            L.bsvd_set_block_choice.argtypes = [i, i, i, i, i]
             L.bsvd_jacobi_variants.restype = i
             L.bsvd_jacobi_variants.argtypes = [i, i, i, i]
             L.bsvd_jacobi_variant_desc.restype = i
@@ -137,6 +139,11 @@ def jacobi_variant_desc(dtype_code: int, max_m: int, max_n: int, k: int) -> dict
     _check("bsvd_jacobi_variant_desc", lib().bsvd_jacobi_variant_desc(dtype_code, max_m, max_n, k, d))
     return dict(zip(("slots", "parts", "rows_a", "rows_v", "ctas_per_sm", "scaled", "qr_precond", "fp64_params",
                      "carried_norms"), list(d)))
+
+
+def set_block_choice(dtype_code: int, max_m: int, max_n: int, block_width: int, inner_variant: int = 0) -> None:
+    """Record the block width and inner variant that block_width = 0 uses for this size bin."""
+    _check("bsvd_set_block_choice", lib().bsvd_set_block_choice(dtype_code, max_m, max_n, block_width, inner_variant))
 
 
 def set_jacobi_choice(dtype_code: int, max_m: int, max_n: int, tier: int) -> None:

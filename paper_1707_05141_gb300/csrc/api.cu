@@ -25,6 +25,31 @@ int size_bin(int x)
     return b;
 }
 
+// Block-tier table: for each (dtype, bin of max(m, n), bin of min(m, n)) up to 16384 the block width
+// | inner register variant << 8 that block_width = 0 selects.  0 = not tuned (width 32, default
+// inner variant).
+constexpr int kBlockBins = 15;   // sizes <= 1, 2, 4, ..., 16384
+std::atomic<int> g_block_choice[2][kBlockBins][kBlockBins];
+
+int block_bin(int x)
+{
+    int b = 0;
+    while ((1 << b) < x && b < kBlockBins - 1) ++b;
+    return b;
+}
+
+// block_width 0: the recorded choice for this size bin (its inner variant joins `method` unless the
+// caller named one); returns the block width to use
+int resolve_block_choice(int dtype, int max_m, int max_n, int block_width, int* method)
+{
+    if (block_width != 0) return block_width;
+    const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+    const int c = g_block_choice[dtype == BSVD_F64][block_bin(mm)][block_bin(nn)].load(std::memory_order_relaxed);
+    if (c == 0) return 32;
+    if (((*method >> 8) & 0xff) == 0) *method |= (c >> 8 & 0xff) << 8;
+    return c & 0xff;
+}
+
 template <typename T>
 int svd_dispatch(int batch, int max_m, int max_n, int tier, void* const* dA, const int* d_m, const int* d_n,
                  const int* d_lda, void* const* dS, void* const* dU, const int* d_ldu, void* const* dV, const int* d_ldv,
@@ -195,9 +220,23 @@ int bsvd_set_jacobi_choice(int dtype, int max_m, int max_n, int tier)
     return BSVD_SUCCESS;
 }
 
+int bsvd_set_block_choice(int dtype, int max_m, int max_n, int block_width, int inner_variant)
+{
+    if (dtype != BSVD_F32 && dtype != BSVD_F64) return -1;
+    if (max_m < 0 || max_m > 16384) return -2;
+    if (max_n < 0 || max_n > 16384) return -3;
+    if (block_width != 0 && block_width != 16 && block_width != 32) return -4;
+    if (inner_variant < 0 || inner_variant > 255 || (block_width == 0 && inner_variant != 0)) return -5;
+    const int mm = max_m > max_n ? max_m : max_n, nn = max_m > max_n ? max_n : max_m;
+    g_block_choice[dtype == BSVD_F64][block_bin(mm)][block_bin(nn)].store(
+        block_width == 0 ? 0 : (block_width | inner_variant << 8), std::memory_order_relaxed);
+    return BSVD_SUCCESS;
+}
+
 size_t batched_svd_block_jacobi_workspace(int dtype, int batch, int max_m, int max_n, int block_width, int method)
 {
     if ((dtype != BSVD_F32 && dtype != BSVD_F64) || batch < 0 || max_m < 0 || max_n < 0) return 0;
+    block_width = resolve_block_choice(dtype, max_m, max_n, block_width, &method);
     const int base = method & 0xff;
     if ((block_width != 16 && block_width != 32) || (base != BSVD_BLOCK_GRAM && base != BSVD_BLOCK_DIRECT)) return 0;
     const int m2 = base | (method & BSVD_BLOCK_QR_PRECONDITION);
@@ -226,7 +265,8 @@ int batched_svd_block_jacobi(int dtype, int batch, int max_m, int max_n, void* c
     if (!dV) return -12;
     if (!d_ldv) return -13;
     if (!(tol == tol)) return -14;
-    if (block_width != 16 && block_width != 32) return -16;
+    if (block_width != 0 && block_width != 16 && block_width != 32) return -16;
+    block_width = resolve_block_choice(dtype, max_m, max_n, block_width, &method);
     if ((method & 0xff) != BSVD_BLOCK_GRAM && (method & 0xff) != BSVD_BLOCK_DIRECT) return -17;
     // method bits: 0-7 method, 8-15 inner variant, 16 SIMT Gram products, 17 failure-path test,
     // 18 QR preconditioning, 19 re-test every pair, 24-30 inner sweep cap

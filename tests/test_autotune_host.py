@@ -41,3 +41,33 @@ def test_apply_cache_only_for_this_gpu_model(tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "set_jacobi_choice", lambda *a: calls.append(a))
     assert autotune.apply_cache() == 1
     assert calls == [(bs.F32, 64, 32, 1 | (3 << 8))]
+
+
+def test_block_choice_arguments_and_cache_keys(tmp_path, monkeypatch):
+    """The block tier's table (host checks only) and its keys: bins of max(m, n), min(m, n) up to
+    16384 and the base method; a cached block entry is re-applied for the same GPU model."""
+    L = bs.lib()
+    assert L.bsvd_set_block_choice(0, 512, 512, 32, 10) == 0
+    assert L.bsvd_set_block_choice(0, 512, 512, 0, 0) == 0                 # clears the entry
+    assert L.bsvd_set_block_choice(2, 512, 512, 32, 0) == -1
+    assert L.bsvd_set_block_choice(0, 20000, 512, 32, 0) == -2
+    assert L.bsvd_set_block_choice(0, 512, 512, 24, 0) == -4
+    assert L.bsvd_set_block_choice(0, 512, 512, 0, 3) == -5
+    assert autotune._block_key("GB300", bs.F32, 512, 300, bs.BLOCK_GRAM | bs.BLOCK_QR_PRECONDITION) == \
+        "block|GB300|f32|9|9|0"
+    assert autotune._block_key("GB300", bs.F64, 4000, 20000, bs.BLOCK_DIRECT) == "block|GB300|f64|14|12|1"
+    c = autotune.block_candidates(bs.F32, bs.BLOCK_GRAM)
+    assert [w for w, _ in c] == [16, 16, 32, 32] and c[0][1] == 0 and c[2][1] == 0
+    for w, k in c[1::2]:
+        d = bs.jacobi_variant_desc(bs.F32, 2 * w, 2 * w, k)
+        assert d["qr_precond"] and d["carried_norms"]
+    assert autotune.block_candidates(bs.F32, bs.BLOCK_DIRECT) == [(16, 0), (32, 0)]
+    path = tmp_path / "autotune.json"
+    path.write_text(json.dumps({"block|GB300|f32|9|9|0": {"block_width": 16, "inner_variant": 13},
+                                "block|OTHER|f32|9|9|0": {"block_width": 32, "inner_variant": 0}}))
+    monkeypatch.setattr(autotune, "CACHE", str(path))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda device=None: "GB300")
+    calls = []
+    monkeypatch.setattr(autotune, "set_block_choice", lambda *a: calls.append(a))
+    assert autotune.apply_cache() == 1
+    assert calls == [(bs.F32, 512, 512, 16, 13)]

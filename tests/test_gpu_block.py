@@ -209,3 +209,25 @@ def test_block_qr_preconditioning_on_tall_matrices(bs):
         So = O.svd(a64)[1]
         e = svd_errors(a64, u[i].T, s[i], v[i].T, So)
         assert max(e.values()) <= 1e-5, (i, e)
+
+
+def test_block_width_autotuned(bs, tmp_path, monkeypatch):
+    """The autotuner times both block widths (and, for GRAM, the inner register variant) and records
+    the fastest; block_width = 0 then runs that choice: the same result bit for bit as naming it."""
+    from paper_1707_05141_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    b = gen.uniform_batch(93, 8, 256, 256, np.float32, lambda i: np.logspace(0, -4, 256))
+    a = torch.from_numpy(b.a).cuda()
+    rec = autotune.tune_block(a, method=QR, force=True)
+    try:
+        assert rec["block_width"] in (16, 32) and len(rec["all_ms"]) == 4
+        r0 = bs.svd_block(a, block_width=0, method=QR, max_sweeps=30)
+        r1 = bs.svd_block(a, block_width=rec["block_width"], method=QR | (rec["inner_variant"] << 8),
+                          max_sweeps=30)
+        torch.cuda.synchronize()
+        for x, y in zip(r0[:3], r1[:3]):
+            assert torch.equal(_bits(x), _bits(y))
+        assert torch.equal(r0[3], r1[3])
+        assert autotune.tune_block(a, method=QR)["block_width"] == rec["block_width"]   # from the cache
+    finally:
+        bs.set_block_choice(bs.F32, 256, 256, 0)
