@@ -389,39 +389,116 @@ __global__ void __launch_bounds__(256) bj_pack_kernel(int batch, int npairs, int
 // only to ~25 u; V multiplies ~150 of them per column, so their errors would add up.  After the
 // step ||X^T X - I|| is at the rounding level of one product.
 // ------------------------------------------------------------------------------------------------
+// BI consecutive shared-memory values at an address aligned to their size, in the widest loads
+template <typename T, int BI>
+__device__ __forceinline__ void ld_shared_run(const T* p, T (&v)[BI])
+{
+    constexpr int bytes = BI * (int)sizeof(T);
+    if constexpr (bytes % 16 == 0) {
+#pragma unroll
+        for (int i = 0; i < bytes / 16; ++i) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 x = reinterpret_cast<const float4*>(p)[i];
+                v[4 * i] = x.x;
+                v[4 * i + 1] = x.y;
+                v[4 * i + 2] = x.z;
+                v[4 * i + 3] = x.w;
+            } else {
+                const double2 x = reinterpret_cast<const double2*>(p)[i];
+                v[2 * i] = x.x;
+                v[2 * i + 1] = x.y;
+            }
+        }
+    } else if constexpr (bytes == 8 && sizeof(T) == 4) {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < BI; ++i) v[i] = p[i];
+    }
+}
+
+// shared memory of the polish: X twice (row-major and column-major) and E, rows padded to 16 bytes
+template <typename T, int K2>
+constexpr size_t bj_polish_smem() { return 3 * sizeof(T) * (size_t)K2 * (K2 + 16 / sizeof(T)); }
+
 template <typename T, int K2>
 __device__ __forceinline__ void bj_polish_item(T* X, unsigned char* pol_sm)
 {
-    constexpr int TPO = (K2 * K2) / 256;
-    T(*xs)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm);                                  // X(r, c) at [c][r]
-    T(*es)[K2 + 1] = reinterpret_cast<T(*)[K2 + 1]>(pol_sm + sizeof(T) * K2 * (K2 + 1));      // X^T X - I
-    for (int e = threadIdx.x; e < K2 * K2; e += blockDim.x) xs[e / K2][e % K2] = X[e];
+    constexpr int LD = K2 + 16 / (int)sizeof(T);   // padded row (16-byte multiple)
+    constexpr int BI = K2 / 16;                     // each thread: a BI x BI block of the 16 x 16 grid
+    constexpr int VE = 16 / (int)sizeof(T);         // elements per 16-byte global load
+    T* xr = reinterpret_cast<T*>(pol_sm);           // xr[k * LD + c] = X(k, c) (row-major)
+    T* xc = xr + K2 * LD;                           // xc[k * LD + r] = X(r, k) (column-major)
+    T* es = xc + K2 * LD;                           // es[k * LD + c] = E(k, c), E = X^T X - I
+    const int tid = threadIdx.x;
+    // X in 16-byte loads, all in flight (X is K2 x K2 column-major, contiguous, 256-byte aligned)
+#pragma unroll
+    for (int q = 0; q < (K2 * K2) / (VE * 256); ++q) {
+        const int e = tid + 256 * q;
+        const int c = e / (K2 / VE), r = (e - c * (K2 / VE)) * VE;
+        T v[VE];
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = reinterpret_cast<const float4*>(X)[e];
+            v[0] = x.x;
+            v[1] = x.y;
+            v[2] = x.z;
+            v[3] = x.w;
+        } else {
+            const double2 x = reinterpret_cast<const double2*>(X)[e];
+            v[0] = x.x;
+            v[1] = x.y;
+        }
+#pragma unroll
+        for (int i = 0; i < VE; ++i) {
+            xc[c * LD + r + i] = v[i];
+            xr[(r + i) * LD + c] = v[i];
+        }
+    }
     __syncthreads();
-    const int o0 = threadIdx.x * TPO;
-    const int oc = o0 / K2, or0 = o0 % K2;
-    T acc[TPO];
+    const int i0 = (tid & 15) * BI, j0 = (tid >> 4) * BI;
+    T acc[BI][BI];
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+    for (int i = 0; i < BI; ++i)
+#pragma unroll
+        for (int j = 0; j < BI; ++j) acc[i][j] = T(0);
+    // E(i, j) = sum_k X(k, i) X(k, j) - [i == j]
+#pragma unroll 4
     for (int k = 0; k < K2; ++k) {
-        const T y = xs[oc][k];
+        T a[BI], bv[BI];
+        ld_shared_run<T, BI>(xr + k * LD + i0, a);
+        ld_shared_run<T, BI>(xr + k * LD + j0, bv);
 #pragma unroll
-        for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[or0 + q][k], y, acc[q]);  // (X^T X)(or0+q, oc)
+        for (int i = 0; i < BI; ++i)
+#pragma unroll
+            for (int j = 0; j < BI; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) es[oc][or0 + q] = acc[q] - (or0 + q == oc ? T(1) : T(0));
+    for (int i = 0; i < BI; ++i)
+#pragma unroll
+        for (int j = 0; j < BI; ++j) es[(i0 + i) * LD + j0 + j] = acc[i][j] - (i0 + i == j0 + j ? T(1) : T(0));
     __syncthreads();
-    // X(r, c) -= 0.5 * sum_k X(r, k) E(k, c)
+    // X(r, c) <- X(r, c) - 0.5 sum_k X(r, k) E(k, c), rows i0.., columns j0..
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) acc[q] = T(0);
+    for (int i = 0; i < BI; ++i)
+#pragma unroll
+        for (int j = 0; j < BI; ++j) acc[i][j] = T(0);
+#pragma unroll 4
     for (int k = 0; k < K2; ++k) {
-        const T e = es[oc][k];
+        T a[BI], ev[BI];
+        ld_shared_run<T, BI>(xc + k * LD + i0, a);
+        ld_shared_run<T, BI>(es + k * LD + j0, ev);
 #pragma unroll
-        for (int q = 0; q < TPO; ++q) acc[q] = fma(xs[k][or0 + q], e, acc[q]);
+        for (int i = 0; i < BI; ++i)
+#pragma unroll
+            for (int j = 0; j < BI; ++j) acc[i][j] = fma(a[i], ev[j], acc[i][j]);
     }
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) acc[q] = xs[oc][or0 + q] - T(0.5) * acc[q];
+    for (int j = 0; j < BI; ++j)
 #pragma unroll
-    for (int q = 0; q < TPO; ++q) X[(size_t)oc * K2 + or0 + q] = acc[q];
+        for (int i = 0; i < BI; ++i)
+            X[(size_t)(j0 + j) * K2 + i0 + i] = xc[(j0 + j) * LD + i0 + i] - T(0.5) * acc[i][j];
     __syncthreads();  // the shared buffers are reused by the next item
 }
 
@@ -521,26 +598,53 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
     const T* Sv = reinterpret_cast<T* const*>(ws + L.off_pS)[it];
     const bool useUR = direct && !onV;
     const int tid = threadIdx.x;
-    for (int e = tid; e < K2 * K2; e += 256) {
+    // source tile, k-major: column kk of the pair (or of the packed Q), rows r0 .. r0 + 127.  Where
+    // the columns are 16-byte aligned every thread has all its 16-byte copies in flight at once
+    // (cp.async, rows past the matrix zero-filled), so the tile arrives in about one memory latency
+    const T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
+    const int ldp = mm > K2 ? mm : K2;
+    const T* sb = useUR ? P : dstM;
+    const int lds = useUR ? ldp : ldd;
+    constexpr int VE = 16 / (int)sizeof(T);    // elements per 16-byte copy
+    constexpr int CPC = kUpdRows / VE;         // copies per column
+    if ((reinterpret_cast<uintptr_t>(sb) & 15) == 0 && (lds % VE) == 0) {
+#pragma unroll
+        for (int q = 0; q < (K2 * CPC) / 256; ++q) {
+            const int e = tid + 256 * q;
+            const int kk = e / CPC, r = (e - kk * CPC) * VE;
+            const int col = useUR ? kk : bj_col(bi, bj, bw, kk, nn);
+            int valid = col >= 0 ? rows - (r0 + r) : 0;
+            valid = valid < 0 ? 0 : (valid > VE ? VE : valid);
+            const T* src = valid > 0 ? sb + (size_t)col * lds + r0 + r : sb;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(As + kk * LDA + r);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                         "r"(valid * (int)sizeof(T))
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    } else {
+        for (int e = tid; e < K2 * kUpdRows; e += 256) {
+            const int kk = e / kUpdRows, r = e - kk * kUpdRows;
+            T v = T(0);
+            if (r0 + r < rows) {
+                if (useUR) {
+                    v = P[(size_t)kk * ldp + r0 + r];
+                } else {
+                    const int col = bj_col(bi, bj, bw, kk, nn);
+                    if (col >= 0) v = dstM[(size_t)col * ldd + r0 + r];
+                }
+            }
+            As[kk * LDA + r] = v;
+        }
+    }
+    // the multiplier, transposed into Bs (its loads issued together, then stored)
+#pragma unroll
+    for (int q = 0; q < (K2 * K2) / 256; ++q) {
+        const int e = tid + 256 * q;
         const int n = e / K2, kk = e - n * K2;  // consecutive threads: consecutive k of column n
         Bs[kk * K2 + n] = useUR ? URv[e] * Sv[n] : Xv[e];
     }
-    // source tile, k-major: column kk of the pair (or of the packed Q), rows r0 .. r0 + 127
-    const T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
-    const int ldp = mm > K2 ? mm : K2;
-    for (int e = tid; e < K2 * kUpdRows; e += 256) {
-        const int kk = e / kUpdRows, r = e - kk * kUpdRows;
-        T v = T(0);
-        if (r0 + r < rows) {
-            if (useUR) {
-                v = P[(size_t)kk * ldp + r0 + r];
-            } else {
-                const int col = bj_col(bi, bj, bw, kk, nn);
-                if (col >= 0) v = dstM[(size_t)col * ldd + r0 + r];
-            }
-        }
-        As[kk * LDA + r] = v;
-    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     const int tx = tid & 31, ty = tid >> 5;       // rows 4 tx .. 4 tx + 3, columns NC ty .. NC ty + NC - 1
     T acc[4][NC];
@@ -1096,7 +1200,7 @@ static int run_block(int batch, int max_m, int max_n, void* const* A, const int*
                                                      (int)upd_smem) != cudaSuccess)
         return BSVD_ERR_CUDA;
     const int sweeps = max_sweeps > 0 ? max_sweeps : 20;
-    const size_t polish_smem = 2 * sizeof(T) * K2 * (K2 + 1);
+    const size_t polish_smem = bj_polish_smem<T, K2>();
     if (polish_smem > 48 * 1024 && cudaFuncSetAttribute(bj_polish_kernel<T, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)polish_smem) != cudaSuccess)
         return BSVD_ERR_CUDA;
