@@ -265,10 +265,20 @@ __device__ __forceinline__ void bj_gram_item(int it, int batch, int npairs, int 
 #pragma unroll
     for (int q = 0; q < TPO; ++q) acc[q] = T(0);
     for (int r0 = 0; r0 < mm; r0 += RC) {
-        for (int e = tid; e < K2 * RC; e += 256) {
+        // the thread's loads of the chunk in flight together, then its shared stores
+        constexpr int PL = (K2 * RC) / 256;
+        T xl[PL];
+#pragma unroll
+        for (int q = 0; q < PL; ++q) {
+            const int e = tid + 256 * q;
             const int c = e / RC, r = e % RC;
             const int col = bj_col(bi, bj, bw, c, nn);
-            xs[c][r] = (col >= 0 && r0 + r < mm) ? W[(size_t)col * ldw + r0 + r] : T(0);
+            xl[q] = (col >= 0 && r0 + r < mm) ? W[(size_t)col * ldw + r0 + r] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < PL; ++q) {
+            const int e = tid + 256 * q;
+            xs[e / RC][e % RC] = xl[q];
         }
         __syncthreads();
 #pragma unroll 4

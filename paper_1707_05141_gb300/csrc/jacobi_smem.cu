@@ -64,15 +64,38 @@ __global__ void __launch_bounds__(80 * G > 1024 ? 1024 : 80 * G) jacobi_smem_ker
 
         // ---- load W (coalesced along columns of A), zero the padding column, V = I ----
         const T* a = A[b];
-        if (!tr) {
-            for (int e = tid; e < mm * nn; e += nthreads) {
-                const int j = e / mm, i = e - j * mm;
-                W[j * ldw + i] = a[(size_t)j * lda + i];
+        // kRun loads per thread in flight before their stores (a shared store between two global
+        // loads would make each load wait for the previous one's data)
+        constexpr int kRun = 8;
+        const int tot = mm * nn;
+        for (int e0 = 0; e0 < tot; e0 += kRun * nthreads) {
+            T x[kRun];
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) {
+                const int e = e0 + tid + u * nthreads;
+                x[u] = T(0);
+                if (e < tot) {
+                    if (!tr) {
+                        const int j = e / mm, i = e - j * mm;
+                        x[u] = a[(size_t)j * lda + i];
+                    } else {   // W(i, j) = A(j, i): read A by columns
+                        const int i = e / nn, j = e - i * nn;
+                        x[u] = a[(size_t)i * lda + j];
+                    }
+                }
             }
-        } else {
-            for (int e = tid; e < mm * nn; e += nthreads) {  // W(i, j) = A(j, i): read A by columns
-                const int i = e / nn, j = e - i * nn;
-                W[j * ldw + i] = a[(size_t)i * lda + j];
+#pragma unroll
+            for (int u = 0; u < kRun; ++u) {
+                const int e = e0 + tid + u * nthreads;
+                if (e < tot) {
+                    if (!tr) {
+                        const int j = e / mm, i = e - j * mm;
+                        W[j * ldw + i] = x[u];
+                    } else {
+                        const int i = e / nn, j = e - i * nn;
+                        W[j * ldw + i] = x[u];
+                    }
+                }
             }
         }
         if (np != nn)

@@ -47,20 +47,46 @@ __global__ void qr_kernel(int batch, int max_m, int max_n, T* const* A, const in
         if (n == 0) continue;
         const T* a = A[b];
         int nonfinite = 0;  // a NaN or an infinity in A (the factorisation would take a NaN norm for 0)
+        // each lane loads kLoadRun elements of a column into registers before storing any of them,
+        // so that their global loads are in flight together (a store to shared memory between two
+        // loads would make each load wait for the previous one's data)
+        constexpr int kLoadRun = 8;
         if (!at) {
             for (int j = warp; j < n; j += nwarps)
-                for (int i = lane; i < m; i += 32) {
-                    const T x = a[(size_t)j * lda + i];
-                    nonfinite |= !isfinite(x);
-                    S[j * ld + i] = x;
+                for (int i0 = 0; i0 < m; i0 += 32 * kLoadRun) {
+                    T x[kLoadRun];
+#pragma unroll
+                    for (int u = 0; u < kLoadRun; ++u) {
+                        const int i = i0 + lane + 32 * u;
+                        x[u] = i < m ? a[(size_t)j * lda + i] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLoadRun; ++u) {
+                        const int i = i0 + lane + 32 * u;
+                        if (i < m) {
+                            nonfinite |= !isfinite(x[u]);
+                            S[j * ld + i] = x[u];
+                        }
+                    }
                 }
         } else {
             // S(i, j) = A(j, i): row i of S is column i of the stored matrix (coalesced reads)
             for (int i = warp; i < m; i += nwarps)
-                for (int j = lane; j < n; j += 32) {
-                    const T x = a[(size_t)i * lda + j];
-                    nonfinite |= !isfinite(x);
-                    S[j * ld + i] = x;
+                for (int j0 = 0; j0 < n; j0 += 32 * kLoadRun) {
+                    T x[kLoadRun];
+#pragma unroll
+                    for (int u = 0; u < kLoadRun; ++u) {
+                        const int j = j0 + lane + 32 * u;
+                        x[u] = j < n ? a[(size_t)i * lda + j] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLoadRun; ++u) {
+                        const int j = j0 + lane + 32 * u;
+                        if (j < n) {
+                            nonfinite |= !isfinite(x[u]);
+                            S[j * ld + i] = x[u];
+                        }
+                    }
                 }
         }
         if (__syncthreads_or(nonfinite) && tid == 0) info[b] = BSVD_INFO_NONFINITE;

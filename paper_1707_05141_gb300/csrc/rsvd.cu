@@ -213,8 +213,14 @@ __device__ __forceinline__ void gemm_tile(int b, int tm, int tn, T* const* A, co
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     for (int k0 = 0; k0 < Kb; k0 += BK) {
-        // A tile: op(A)(m0 + i, k0 + kk)
-        for (int e = tid; e < BM * BK; e += 256) {
+        // A tile: op(A)(m0 + i, k0 + kk), and the B tile B(k0 + kk, n0 + j): each thread's global
+        // loads are issued together before any of its shared stores (a store between two loads
+        // would make each load wait for the previous one's data)
+        constexpr int PA = (BM * BK) / 256, PB = (BK * BN) / 256;
+        T xa[PA], xb[PB];
+#pragma unroll
+        for (int q = 0; q < PA; ++q) {
+            const int e = tid + 256 * q;
             int i, kk;
             if (!TRANS_A) {
                 i = e % BM;
@@ -224,16 +230,28 @@ __device__ __forceinline__ void gemm_tile(int b, int tm, int tn, T* const* A, co
                 i = e / BK;   // consecutive threads walk down a column of A (= a row of A^T)
             }
             const int gi = m0 + i, gk = k0 + kk;
-            T v = T(0);
-            if (gi < Mb && gk < Kb) v = TRANS_A ? a[(size_t)gi * lda + gk] : a[(size_t)gk * lda + gi];
-            As[kk][i] = v;
+            xa[q] = (gi < Mb && gk < Kb) ? (TRANS_A ? a[(size_t)gi * lda + gk] : a[(size_t)gk * lda + gi]) : T(0);
         }
-        // B tile: B(k0 + kk, n0 + j)
         if (!OMEGA) {
-            for (int e = tid; e < BK * BN; e += 256) {
+#pragma unroll
+            for (int q = 0; q < PB; ++q) {
+                const int e = tid + 256 * q;
                 const int kk = e % BK, j = e / BK;
                 const int gk = k0 + kk, gj = n0 + j;
-                Bs[kk][j] = (gk < Kb && gj < Nb) ? bm[(size_t)gj * ldb + gk] : T(0);
+                xb[q] = (gk < Kb && gj < Nb) ? bm[(size_t)gj * ldb + gk] : T(0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PA; ++q) {
+            const int e = tid + 256 * q;
+            const int i = !TRANS_A ? e % BM : e / BK, kk = !TRANS_A ? e / BM : e % BK;
+            As[kk][i] = xa[q];
+        }
+        if (!OMEGA) {
+#pragma unroll
+            for (int q = 0; q < PB; ++q) {
+                const int e = tid + 256 * q;
+                Bs[e % BK][e / BK] = xb[q];
             }
         } else {
             // 4 rows per Philox call: BK / 4 = 4 groups x 64 columns = 256 calls, one per thread
