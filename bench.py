@@ -88,9 +88,9 @@ TRAFFIC = {
     # jacobi_reg_kernel tier 0xa01, 10 000 64x64 matrices: 164.61 MB read + 277.57 MB written, per
     # 20 000-matrix launch (profiles/jacobi_reg_qr_svd64_qr128.md)
     "jacobi_reg:657c5a9dca399a6b": 2 * (164.607744e6 + 277.571072e6),
-    # qr_warp_kernel<float, 128, 1>, 10 000 128x32 matrices: 164.69 MB read + 146.98 MB written, per
-    # 20 000-matrix launch
-    "qr:e67df0692f0a080a": 2 * (164.692224e6 + 146.980608e6),
+    # qr_warp_kernel<float, 128, 1>, 10 000 128x32 matrices: 164.79 MB read + 146.25 MB written, per
+    # 20 000-matrix launch (re-captured after the CTA QR kernel's load phase changed in the same file)
+    "qr:228caeb56544bd00": 2 * (164.788992e6 + 146.252800e6),
 }
 
 
@@ -1057,10 +1057,12 @@ WORKLOADS = {c.name: c for c in (SvdQr64, Fp64_32, Block512, RsvdUneven, Hmatrix
 # harness
 # ----------------------------------------------------------------------------------------------
 
-def time_arm(step, stream, steps, local_rank, world, dev, flush=None):
+def time_arm(step, stream, steps, local_rank, world, dev, flush=None, profile=False):
     """Times exactly `steps` calls of step(stream, events) on `stream` with CUDA events, between a
     barrier and a synchronize on both sides, with the SM clocks sampled meanwhile.  With `flush` (a
     buffer larger than L2) L2 is overwritten before every step, outside that step's own events.
+    With `profile` the region is bracketed by cudaProfilerStart/Stop, so that a profiler started
+    with profiling off (ncu --profile-from-start off) records exactly the timed steps.
     Returns the per-step time (max over ranks), the mean time between the events the step records
     around its dominant call, and the clock record."""
     import torch
@@ -1070,6 +1072,8 @@ def time_arm(step, stream, steps, local_rank, world, dev, flush=None):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.start()
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.time()
     t0e.record(stream)
@@ -1086,6 +1090,8 @@ def time_arm(step, stream, steps, local_rank, world, dev, flush=None):
         kev.append(ev)
     t1e.record(stream)
     torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.stop()
     wall1 = time.time()
     if world > 1:
         torch.distributed.barrier()
@@ -1114,7 +1120,7 @@ def run_ours(W, args, rank, world, local_rank):
     # a batch smaller than L2 is evicted before every timed step by writing a buffer larger than L2
     # (256 MB against 129 MB); each step then has its own events, which exclude the flush
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if getattr(W, "flush_l2", False) else None
-    t = time_arm(W.step, stream, args.steps, local_rank, world, dev, flush)
+    t = time_arm(W.step, stream, args.steps, local_rank, world, dev, flush, profile=args.profile_timed)
     ms_step, kernel_ms, ck = t["ms_step"], t["kernel_ms"], t["clocks"]
     roof, detail = W.roofline(kernel_ms)
 
@@ -1220,6 +1226,8 @@ def main():
                     help="chunks of the host entries' end-to-end run whose copies overlap the computation")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0: per-workload default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="bracket the main timed steps by cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     name = args.workload or "svd64_qr128"
