@@ -145,18 +145,21 @@ def _block_key(gpu: str, code: int, m: int, n: int, method: int) -> str:
 
 def block_candidates(code: int, method: int):
     """(block width, inner variant) pairs: both widths with the default inner SVD and, for GRAM, the
-    QR-preconditioned register variant with carried column norms for the 2bw x 2bw Gram matrices."""
+    register variants with carried column norms for the 2bw x 2bw Gram matrices, QR-preconditioned
+    (X = its U) and plain (X = its V, no QR of G: cheaper per visit, fewer sweeps' worth of
+    progress in the capped inner SVD)."""
     out = []
     for bw in (16, 32):
         out.append((bw, 0))
         if (method & 0xff) == BLOCK_GRAM:
             k2 = 2 * bw
             nv = jacobi_variants(code, k2, k2, TIER_REGISTER)
-            for k in range(1, nv + 1):
-                d = jacobi_variant_desc(code, k2, k2, k)
-                if d["qr_precond"] and d["carried_norms"]:
-                    out.append((bw, k))
-                    break
+            for pre in (1, 0):
+                for k in range(1, nv + 1):
+                    d = jacobi_variant_desc(code, k2, k2, k)
+                    if d["qr_precond"] == pre and d["carried_norms"]:
+                        out.append((bw, k))
+                        break
     return out
 
 

@@ -57,10 +57,10 @@ def test_block_choice_arguments_and_cache_keys(tmp_path, monkeypatch):
         "block|GB300|f32|9|9|0"
     assert autotune._block_key("GB300", bs.F64, 4000, 20000, bs.BLOCK_DIRECT) == "block|GB300|f64|14|12|1"
     c = autotune.block_candidates(bs.F32, bs.BLOCK_GRAM)
-    assert [w for w, _ in c] == [16, 16, 32, 32] and c[0][1] == 0 and c[2][1] == 0
-    for w, k in c[1::2]:
+    assert [w for w, _ in c] == [16, 16, 16, 32, 32, 32] and c[0][1] == 0 and c[3][1] == 0
+    for (w, k), pre in zip(c[1:3] + c[4:6], (1, 0, 1, 0)):
         d = bs.jacobi_variant_desc(bs.F32, 2 * w, 2 * w, k)
-        assert d["qr_precond"] and d["carried_norms"]
+        assert d["qr_precond"] == pre and d["carried_norms"]
     assert autotune.block_candidates(bs.F32, bs.BLOCK_DIRECT) == [(16, 0), (32, 0)]
     path = tmp_path / "autotune.json"
     path.write_text(json.dumps({"block|GB300|f32|9|9|0": {"block_width": 16, "inner_variant": 13},

@@ -220,7 +220,7 @@ def test_block_width_autotuned(bs, tmp_path, monkeypatch):
     a = torch.from_numpy(b.a).cuda()
     rec = autotune.tune_block(a, method=QR, force=True)
     try:
-        assert rec["block_width"] in (16, 32) and len(rec["all_ms"]) == 4
+        assert rec["block_width"] in (16, 32) and len(rec["all_ms"]) == 6
         r0 = bs.svd_block(a, block_width=0, method=QR, max_sweeps=30)
         r1 = bs.svd_block(a, block_width=rec["block_width"], method=QR | (rec["inner_variant"] << 8),
                           max_sweeps=30)
@@ -231,3 +231,21 @@ def test_block_width_autotuned(bs, tmp_path, monkeypatch):
         assert autotune.tune_block(a, method=QR)["block_width"] == rec["block_width"]   # from the cache
     finally:
         bs.set_block_choice(bs.F32, 256, 256, 0)
+
+
+def test_block_512_plain_inner_variant(bs, w2):
+    """GRAM with the inner 64 x 64 SVDs on the plain carried-norm register variant (X = its V, no
+    QR of G; the autotuner's choice on this GPU), on R^T of the blocked QR: every gate at 1e-5."""
+    b, mats, So = w2
+    k = next(k for k in range(1, bs.jacobi_variants(bs.F32, 64, 64, bs.TIER_REGISTER) + 1)
+             if bs.jacobi_variant_desc(bs.F32, 64, 64, k)["carried_norms"]
+             and not bs.jacobi_variant_desc(bs.F32, 64, 64, k)["qr_precond"])
+    a = torch.from_numpy(b.a).cuda()
+    u, s, v, info, rots = bs.svd_block(a, block_width=32, method=QR | (k << 8), max_sweeps=30)
+    torch.cuda.synchronize()
+    u, s, v = _host(u, s, v)
+    info = info.cpu().numpy()
+    for i in range(b.batch):
+        assert 0 < info[i] < (1 << 20), (i, info[i])
+        e = svd_errors(mats[i], u[i].T, s[i], v[i].T, So[i])
+        assert max(e.values()) <= 1e-5, (i, e)
