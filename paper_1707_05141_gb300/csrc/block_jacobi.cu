@@ -571,10 +571,15 @@ __device__ __forceinline__ void ld_shared_vec(const T* p, T (&v)[V])
 template <int K2>
 constexpr int bj_upd_cols() { return K2 / 8; }  // output columns per thread
 
+// the multiplier's rows padded by 16 bytes: its transposed stores (consecutive threads, consecutive
+// rows) then fall in 8 banks instead of one
+template <typename T, int K2>
+constexpr int bj_upd_ldb() { return K2 + 16 / (int)sizeof(T); }
+
 template <typename T, int K2>
 constexpr size_t bj_update_smem()
 {
-    return sizeof(T) * ((size_t)K2 * (kUpdRows + 4) + (size_t)K2 * K2);
+    return sizeof(T) * ((size_t)K2 * (kUpdRows + 4) + (size_t)K2 * bj_upd_ldb<T, K2>());
 }
 
 template <typename T, int K2>
@@ -586,7 +591,8 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
     constexpr int LDA = kUpdRows + 4;            // padded row length of the k-major source tile
     constexpr int NC = bj_upd_cols<K2>();        // output columns per thread (8 for K2 = 64)
     T* As = reinterpret_cast<T*>(upd_sm);        // As[k * LDA + r] = src(r0 + r, k)
-    T* Bs = As + (size_t)K2 * LDA;               // Bs[k * K2 + n] = multiplier(k, n)
+    constexpr int LDB = bj_upd_ldb<T, K2>();
+    T* Bs = As + (size_t)K2 * LDA;               // Bs[k * LDB + n] = multiplier(k, n)
     const int b = it / npairs, k = it - b * npairs;
     BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
     const int mm = st->mm, nn = st->nn, nblk = st->nblk;
@@ -652,7 +658,7 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
     for (int q = 0; q < (K2 * K2) / 256; ++q) {
         const int e = tid + 256 * q;
         const int n = e / K2, kk = e - n * K2;  // consecutive threads: consecutive k of column n
-        Bs[kk * K2 + n] = useUR ? URv[e] * Sv[n] : Xv[e];
+        Bs[kk * LDB + n] = useUR ? URv[e] * Sv[n] : Xv[e];
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
@@ -666,20 +672,31 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
     for (int kk = 0; kk < K2; ++kk) {
         T a[4], bv[NC];
         ld_shared_vec<T, 4>(As + kk * LDA + 4 * tx, a);     // 16-byte aligned: LDA * size and 4 tx
-        ld_shared_vec<T, NC>(Bs + kk * K2 + NC * ty, bv);
+        ld_shared_vec<T, NC>(Bs + kk * LDB + NC * ty, bv);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < NC; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
+    // the thread's 4 rows of each output column in 16-byte stores where aligned and whole
+    const bool vst = (reinterpret_cast<uintptr_t>(dstM) & 15) == 0 && (ldd % VE) == 0 && r0 + 4 * tx + 3 < rows;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         const int col = bj_col(bi, bj, bw, NC * ty + j, nn);
         if (col < 0) continue;
         T* d = dstM + (size_t)col * ldd + r0 + 4 * tx;
+        if (vst) {
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4*>(d) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+            } else {
+                reinterpret_cast<double2*>(d)[0] = make_double2(acc[0][j], acc[1][j]);
+                reinterpret_cast<double2*>(d)[1] = make_double2(acc[2][j], acc[3][j]);
+            }
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (r0 + 4 * tx + i < rows) d[i] = acc[i][j];
+            for (int i = 0; i < 4; ++i)
+                if (r0 + 4 * tx + i < rows) d[i] = acc[i][j];
+        }
     }
 }
 
