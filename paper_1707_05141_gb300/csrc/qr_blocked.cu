@@ -144,9 +144,20 @@ __global__ void __launch_bounds__(256) qb_panel_kernel(int p, unsigned char* ws,
     T* G = diag + kPw;                                 // V^T V, 32 x 33
     T* Ts = G + kPw * (kPw + 1);                       // T, 32 x 33
     T* X = qb_X<T>(ws, L, b);
-    for (int e = threadIdx.x; e < ld * kPw; e += blockDim.x) {
-        const int c = e / ld, r = e - c * ld;
-        S[e] = (r < rows && j0 + c < nn) ? X[(size_t)(j0 + c) * mm + j0 + r] : T(0);
+    constexpr int kRun = 8;   // each thread's loads in flight together, then its shared stores
+    for (int e0 = 0; e0 < ld * kPw; e0 += kRun * (int)blockDim.x) {
+        T x[kRun];
+#pragma unroll
+        for (int u = 0; u < kRun; ++u) {
+            const int e = e0 + threadIdx.x + u * blockDim.x;
+            const int c = e / ld, r = e - c * ld;
+            x[u] = (e < ld * kPw && r < rows && j0 + c < nn) ? X[(size_t)(j0 + c) * mm + j0 + r] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kRun; ++u) {
+            const int e = e0 + threadIdx.x + u * blockDim.x;
+            if (e < ld * kPw) S[e] = x[u];
+        }
     }
     __syncthreads();
     house_factor_smem(S, ld, diag, mr, kPw);
@@ -221,19 +232,34 @@ __global__ void __launch_bounds__(256) qb_apply_kernel(int p, int trans, int til
     const int ti = tid & 15, tj = tid >> 4;
     T w00 = T(0), w01 = T(0), w10 = T(0), w11 = T(0);
     const int rows = mm - j0;
-    for (int r0 = 0; r0 < rows; r0 += kCh) {
-        __syncthreads();
-        for (int e = tid; e < kPw * kCh; e += 256) {
+    // a chunk of V and of C: each thread's loads in flight together, then its shared stores (a
+    // store between two loads would make each load wait for the previous one's data)
+    constexpr int PE = (kPw * kCh) / 256;
+    auto stage = [&](int r0) {
+        T v[PE], x[PE];
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = tid + 256 * q;
             const int c = e / kCh, r = e - c * kCh;
             const int gr = j0 + r0 + r;                // row of X / C
-            T v = T(0), x = T(0);
+            v[q] = T(0);
+            x[q] = T(0);
             if (r0 + r < rows) {
-                if (c < vcols && r0 + r >= c) v = X[(size_t)(j0 + c) * mm + gr];
-                if (c < ncol) x = C[(size_t)(c0 + c) * ldc + gr];
+                if (c < vcols && r0 + r >= c) v[q] = X[(size_t)(j0 + c) * mm + gr];
+                if (c < ncol) x[q] = C[(size_t)(c0 + c) * ldc + gr];
             }
-            Vs[c][r] = v;
-            Cs[c][r] = x;
         }
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = tid + 256 * q;
+            const int c = e / kCh, r = e - c * kCh;
+            Vs[c][r] = v[q];
+            Cs[c][r] = x[q];
+        }
+    };
+    for (int r0 = 0; r0 < rows; r0 += kCh) {
+        __syncthreads();
+        stage(r0);
         __syncthreads();
         const int rn = rows - r0 < kCh ? rows - r0 : kCh;
         for (int r = 0; r < rn; ++r) {
@@ -269,17 +295,7 @@ __global__ void __launch_bounds__(256) qb_apply_kernel(int p, int trans, int til
     // C -= V (op(T) V^T C), chunk by chunk again
     for (int r0 = 0; r0 < rows; r0 += kCh) {
         __syncthreads();
-        for (int e = tid; e < kPw * kCh; e += 256) {
-            const int c = e / kCh, r = e - c * kCh;
-            const int gr = j0 + r0 + r;
-            T v = T(0), x = T(0);
-            if (r0 + r < rows) {
-                if (c < vcols && r0 + r >= c) v = X[(size_t)(j0 + c) * mm + gr];
-                if (c < ncol) x = C[(size_t)(c0 + c) * ldc + gr];
-            }
-            Vs[c][r] = v;
-            Cs[c][r] = x;
-        }
+        stage(r0);
         __syncthreads();
         const int rn = rows - r0 < kCh ? rows - r0 : kCh;
         // thread: row r = tid % kCh, columns (tid / kCh) * 16 .. + 15
@@ -448,9 +464,23 @@ __global__ void __launch_bounds__(256) qb_panel_cluster_kernel(int p, int cs, un
     T* wpart = xq + 2;                  // [2][32]: partial products with the columns to its right
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T* X = qb_X<T>(ws, L, b);
-    for (int e = tid; e < nr * kPw; e += blockDim.x) {
-        const int c = e / nr, lr = e - c * nr;
-        S[c * lds + lr] = j0 + c < nn ? X[(size_t)(j0 + c) * mm + j0 + r0 + lr] : T(0);
+    constexpr int kRun = 8;   // each thread's loads in flight together, then its shared stores
+    for (int e0 = 0; e0 < nr * kPw; e0 += kRun * (int)blockDim.x) {
+        T x[kRun];
+#pragma unroll
+        for (int u = 0; u < kRun; ++u) {
+            const int e = e0 + tid + u * blockDim.x;
+            const int c = e / (nr > 0 ? nr : 1), lr = e - c * nr;
+            x[u] = (e < nr * kPw && j0 + c < nn) ? X[(size_t)(j0 + c) * mm + j0 + r0 + lr] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kRun; ++u) {
+            const int e = e0 + tid + u * blockDim.x;
+            if (e < nr * kPw) {
+                const int c = e / nr, lr = e - c * nr;
+                S[c * lds + lr] = x[u];
+            }
+        }
     }
     __syncthreads();
     for (int i = 0; i < vcols; ++i) {
