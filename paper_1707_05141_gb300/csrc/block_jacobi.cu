@@ -576,92 +576,133 @@ constexpr int bj_upd_cols() { return K2 / 8; }  // output columns per thread
 template <typename T, int K2>
 constexpr int bj_upd_ldb() { return K2 + 16 / (int)sizeof(T); }
 
+// two source tiles (the current item's and the next one's) and the multiplier
 template <typename T, int K2>
 constexpr size_t bj_update_smem()
 {
-    return sizeof(T) * ((size_t)K2 * (kUpdRows + 4) + (size_t)K2 * bj_upd_ldb<T, K2>());
+    return sizeof(T) * (2 * (size_t)K2 * (kUpdRows + 4) + (size_t)K2 * bj_upd_ldb<T, K2>());
 }
 
+// one update item: (rotating pair `it`, 128-row tile `tile`) of a W or V block-column pair
+template <typename T>
+struct UpdItem {
+    bool valid, useUR;
+    int bi, bj, r0, rows, nn, ldd, lds;
+    T* dstM;              // the tile's destination (and, except DIRECT's W tile, its source)
+    const T* sb;          // the source columns (dstM, or DIRECT's packed Q)
+    const T* Xv;          // multiplier: X (GRAM) / V_R (DIRECT), column-major K2 x K2
+    const T* URv;         // DIRECT's W tile: U_R, scaled by S_R
+    const T* Sv;
+};
+
 template <typename T, int K2>
-__device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int step, int bw, int direct, T* const* U,
-                                               const int* LDU, T* const* V, const int* LDV, const int* M,
-                                               const int* N, unsigned char* ws, const BjLayout& L,
-                                               unsigned char* upd_sm)
+__device__ __forceinline__ UpdItem<T> bj_upd_item(int it, int tile, int npairs, int step, int direct, T* const* U,
+                                                  const int* LDU, T* const* V, const int* LDV, const int* M,
+                                                  const int* N, unsigned char* ws, const BjLayout& L)
 {
-    constexpr int LDA = kUpdRows + 4;            // padded row length of the k-major source tile
-    constexpr int NC = bj_upd_cols<K2>();        // output columns per thread (8 for K2 = 64)
-    T* As = reinterpret_cast<T*>(upd_sm);        // As[k * LDA + r] = src(r0 + r, k)
-    constexpr int LDB = bj_upd_ldb<T, K2>();
-    T* Bs = As + (size_t)K2 * LDA;               // Bs[k * LDB + n] = multiplier(k, n)
+    UpdItem<T> q;
     const int b = it / npairs, k = it - b * npairs;
-    BjState* st = reinterpret_cast<BjState*>(ws + L.off_state) + b;
+    const BjState* st = reinterpret_cast<const BjState*>(ws + L.off_state) + b;
     const int mm = st->mm, nn = st->nn, nblk = st->nblk;
     const int nbp = nblk + (nblk & 1);
     const int tilesW = (mm + kUpdRows - 1) / kUpdRows, tilesV = (nn + kUpdRows - 1) / kUpdRows;
-    if (tile >= tilesW + tilesV) return;
-    int bi, bj;
-    round_robin_pair(nbp, step, k, bi, bj);
+    q.valid = tile < tilesW + tilesV;
+    if (!q.valid) return q;
+    round_robin_pair(nbp, step, k, q.bi, q.bj);
     const bool onV = tile >= tilesW;
-    const int r0 = (onV ? tile - tilesW : tile) * kUpdRows;
-    const int rows = onV ? nn : mm;
+    q.r0 = (onV ? tile - tilesW : tile) * kUpdRows;
+    q.rows = onV ? nn : mm;
+    q.nn = nn;
     const bool tr = M[b] < N[b];
-    T* dstM = onV ? (tr ? U[b] : V[b]) : (tr ? V[b] : U[b]);
-    const int ldd = onV ? (tr ? LDU[b] : LDV[b]) : (tr ? LDV[b] : LDU[b]);
-    // multiplier: the inner SVD's right factor X (GRAM: eigenvectors of G; DIRECT: V_R), or, for
-    // the W tile of DIRECT, U_R diag(S_R); column-major K2 x K2, staged row-major (k, n)
-    const T* Xv = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
-    const T* URv = reinterpret_cast<T* const*>(ws + L.off_pUR)[it];
-    const T* Sv = reinterpret_cast<T* const*>(ws + L.off_pS)[it];
-    const bool useUR = direct && !onV;
-    const int tid = threadIdx.x;
-    // source tile, k-major: column kk of the pair (or of the packed Q), rows r0 .. r0 + 127.  Where
-    // the columns are 16-byte aligned every thread has all its 16-byte copies in flight at once
-    // (cp.async, rows past the matrix zero-filled), so the tile arrives in about one memory latency
+    q.dstM = onV ? (tr ? U[b] : V[b]) : (tr ? V[b] : U[b]);
+    q.ldd = onV ? (tr ? LDU[b] : LDV[b]) : (tr ? LDV[b] : LDU[b]);
+    q.Xv = reinterpret_cast<T* const*>(ws + L.off_pX)[it];
+    q.URv = reinterpret_cast<T* const*>(ws + L.off_pUR)[it];
+    q.Sv = reinterpret_cast<T* const*>(ws + L.off_pS)[it];
+    q.useUR = direct && !onV;
     const T* P = reinterpret_cast<T* const*>(ws + L.off_pP)[it];
-    const int ldp = mm > K2 ? mm : K2;
-    const T* sb = useUR ? P : dstM;
-    const int lds = useUR ? ldp : ldd;
+    q.sb = q.useUR ? P : q.dstM;
+    q.lds = q.useUR ? (mm > K2 ? mm : K2) : q.ldd;
+    return q;
+}
+
+// the item's source tile, k-major (As[k * LDA + r] = src(r0 + r, column k of the pair)), rows past
+// the matrix zero: 16-byte cp.async copies, all of a thread's in flight at once, committed as one
+// group (an empty group for an invalid item or unaligned columns, which are copied here directly)
+template <typename T, int K2>
+__device__ __forceinline__ void bj_upd_stage_a(const UpdItem<T>& q, int bw, T* As)
+{
+    constexpr int LDA = kUpdRows + 4;
     constexpr int VE = 16 / (int)sizeof(T);    // elements per 16-byte copy
     constexpr int CPC = kUpdRows / VE;         // copies per column
-    if ((reinterpret_cast<uintptr_t>(sb) & 15) == 0 && (lds % VE) == 0) {
+    const int tid = threadIdx.x;
+    if (q.valid) {
+        if ((reinterpret_cast<uintptr_t>(q.sb) & 15) == 0 && (q.lds % VE) == 0) {
 #pragma unroll
-        for (int q = 0; q < (K2 * CPC) / 256; ++q) {
-            const int e = tid + 256 * q;
-            const int kk = e / CPC, r = (e - kk * CPC) * VE;
-            const int col = useUR ? kk : bj_col(bi, bj, bw, kk, nn);
-            int valid = col >= 0 ? rows - (r0 + r) : 0;
-            valid = valid < 0 ? 0 : (valid > VE ? VE : valid);
-            const T* src = valid > 0 ? sb + (size_t)col * lds + r0 + r : sb;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(As + kk * LDA + r);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
-                         "r"(valid * (int)sizeof(T))
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    } else {
-        for (int e = tid; e < K2 * kUpdRows; e += 256) {
-            const int kk = e / kUpdRows, r = e - kk * kUpdRows;
-            T v = T(0);
-            if (r0 + r < rows) {
-                if (useUR) {
-                    v = P[(size_t)kk * ldp + r0 + r];
-                } else {
-                    const int col = bj_col(bi, bj, bw, kk, nn);
-                    if (col >= 0) v = dstM[(size_t)col * ldd + r0 + r];
-                }
+            for (int u = 0; u < (K2 * CPC) / 256; ++u) {
+                const int e = tid + 256 * u;
+                const int kk = e / CPC, r = (e - kk * CPC) * VE;
+                const int col = q.useUR ? kk : bj_col(q.bi, q.bj, bw, kk, q.nn);
+                int valid = col >= 0 ? q.rows - (q.r0 + r) : 0;
+                valid = valid < 0 ? 0 : (valid > VE ? VE : valid);
+                const T* src = valid > 0 ? q.sb + (size_t)col * q.lds + q.r0 + r : q.sb;
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(As + kk * LDA + r);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                             "r"(valid * (int)sizeof(T))
+                             : "memory");
             }
-            As[kk * LDA + r] = v;
+        } else {
+            for (int e = tid; e < K2 * kUpdRows; e += 256) {
+                const int kk = e / kUpdRows, r = e - kk * kUpdRows;
+                T v = T(0);
+                if (q.r0 + r < q.rows) {
+                    const int col = q.useUR ? kk : bj_col(q.bi, q.bj, bw, kk, q.nn);
+                    if (col >= 0) v = q.sb[(size_t)col * q.lds + q.r0 + r];
+                }
+                As[kk * LDA + r] = v;
+            }
         }
     }
-    // the multiplier, transposed into Bs (its loads issued together, then stored)
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// the multiplier of the item (consecutive threads: consecutive k of a column), into registers
+template <typename T, int K2>
+__device__ __forceinline__ void bj_upd_load_b(const UpdItem<T>& q, T (&br)[(K2 * K2) / 256])
+{
 #pragma unroll
-    for (int q = 0; q < (K2 * K2) / 256; ++q) {
-        const int e = tid + 256 * q;
-        const int n = e / K2, kk = e - n * K2;  // consecutive threads: consecutive k of column n
-        Bs[kk * LDB + n] = useUR ? URv[e] * Sv[n] : Xv[e];
+    for (int u = 0; u < (K2 * K2) / 256; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        const int n = e / K2;
+        br[u] = !q.valid ? T(0) : (q.useUR ? q.URv[e] * q.Sv[n] : q.Xv[e]);
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
+}
+
+// ... and transposed into Bs (Bs[k * LDB + n] = multiplier(k, n))
+template <typename T, int K2>
+__device__ __forceinline__ void bj_upd_store_b(const T (&br)[(K2 * K2) / 256], T* Bs)
+{
+    constexpr int LDB = bj_upd_ldb<T, K2>();
+#pragma unroll
+    for (int u = 0; u < (K2 * K2) / 256; ++u) {
+        const int e = threadIdx.x + 256 * u;
+        const int n = e / K2, kk = e - n * K2;
+        Bs[kk * LDB + n] = br[u];
+    }
+}
+
+// the 128 x K2 product of the staged tile and multiplier, written to the destination: each of the
+// 256 threads accumulates a 4-row x (K2 / 8)-column block (one 4-wide and two (K2/16)-wide shared
+// loads per 4 x K2/8 FMAs)
+template <typename T, int K2>
+__device__ __forceinline__ void bj_upd_compute(const UpdItem<T>& q, int bw, const T* As, const T* Bs)
+{
+    if (!q.valid) return;
+    constexpr int LDA = kUpdRows + 4;
+    constexpr int LDB = bj_upd_ldb<T, K2>();
+    constexpr int NC = bj_upd_cols<K2>();
+    constexpr int VE = 16 / (int)sizeof(T);
+    const int tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;       // rows 4 tx .. 4 tx + 3, columns NC ty .. NC ty + NC - 1
     T acc[4][NC];
 #pragma unroll
@@ -679,12 +720,12 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
             for (int j = 0; j < NC; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
     }
     // the thread's 4 rows of each output column in 16-byte stores where aligned and whole
-    const bool vst = (reinterpret_cast<uintptr_t>(dstM) & 15) == 0 && (ldd % VE) == 0 && r0 + 4 * tx + 3 < rows;
+    const bool vst = (reinterpret_cast<uintptr_t>(q.dstM) & 15) == 0 && (q.ldd % VE) == 0 && q.r0 + 4 * tx + 3 < q.rows;
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        const int col = bj_col(bi, bj, bw, NC * ty + j, nn);
+        const int col = bj_col(q.bi, q.bj, bw, NC * ty + j, q.nn);
         if (col < 0) continue;
-        T* d = dstM + (size_t)col * ldd + r0 + 4 * tx;
+        T* d = q.dstM + (size_t)col * q.ldd + q.r0 + 4 * tx;
         if (vst) {
             if constexpr (sizeof(T) == 4) {
                 *reinterpret_cast<float4*>(d) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
@@ -695,25 +736,60 @@ __device__ __forceinline__ void bj_update_item(int it, int tile, int npairs, int
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (r0 + 4 * tx + i < rows) d[i] = acc[i][j];
+                if (q.r0 + 4 * tx + i < q.rows) d[i] = acc[i][j];
         }
     }
 }
 
-// work items are (rotating pair, row tile) flattened; `tiles` is the bound on tiles per pair
+// Work items are (rotating pair, row tile) flattened; `tiles` is the bound on tiles per pair.  Two
+// source-tile buffers: while a CTA multiplies one item, the next item's tile is already being
+// copied in and its multiplier loaded into registers, so the copies' latency is hidden behind the
+// product.
 template <typename T, int K2>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) bj_update_kernel(int tiles, int npairs, int step, int bw, int direct,
-                                                        T* const* U, const int* LDU, T* const* V, const int* LDV,
-                                                        const int* M, const int* N, unsigned char* ws, BjLayout L)
+__global__ void __launch_bounds__(256, 2) bj_update_kernel(int tiles, int npairs, int step, int bw, int direct,
+                                                           T* const* U, const int* LDU, T* const* V, const int* LDV,
+                                                           const int* M, const int* N, unsigned char* ws, BjLayout L)
 {
     extern __shared__ __align__(16) unsigned char upd_sm[];
+    constexpr int LDA = kUpdRows + 4;
+    T* As0 = reinterpret_cast<T*>(upd_sm);
+    T* As1 = As0 + (size_t)K2 * LDA;
+    T* Bs = As1 + (size_t)K2 * LDA;
     BjCounters* C = reinterpret_cast<BjCounters*>(ws + L.off_ctr);
     const int* plist = reinterpret_cast<const int*>(ws + L.off_plist);
     const long long total = (long long)C->pcount * tiles;
-    for (long long w = next_work(&C->claim[3]); w < total; w = next_work(&C->claim[3])) {
-        const long long j = w / tiles;
-        bj_update_item<T, K2>(plist[j], (int)(w - j * tiles), npairs, step, bw, direct, U, LDU, V, LDV, M, N, ws, L,
-                              upd_sm);
+    long long w = next_work(&C->claim[3]);
+    if (w >= total) return;   // (uniform: every thread read the same claimed position)
+    UpdItem<T> q = bj_upd_item<T, K2>(plist[w / tiles], (int)(w % tiles), npairs, step, direct, U, LDU, V, LDV, M,
+                                      N, ws, L);
+    bj_upd_stage_a<T, K2>(q, bw, As0);
+    {
+        T br[(K2 * K2) / 256];
+        bj_upd_load_b<T, K2>(q, br);
+        bj_upd_store_b<T, K2>(br, Bs);
+    }
+    int buf = 0;
+    for (;;) {
+        const long long wn = next_work(&C->claim[3]);   // its barrier: the other buffer is free
+        const bool next = wn < total;
+        UpdItem<T> qn;
+        T br[(K2 * K2) / 256];
+        if (next) {
+            qn = bj_upd_item<T, K2>(plist[wn / tiles], (int)(wn % tiles), npairs, step, direct, U, LDU, V, LDV, M,
+                                    N, ws, L);
+            bj_upd_stage_a<T, K2>(qn, bw, buf ? As0 : As1);
+            bj_upd_load_b<T, K2>(qn, br);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this item's tile has landed
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        bj_upd_compute<T, K2>(q, bw, buf ? As1 : As0, Bs);
+        if (!next) break;
+        __syncthreads();   // every thread is done with Bs
+        bj_upd_store_b<T, K2>(br, Bs);
+        q = qn;
+        buf ^= 1;
     }
 }
 
