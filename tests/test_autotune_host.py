@@ -71,3 +71,21 @@ def test_block_choice_arguments_and_cache_keys(tmp_path, monkeypatch):
     monkeypatch.setattr(autotune, "set_block_choice", lambda *a: calls.append(a))
     assert autotune.apply_cache() == 1
     assert calls == [(bs.F32, 512, 512, 16, 13)]
+
+
+def test_block_width_zero_resolves_through_the_table():
+    """block_width = 0 in the workspace query takes the recorded block width for the size bin (the
+    call resolves it the same way), and 32 when nothing is recorded (host only)."""
+    L = bs.lib()
+    w32 = L.batched_svd_block_jacobi_workspace(0, 10, 512, 512, 32, 0)
+    w16 = L.batched_svd_block_jacobi_workspace(0, 10, 512, 512, 16, 0)
+    assert w32 > 0 and w16 > 0 and w16 != w32
+    try:
+        assert L.bsvd_set_block_choice(0, 512, 512, 0, 0) == 0
+        assert L.batched_svd_block_jacobi_workspace(0, 10, 512, 512, 0, 0) == w32
+        assert L.bsvd_set_block_choice(0, 400, 300, 16, 0) == 0              # the same size bin (512, 512)
+        assert L.batched_svd_block_jacobi_workspace(0, 10, 512, 512, 0, 0) == w16
+        assert L.batched_svd_block_jacobi_workspace(0, 10, 200, 200, 0, 0) == \
+            L.batched_svd_block_jacobi_workspace(0, 10, 200, 200, 32, 0)        # another bin: untouched
+    finally:
+        L.bsvd_set_block_choice(0, 512, 512, 0, 0)
